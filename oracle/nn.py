@@ -1,0 +1,89 @@
+"""The light-matter network of Sec. 2 (FP64, numpy), forward and adjoint.
+
+Sec. 2.1: a fully connected network y = phi(W x + b) per layer (Eq. 1), two
+hidden layers of 50 and 30 ReLU units (Eq. relu). Sec. 2.2: its input at a
+grid point is the value of three density fields at the 27 points of the
+3x3x3 cube around it (3 x 27 = 81 inputs).
+
+Output head: the synthetic workload uses one network with a softplus output
+scaled by M_scale (a positive halo-mass field), M = M_scale ln(1 + e^y).
+
+Input ordering (any fixed order is equivalent; this one is shared by the
+weights and both implementations): index = c*27 + (ox+1)*9 + (oy+1)*3 + (oz+1)
+for field c and neighbour offset (ox, oy, oz) in {-1,0,1}^3, periodic.
+Weights: flat vector W1[50][81], b1[50], W2[30][50], b2[30], w3[30], b3.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import expit
+
+N_IN, N_H1, N_H2 = 81, 50, 30
+STENCIL = [(ox, oy, oz) for ox in (-1, 0, 1) for oy in (-1, 0, 1) for oz in (-1, 0, 1)]
+
+
+def unpack(w: np.ndarray):
+    w = np.asarray(w, np.float64)
+    o = 0
+    W1 = w[o:o + N_H1 * N_IN].reshape(N_H1, N_IN); o += N_H1 * N_IN
+    b1 = w[o:o + N_H1]; o += N_H1
+    W2 = w[o:o + N_H2 * N_H1].reshape(N_H2, N_H1); o += N_H2 * N_H1
+    b2 = w[o:o + N_H2]; o += N_H2
+    w3 = w[o:o + N_H2]; o += N_H2
+    b3 = w[o]; o += 1
+    assert o == w.size
+    return W1, b1, W2, b2, w3, b3
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def softplus(y):
+    return np.logaddexp(0.0, y)
+
+
+def stencil_gather(fields: np.ndarray) -> np.ndarray:
+    """[3][N][N][N] -> [81][N^3]: v[c,o](x) = f_c(x + o), periodic."""
+    rows = []
+    for c in range(3):
+        for (ox, oy, oz) in STENCIL:
+            rows.append(np.roll(fields[c], (-ox, -oy, -oz), axis=(0, 1, 2)).ravel())
+    return np.stack(rows)
+
+
+def stencil_gather_T(gv: np.ndarray, N: int) -> np.ndarray:
+    """Transpose of stencil_gather: g_c(y) = sum_o gv[c,o](y - o)."""
+    out = np.zeros((3, N, N, N))
+    r = 0
+    for c in range(3):
+        for (ox, oy, oz) in STENCIL:
+            out[c] += np.roll(gv[r].reshape(N, N, N), (ox, oy, oz), axis=(0, 1, 2))
+            r += 1
+    return out
+
+
+def mlp_forward(fields: np.ndarray, weights: np.ndarray, M_scale: float):
+    """Per-voxel network; returns (M [N][N][N], cache for the adjoint)."""
+    N = fields.shape[1]
+    W1, b1, W2, b2, w3, b3 = unpack(weights)
+    v = stencil_gather(fields)
+    a1 = W1 @ v + b1[:, None]
+    z1 = relu(a1)
+    a2 = W2 @ z1 + b2[:, None]
+    z2 = relu(a2)
+    y = w3 @ z2 + b3
+    M = M_scale * softplus(y)
+    return M.reshape(N, N, N), (a1, a2, y)
+
+
+def mlp_backward(gM: np.ndarray, fields: np.ndarray, weights: np.ndarray, M_scale: float) -> np.ndarray:
+    """Gradient of <gM, M(fields)> w.r.t. the three input fields."""
+    N = fields.shape[1]
+    W1, b1, W2, b2, w3, b3 = unpack(weights)
+    _, (a1, a2, y) = mlp_forward(fields, weights, M_scale)
+    gy = gM.ravel() * M_scale * expit(y)
+    ga2 = np.outer(w3, gy) * (a2 > 0)
+    ga1 = (W2.T @ ga2) * (a1 > 0)
+    gv = W1.T @ ga1
+    return stencil_gather_T(gv, N)

@@ -1,0 +1,182 @@
+"""Pins for oracle.nn, oracle.loss and oracle.lbfgs."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbfgs, loss, nn, pm
+from paper_1805_02247_gb300 import synth
+
+
+def rdot(a, b):
+    a = np.asarray(a); b = np.asarray(b)
+    return float(np.sum(a.real * b.real + a.imag * b.imag))
+
+
+# ----------------------------------------------------------------------------- network
+
+def test_activation_special_values():
+    assert nn.softplus(0.0) == pytest.approx(math.log(2.0), rel=1e-15)
+    assert nn.softplus(800.0) == pytest.approx(800.0, rel=1e-15)  # no overflow
+    assert nn.softplus(-800.0) == pytest.approx(math.exp(-800.0))
+    assert nn.relu(-1e-300) == 0.0 and nn.relu(2.5) == 2.5
+
+
+def test_stencil_order_on_a_delta_field():
+    N = 5
+    f = np.zeros((3, N, N, N))
+    f[1, 2, 3, 4] = 1.0  # field 1, voxel (2,3,4)
+    v = nn.stencil_gather(f)
+    for r, (ox, oy, oz) in enumerate(nn.STENCIL):
+        row = v[27 + r].reshape(N, N, N)
+        # v[c,o](x) = f_c(x + o): nonzero at x = (2,3,4) - o
+        want = np.zeros((N, N, N)); want[(2 - ox) % N, (3 - oy) % N, (4 - oz) % N] = 1.0
+        assert np.array_equal(row, want)
+    assert not v[:27].any() and not v[54:].any()
+    assert nn.STENCIL[13] == (0, 0, 0)
+
+
+def test_stencil_transpose():
+    rng = np.random.default_rng(1)
+    N = 4
+    f = rng.standard_normal((3, N, N, N))
+    gv = rng.standard_normal((81, N**3))
+    assert rdot(nn.stencil_gather(f), gv) == pytest.approx(rdot(f, nn.stencil_gather_T(gv, N)), rel=1e-12)
+
+
+def test_mlp_closed_form_with_hand_set_weights():
+    # W1 picks the centre value of field 0, W2 and w3 pass it through:
+    # M = M_scale * softplus(relu(relu(f0(x))) - 0.5)
+    N = 4
+    w = np.zeros(synth.N_WEIGHTS)
+    W1, b1, W2, b2, w3, _ = nn.unpack(w)  # views into w
+    W1[0, 13] = 1.0
+    W2[0, 0] = 1.0
+    w3[0] = 1.0
+    w[-1] = -0.5  # b3
+    f = np.random.default_rng(2).standard_normal((3, N, N, N))
+    M, _ = nn.mlp_forward(f, w, 1e12)
+    want = 1e12 * np.log1p(np.exp(np.maximum(f[0], 0.0) - 0.5))
+    assert np.allclose(M, want, rtol=1e-14)
+
+
+def test_mlp_backward_by_finite_differences():
+    rng = np.random.default_rng(3)
+    N = 4
+    w = synth.xavier_weights(1).astype(np.float64)
+    w[4050:4100] = rng.uniform(-0.3, 0.3, 50)  # nonzero biases exercise more branches
+    f = rng.standard_normal((3, N, N, N))
+    gM = rng.standard_normal((N, N, N))
+    g = nn.mlp_backward(gM, f, w, 2.0)
+    fun = lambda ff: float(np.sum(gM * nn.mlp_forward(ff, w, 2.0)[0]))
+    for _ in range(5):
+        v = rng.standard_normal(f.shape)
+        eps = 1e-6
+        fd = (fun(f + eps * v) - fun(f - eps * v)) / (2 * eps)
+        assert rdot(g, v) == pytest.approx(fd, rel=1e-6)
+
+
+# ----------------------------------------------------------------------------- loss
+
+def test_prior_equals_full_grid_sum_and_its_gradient():
+    # for a Hermitian field the weighted half-array sum is the full-grid sum
+    setup = pm.PMSetup(N=8, L=100.0, nsteps=1)
+    s = pm.linear_field(synth.white_noise(8, 4), setup)
+    P = pm.power_half(setup)
+    full = np.fft.fftn(pm.irfft3(s))
+    kphys = np.sqrt(sum(k**2 for k in np.meshgrid(*(2 * np.pi * np.fft.fftfreq(8, d=100.0 / 8),) * 3, indexing="ij")))
+    from oracle import cosmo
+    Pfull = cosmo.P_lin_array(kphys) * 8**6 / 100.0**3
+    m = kphys > 0
+    brute = 0.5 * np.sum(np.abs(full[m]) ** 2 / Pfull[m])
+    assert loss.prior(s, P) == pytest.approx(brute, rel=1e-10)
+    g = loss.prior_grad(s, P)
+    w = pm.half_weights(8)
+    assert np.allclose(g[P > 0], (w * s)[P > 0] / P[P > 0], rtol=0, atol=0)
+    assert g[0, 0, 0] == 0
+
+
+def test_residual_without_smoothing_is_closed_form():
+    N = 4
+    rng = np.random.default_rng(5)
+    M = np.exp(rng.uniform(20, 30, (N, N, N)))
+    Dm = np.exp(rng.uniform(20, 30, (N, N, N)))
+    pms = pm.PMSetup(N=N, L=4.0, nsteps=1)
+    ls = loss.LossSetup(R_M=0.0, sigma_N2=0.25, mu_N=0.1, f_eff=0.7)
+    an = loss.Anneal(R_sm=0.0, M0=1e10)
+    L, _ = loss.residual_terms(M, Dm, pms, ls, an)
+    r = 0.1 + np.log(M + 1e10) - np.log(Dm + 1e10)
+    assert L == pytest.approx(0.7 * np.sum((r / (2 * 0.5)) ** 2), rel=1e-13)
+
+
+def test_loss_reduces_to_prior_when_noise_is_huge():
+    N = 8
+    pms = pm.PMSetup(N=N, L=100.0, nsteps=1)
+    ls = loss.LossSetup(sigma_N2=1e30)
+    an = loss.Anneal(R_sm=4.0, M0=1e8)
+    s = pm.linear_field(synth.white_noise(N, 0), pms)
+    w = synth.xavier_weights(1)
+    data = np.full((N, N, N), 1e12)
+    parts, g = loss.loss_and_grad(s, data, w, pms, ls, an)
+    P = pm.power_half(pms)
+    assert parts["loss"] == pytest.approx(loss.prior(s, P), rel=1e-12)
+    assert np.allclose(g, loss.prior_grad(s, P), rtol=1e-9, atol=1e-20)
+
+
+@pytest.mark.parametrize("R_sm", [0.0, 4.0])
+def test_full_gradient_by_finite_differences(R_sm):
+    N = 8
+    pms = pm.PMSetup(N=N, L=100.0, nsteps=2)
+    ls = loss.LossSetup()
+    an = loss.Anneal(R_sm=R_sm, M0=1e8)
+    w = synth.xavier_weights(1)
+    data = loss.synthetic_data(synth.white_noise(N, 2), synth.scatter_noise(N, 2), w, pms, ls)
+    s = 0.5 * pm.linear_field(synth.white_noise(N, 0), pms)
+    parts, g = loss.loss_and_grad(s, data, w, pms, ls, an)
+    f = lambda ss: loss.loss(ss, data, w, pms, ls, an)["loss"]
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = pm.rfft3(rng.standard_normal((N, N, N))) * np.sqrt(pm.power_half(pms) / N**3)
+        v[0, 0, 0] = 0
+        eps = 1e-6
+        fd = (f(s + eps * v) - f(s - eps * v)) / (2 * eps)
+        assert rdot(g, v) == pytest.approx(fd, rel=1e-5)
+
+
+# ----------------------------------------------------------------------------- L-BFGS
+
+def _quadratic(n, seed):
+    rng = np.random.default_rng(seed)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(np.linspace(1.0, 20.0, n)) @ Q.T
+    b = rng.standard_normal(n)
+    return A, b, (lambda x: (0.5 * x @ A @ x - b @ x, A @ x - b))
+
+
+def test_lbfgs_minimises_a_quadratic():
+    A, b, fun = _quadratic(20, 1)
+    st = lbfgs.LBFGSState(x=np.zeros(20))
+    for _ in range(60):
+        status, _, _ = lbfgs.step(fun, st, m=10, tol=0.0)
+        assert status == "ok"
+        if np.linalg.norm(st.g) < 1e-7:  # Armijo on f resolves |g| to ~1e-9 in fp64
+            break
+    assert np.allclose(st.x, np.linalg.solve(A, b), atol=1e-7)
+
+
+def test_two_loop_equals_dense_bfgs_matrix():
+    # with every pair kept, the two-loop product is the BFGS inverse Hessian
+    # built from H0 = gamma I by the rank-two update, applied to g
+    rng = np.random.default_rng(2)
+    n, k = 12, 5
+    S = [rng.standard_normal(n) for _ in range(k)]
+    M = rng.standard_normal((n, n)); M = M @ M.T + n * np.eye(n)
+    Y = [M @ s for s in S]  # s.y > 0
+    g = rng.standard_normal(n)
+    gamma = S[-1] @ Y[-1] / (Y[-1] @ Y[-1])
+    H = gamma * np.eye(n)
+    for s, y in zip(S, Y):
+        rho = 1.0 / (y @ s)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    assert np.allclose(lbfgs.two_loop(g, S, Y), -H @ g, rtol=1e-12, atol=1e-12)
