@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Throughput of the reconstruction hot path: loss + gradient evaluations per second.
+
+One step = one loss_and_grad() call through the C ABI: Zel'dovich ICs, the PM
+kick/drift steps, the network halo-mass map, the smoothed log-mass residual
+and prior (Eq. loss), and the hand-written adjoint back to dL/ds(k), on a
+256^3 mesh with 256^3 particles in a 400 Mpc/h box with 10 PM steps.
+Inputs are seeded synthetic fields (white noise coloured by the BBKS spectrum,
+Xavier network weights, log-normal data scatter). Multi-GPU runs are
+independent replicas (the path does not shard); value counts all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grad evals/s (fwd+adjoint) at 256^3"
+UNIT = "evals/s"
+WORK = dict(N=256, L=400.0, nsteps=10, a0=0.1, R_sm=4.0, M0=1e8, amp2=0.1)
+# fallback denominators when the measured-peaks file is absent
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def workload_name(w=WORK) -> str:
+    return (f"{w['N']}^3 mesh and particles, L={w['L']:g} Mpc/h, Zel'dovich ICs at a={w['a0']} + {w['nsteps']} PM "
+            f"kick-drift steps, 81-50-30-1 ReLU/softplus network on 3 Gaussian-smoothed fields (R=1,2,4 Mpc/h), "
+            f"Eq.(loss) with R_M=3 Mpc/h, sigma_N^2=0.25, R_sm={w['R_sm']:g} Mpc/h, M0={w['M0']:g}; "
+            f"s at 10% fiducial power; one loss+gradient evaluation per step")
+
+
+def algorithmic(name: str, N: int):
+    """Algorithmic bytes (or flops) of one launch of a kernel, from its inputs and outputs."""
+    N3 = N**3
+    NH = N * N * (N // 2 + 1)
+    table = {
+        "z_r2c": ("bytes", 4 * N3 + 8 * NH),
+        "z_c2r": ("bytes", 8 * NH + 4 * N3),
+        "col_pass": ("bytes", 16 * NH),
+        "x_conv_1": ("bytes", 16 * NH), "x_conv_3": ("bytes", 32 * NH), "x_conv_in3": ("bytes", 32 * NH),
+        "x_fwd_1": ("bytes", 16 * NH), "x_fwd_in3": ("bytes", 32 * NH),
+        "x_inv_3": ("bytes", 32 * NH), "x_inv_1": ("bytes", 16 * NH),
+        "paint": ("bytes", (12 + 4 + 4 + 4) * N3),     # positions, perm, offsets -> density
+        "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),
+        "kick_drift": ("bytes", (12 + 12 + 24 + 12) * N3),  # F, disp in, mom r/w, disp out
+        "adj_direct": ("bytes", (12 + 12 + 24 + 24) * N3),  # F, disp, lam_x r/w, lam_p r/w
+        "readout_grad": ("bytes", (4 + 12 + 24) * N3),
+        "keys": ("bytes", (12 + 4 + 4) * N3),
+        "scatter": ("bytes", (4 + 4 + 4 + 4) * N3),
+        "stencil_T": ("bytes", (81 + 3) * 4 * N3),
+        "mlp_fwd": ("flops", 2 * (4050 + 1500 + 30) * N3),
+        "mlp_bwd": ("flops", 2 * 2 * (4050 + 1500 + 30) * N3),
+    }
+    return table.get(name)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+def _oracle_eval_seconds(N: int, nsteps: int, threads: int = 1) -> float:
+    """Time one oracle loss+gradient at N^3 in a fresh process limited to `threads` threads."""
+    code = f"""
+import time, numpy as np, sys
+sys.path.insert(0, {ROOT!r})
+from oracle import loss as ol, pm as opm
+from paper_1805_02247_gb300 import synth
+N, L, ns = {N}, {WORK['L']}, {nsteps}
+setup = opm.PMSetup(N=N, L=L, nsteps=ns)
+ls = ol.LossSetup()
+w = synth.xavier_weights(1)
+s = np.sqrt({WORK['amp2']}) * opm.linear_field(synth.white_noise(N, 0).astype(np.float64), setup)
+data = np.exp(26.0 + 0.3 * synth.scatter_noise(N, 2).astype(np.float64))
+an = ol.Anneal(R_sm={WORK['R_sm']}, M0={WORK['M0']})
+t = time.perf_counter()
+ol.loss_and_grad(s, data, w, setup, ls, an)
+print(time.perf_counter() - t)
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(sample_N: int = 64):
+    """Oracle evaluation at sample_N^3 with the same steps, scaled by the voxel ratio to 256^3."""
+    t = _oracle_eval_seconds(sample_N, WORK["nsteps"], threads=1)
+    scale = (WORK["N"] / sample_N) ** 3
+    return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 numpy-oracle loss+gradient at {sample_N}^3 (same box, steps and loss), "
+                       f"{t:.2f} s on 1 host thread, scaled by the voxel ratio {scale:g} to {WORK['N']}^3")}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample_N = 32 if args.steps + args.warmup > 6 else 64
+    for _ in range(args.warmup):
+        _oracle_eval_seconds(sample_N, WORK["nsteps"])
+    times = [_oracle_eval_seconds(sample_N, WORK["nsteps"]) for _ in range(args.steps)]
+    scale = (WORK["N"] / sample_N) ** 3
+    per = sum(times) / len(times) * scale
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "N": WORK["N"], "nsteps": WORK["nsteps"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step one oracle loss+gradient at {sample_N}^3 scaled by {scale:g}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1805_02247_gb300 import build, pmrecon, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(build.LIB):
+        build.build()
+    if world > 1:
+        dist.barrier()
+    build.build()  # no-op once fresh
+    N = WORK["N"]
+    cfg = pmrecon.default_config(N=N, L=WORK["L"], nsteps=WORK["nsteps"], a0=WORK["a0"])
+    w = torch.from_numpy(synth.xavier_weights(1)).to(dev)
+    ctx = pmrecon.Context(cfg, w)
+
+    # synthetic inputs (setup, untimed): truth from seed 2, start at 10% power from seed 0
+    s_true = ctx.linear_field(torch.from_numpy(synth.white_noise(N, 2)).to(dev), 1.0)
+    m_true = ctx.nn_halo_map(ctx.pm_forward(s_true))
+    data = (m_true * torch.exp(0.3 * torch.from_numpy(synth.scatter_noise(N, 2)).to(dev))).contiguous()
+    s = ctx.linear_field(torch.from_numpy(synth.white_noise(N, 0)).to(dev), math.sqrt(WORK["amp2"]))
+    g = ctx.half()
+    del s_true, m_true
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.loss_and_grad(s, data, WORK["R_sm"], WORK["M0"], out=g, readback=True)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ---- device-resident throughput
+    barrier()
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    launches = (ctx.launch_count() - l0) // args.steps
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # ---- per-kernel durations (CUDA events after every launch on the context stream)
+    ksteps = max(1, min(args.steps, 3))
+    ctx.timing(True)
+    for _ in range(ksteps):
+        step()
+    rep = ctx.timing_report()
+    ctx.timing(False)
+    total = sum(v[1] for k, v in rep.items() if k != "begin")
+    kernels = sorted(((k, n, t_) for k, (n, t_) in rep.items() if k != "begin"), key=lambda r: -r[2])
+    peaks, peak_src = measured_peaks()
+    roofline = None
+    for name, n, t_ in kernels:
+        alg = algorithmic(name, N)
+        if alg is None:
+            continue
+        kind, amount = alg
+        avg_s = t_ / n / 1e3
+        if kind == "bytes":
+            ach = amount / avg_s / 1e9
+            roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                        "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
+                        "share": t_ / total, "avg_launch_ms": avg_s * 1e3, "algorithmic_per_launch": amount}
+        else:
+            ach = amount / avg_s / 1e12
+            roofline = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                        "frac": ach / FP32_ALU_TFLOPS, "traffic": None,
+                        "peak_source": "derived FP32 FMA peak 152 SM x 128 lanes x 2 x 2.07 GHz",
+                        "share": t_ / total, "avg_launch_ms": avg_s * 1e3, "algorithmic_per_launch": amount}
+        break
+    breakdown = {k: {"launches": n // ksteps, "ms_per_step": t_ / ksteps, "share": t_ / total} for k, n, t_ in kernels}
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    s_h = s.cpu().pin_memory()
+    d_h = data.cpu().pin_memory()
+    g_h = torch.empty(g.shape, dtype=g.dtype).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.copy_(s_h, non_blocking=True)
+        data.copy_(d_h, non_blocking=True)
+        ctx.loss_and_grad(s, data, WORK["R_sm"], WORK["M0"], out=g, readback=True)
+        g_h.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(t.item())
+    h2d = s.numel() * 8 + data.numel() * 4
+    d2h = g.numel() * 8 + 3 * 8
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(), "N": N, "L": WORK["L"], "nsteps": WORK["nsteps"],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (about 10 GB touched per evaluation)"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches) * args.steps,
+            "clocks": clk.summary(),
+            "roofline": roofline,
+            "kernel_breakdown": breakdown,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                line["cpu_baseline"] = cpu_baseline()
+            except Exception as ex:  # reported, not fatal
+                line["cpu_baseline"] = {"error": str(ex)[-300:]}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

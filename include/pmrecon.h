@@ -1,0 +1,209 @@
+/*
+ * pmrecon.h - C ABI of the GB300 (sm_103a) reconstruction hot path of
+ * Modi, Feng & Seljak (2018), "Cosmological reconstruction from galaxy light:
+ * neural network based light-matter connection".
+ *
+ * One call of loss_and_grad() evaluates the loss of Eq. (loss) (Sec. 4.1) at
+ * the linear modes s(k) and its gradient w.r.t. s(k): Zel'dovich initial
+ * conditions at a0, nsteps particle-mesh kick/drift steps (Sec. 3), the
+ * 27-point, 3-field, 81-50-30-1 network of Sec. 2 on the final density, the
+ * smoothed displaced-log-normal residual (Eq. probnoise) with the annealed
+ * residual smoothing of Sec. 4.2, the Gaussian prior (Eq. priorpdf), and the
+ * hand-written adjoint of all of it. recon_step() is one L-BFGS iteration
+ * (Sec. 4.2) around it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named *_dev, and every array argument unless stated otherwise,
+ *   are CUDA device pointers owned by the caller; the library never frees them
+ *   and keeps no reference after the call returns.
+ * - Real meshes are float32 [N][N][N], C order (z fastest).
+ * - Fourier arrays ("c64") are interleaved complex float32 in the half layout
+ *   [N][N][N/2+1] (the real-to-complex layout), with the field defined as
+ *   f(x) = N^-3 sum_k s(k) exp(i k.x). Real and imaginary parts of every entry
+ *   are independent real variables (Sec. 4.1); gradients are w.r.t. them.
+ * - Particle arrays are float32 SoA [3][np] in grid units (cell = L/N Mpc/h);
+ *   the j-th component of particle i is at p[j*np + i].
+ * - All work is enqueued on the context's stream and is asynchronous unless a
+ *   function says it synchronises (those that return host scalars do).
+ * - Every function returns PMR_OK (0) or a negative PMR_E* code; the message
+ *   of the last failure is available from pmr_last_error(). A failed call
+ *   leaves output buffers in an unspecified state but the context usable.
+ */
+#ifndef PMRECON_H
+#define PMRECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMR_OK 0
+#define PMR_EINVAL (-1)      /* bad argument or configuration */
+#define PMR_ENOMEM (-2)      /* device allocation failed */
+#define PMR_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define PMR_ENAN (-4)        /* loss is not finite (e.g. M_R + M0 <= 0) */
+#define PMR_ELINESEARCH (-5) /* no Armijo step within 20 halvings */
+#define PMR_ESTATE (-6)      /* call order violated (e.g. adjoint before forward) */
+
+/* Problem definition. pmr_default_config() fills the synthetic 32^3 workload. */
+typedef struct pmr_config {
+    int N;              /* mesh side; N = 2^a 3^b, 8 <= N <= 512; one particle per cell */
+    double L;           /* box side, Mpc/h */
+    int nsteps;         /* PM kick-drift steps, uniform in a from a0 to 1 (Sec. 3: 5) */
+    double a0;          /* scale factor of the initial conditions (Sec. 3: z = 9) */
+    double omega_m;     /* Sec. 3: 0.3175 (flat LCDM) */
+    double sigma8;      /* linear amplitude of the BBKS spectrum */
+    double gamma_bbks;  /* BBKS shape parameter */
+    double R_feat[3];   /* Gaussian scales of the three network input fields, Mpc/h (Sec. 2.2) */
+    double R_M;         /* smoothing of model and data mass inside the log, Mpc/h (Sec. 3.2: 3) */
+    double sigma_N2;    /* noise variance of Eq. (loss) (Sec. 4.3: 0.25) */
+    double mu_N;        /* offset of Eq. (loss) */
+    double f_eff;       /* effective-points factor of Eq. (loss) (Sec. 4.1: 1) */
+    double M_scale;     /* halo mass per unit softplus output, M_sun/h */
+    int lbfgs_m;        /* L-BFGS memory (correction pairs), 1..64 */
+    double lbfgs_tol;   /* relative loss decrease that counts as converged (Sec. 4.3: 1e-3) */
+} pmr_config;
+
+/* Per-stage annealing parameters of Sec. 4.2. */
+typedef struct pmr_anneal {
+    double R_sm; /* Gaussian smoothing of the residual, Mpc/h; 0 = none */
+    double M0;   /* nuisance mass added inside the log, M_sun/h (Eq. var) */
+} pmr_anneal;
+
+typedef struct pmr_ctx pmr_ctx;
+
+/* Fills *cfg with the defaults: N=32, L=100, nsteps=3, a0=0.1, omega_m=0.3175,
+ * sigma8=0.8, Gamma=0.21, R_feat={1,2,4}, R_M=3, sigma_N2=0.25, mu_N=0,
+ * f_eff=1, M_scale=1e12, lbfgs_m=10, lbfgs_tol=1e-3. */
+void pmr_default_config(pmr_config* cfg);
+
+/* Device bytes pmr_create() will allocate for this configuration (used to
+ * admit jobs by HBM footprint). Returns 0 for an invalid configuration. */
+size_t pmr_workspace_bytes(const pmr_config* cfg);
+
+/* Creates a context: validates cfg, allocates the workspace on the current
+ * device, computes the growth factors and the linear power table on the host
+ * (float64), and copies the network weights.
+ * nn_weights_dev: device float32[5661] laid out W1[50][81], b1[50], W2[30][50],
+ *   b2[30], w3[30], b3; input index c*27 + (ox+1)*9 + (oy+1)*3 + (oz+1) for
+ *   field c and neighbour offset (ox,oy,oz) (Sec. 2.1-2.2). Copied.
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream, pmr_ctx** out);
+int pmr_destroy(pmr_ctx* ctx);
+int pmr_set_stream(pmr_ctx* ctx, void* stream);
+const char* pmr_last_error(const pmr_ctx* ctx);
+
+/* ---------------------------------------------------------------- the path */
+
+/* Linear modes from white noise: s(k) = amplitude * sqrt(P(k) N^6 / L^3 / N^3)
+ * * rfft(white)(k), s(0) = 0, so <|s|^2> = amplitude^2 P(k) N^6/L^3 (the
+ * Gaussian field of Eq. priorpdf; amplitude^2 = 0.1 gives the 10%-power
+ * starting point of Sec. 4.3). white: float32 mesh. s_k: c64 half array. */
+int pmr_linear_field(pmr_ctx* ctx, const float* white, double amplitude, void* s_k);
+
+/* Forward PM model (Sec. 3): s(k) -> final overdensity delta = rho/rho_bar - 1
+ * (CIC, Sec. 2). Stores the per-step particle positions in the context for
+ * pm_adjoint(). s_k: c64 half array; delta_out: float32 mesh. */
+int pm_forward(pmr_ctx* ctx, const void* s_k, float* delta_out);
+
+/* Adjoint of the last pm_forward() on this context (Sec. 4.2, PM derivatives
+ * written by hand): grad_s_k = (d delta/d s)^T grad_delta. Force fields are
+ * recomputed from the stored positions. Returns PMR_ESTATE without a forward. */
+int pm_adjoint(pmr_ctx* ctx, const float* grad_delta, void* grad_s_k);
+
+/* Network halo-mass map (Sec. 2): delta -> three Gaussian-smoothed fields ->
+ * per-voxel 81-50-30-1 ReLU network on the 3x3x3 neighbourhood -> M_scale *
+ * softplus(y). delta, mass_out: float32 meshes. */
+int nn_halo_map(pmr_ctx* ctx, const float* delta, float* mass_out);
+
+/* Adjoint of nn_halo_map at delta: grad_delta = (dM/d delta)^T grad_mass. */
+int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const float* grad_mass, float* grad_delta);
+
+/* Loss of Eq. (loss) at s(k) and its gradient (Sec. 4.1-4.2).
+ * data_mass: float32 mesh of the observed halo mass M^data (unsmoothed).
+ * loss_out: HOST double[3] = {total, prior, residual}; the call synchronises
+ *   the stream to return it. May be NULL (then nothing is read back).
+ * grad_s_k: c64 half array, may alias nothing else. */
+int loss_and_grad(pmr_ctx* ctx, const void* s_k, const float* data_mass, const pmr_anneal* an,
+                  double* loss_out, void* grad_s_k);
+
+/* One L-BFGS iteration (Sec. 4.2) on s(k) in place: two-loop direction from the
+ * context's history (float64 on the device), Armijo backtracking (step 1,
+ * halved up to 20 times, c1 = 1e-4), history update. The first call after
+ * pmr_lbfgs_reset() (or after the annealing parameters change) evaluates the
+ * gradient at s first and searches along -g/|g|.
+ * loss_out: HOST double[3] of the accepted point. converged: HOST int, set to 1
+ * when (L_old - L_new) < lbfgs_tol * |L_old| (Sec. 4.3 stop rule). Synchronises. */
+int recon_step(pmr_ctx* ctx, void* s_k, const float* data_mass, const pmr_anneal* an,
+               double* loss_out, int* converged);
+int pmr_lbfgs_reset(pmr_ctx* ctx);
+
+/* -------------------------------------------- single steps (for parity tests) */
+
+/* Cell keys and stable counting sort of np particles (CIC, Sec. 2):
+ * key = (floor(wx) N + floor(wy)) N + floor(wz) with w = fmod(u, N), +N if
+ * negative (float32), 0 if the result is N. perm lists particle indices by
+ * (key, index); cell_start[N^3+1] holds segment offsets. keys, perm: uint32[np]. */
+int pmr_cell_sort(pmr_ctx* ctx, const float* x, int64_t np, uint32_t* keys, uint32_t* perm,
+                  uint32_t* cell_start);
+
+/* CIC density by a cell-sorted segmented gather (no float atomics; fixed
+ * summation order): rho(c) = sum over the 8 corner offsets in (ox,oy,oz)
+ * lexicographic order, then over sorted particles, of mass * weight.
+ * mass: float32[np] or NULL for unit mass. rho: float32 mesh. */
+int pmr_paint(pmr_ctx* ctx, const float* x, int64_t np, const float* mass, float* rho);
+
+/* CIC interpolation of a mesh at np positions (the transpose of paint). */
+int pmr_readout(pmr_ctx* ctx, const float* field, const float* x, int64_t np, float* out);
+
+/* Gradient of CIC interpolation w.r.t. position: out[3][np]. */
+int pmr_readout_grad(pmr_ctx* ctx, const float* field, const float* x, int64_t np, float* out);
+
+/* Real-to-complex 3D FFT (unnormalised) and its inverse (with 1/N^3, imaginary
+ * parts of self-conjugate entries ignored). in/out per the conventions above. */
+int pmr_rfft(pmr_ctx* ctx, const float* in, void* out);
+int pmr_irfft(pmr_ctx* ctx, const void* in, float* out);
+
+/* PM force F = -grad phi, lap phi = 1.5 Omega_m delta, spectral (i k / k^2,
+ * zero at k = 0 and on each component's Nyquist plane). F: float32 [3][N^3]. */
+int pmr_force(pmr_ctx* ctx, const float* delta, float* F);
+
+/* Gaussian smoothing exp(-k^2 R^2 / 2), R in Mpc/h; R = 0 copies. */
+int pmr_smooth(pmr_ctx* ctx, const float* in, double R, float* out);
+
+/* Zel'dovich ICs at a0 (Sec. 3): x = q + D(a0) psi, p = G_p(a0) psi with
+ * psi_k = i k s_k / k^2 (k = 2 pi n / N in grid units). Returns the
+ * displacement disp = x - q (q = the particle's lattice point, particle index
+ * (ix N + iy) N + iz) and p, both float32 [3][N^3]. */
+int pmr_za_ics(pmr_ctx* ctx, const void* s_k, float* disp, float* p);
+
+/* Growth factors the stepping uses (float64, host): D(a), G_p(a), G_f(a). */
+int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* Gf);
+
+/* L-BFGS two-loop direction d = -H g (Sec. 4.2) for k pairs, float64 device
+ * vectors of length n: S and Y are [k][n], oldest first. */
+int pmr_lbfgs_direction(pmr_ctx* ctx, const double* g, const double* S, const double* Y, int k,
+                        int64_t n, double* d);
+
+/* ------------------------------------------------------------- instrumentation */
+
+/* Number of kernels this context has launched since creation. */
+int64_t pmr_launch_count(const pmr_ctx* ctx);
+
+/* Per-kernel timing with CUDA events on the context stream. enable != 0
+ * starts recording one event after every kernel launch (cost: one event
+ * record per launch); pmr_timing_report() synchronises the stream and writes
+ * one line per kernel name, "name launches total_ms", attributing to each
+ * launch the time since the previous recorded event (kernels run back to
+ * back on one stream, so this is the kernel's duration plus any idle gap),
+ * then restarts the window. buf: host char[len]. */
+int pmr_timing(pmr_ctx* ctx, int enable);
+int pmr_timing_report(pmr_ctx* ctx, char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMRECON_H */

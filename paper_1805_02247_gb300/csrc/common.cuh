@@ -1,0 +1,216 @@
+// Shared declarations of the sm_103a reconstruction library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pmrecon.h"
+
+namespace pmr {
+
+// Radix schedule of a 1D FFT of length n (Stockham autosort, radices 4/3/2).
+struct Radix {
+    int n;
+    int nr;
+    int r[12];
+};
+
+Radix make_radix(int n);
+bool radix_ok(int n);
+
+// Fourier-space multiplier applied inside the fused x-pass.
+enum MulType : int { MUL_ONE = 0, MUL_GAUSS = 1, MUL_ODD = 2, MUL_POWER = 3 };
+struct Mul {
+    int type;     // MulType
+    int j;        // component for MUL_ODD (0=x, 1=y, 2=z)
+    float scale;  // overall factor
+    float R2;     // Gaussian: R^2 in grid units
+    int weighted; // multiply by the half-array weight w(kz) (2 interior, 1 on kz=0, N/2)
+};
+
+struct FFTPlan {
+    int N = 0, M = 0, P = 0;
+    Radix rN{}, rM{};
+    float2* twN = nullptr;  // exp(-2 pi i t / N), t < N (device)
+    float2* twM = nullptr;  // exp(-2 pi i t / M), t < M (device)
+};
+
+// Stored L-BFGS history on the device (float64), oldest first in a ring.
+struct LBFGS {
+    int m = 0, k = 0, head = 0;  // capacity, stored pairs, slot of the oldest pair
+    int64_t n = 0;               // real dof (2 * N * N * P)
+    double* x = nullptr;         // current point (float64 master copy)
+    double* g = nullptr;         // gradient at x
+    double* d = nullptr;         // direction
+    double* xt = nullptr;        // trial point
+    double* gt = nullptr;        // gradient at the trial point
+    double* yk = nullptr;        // candidate correction pair (s in d, y here)
+    double* S = nullptr;         // [m][n]
+    double* Y = nullptr;         // [m][n]
+    double* alpha = nullptr;     // [m] first-loop coefficients (device)
+    double* scal = nullptr;      // device scalars (dots)
+    float2* gk = nullptr;        // float32 gradient of the last evaluation (half array)
+    std::vector<double> rho_host;  // 1 / (s.y) per slot
+    bool have_f = false;
+    double f = 0, f_prior = 0, f_res = 0;
+    pmr_anneal an{};
+};
+
+}  // namespace pmr
+
+struct pmr_ctx {
+    pmr_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int device = 0;
+
+    int N = 0, P = 0;
+    int64_t N3 = 0, NH = 0;  // N^3 real cells, N*N*P complex entries
+
+    // growth and stepping (host, float64)
+    double D0 = 0, Gp0 = 0;
+    std::vector<double> kick, drift;
+
+    pmr::FFTPlan plan;
+    float* power_tab = nullptr;     // sqrt(P~/N^3) by integer |n|^2 (device, float32)
+    double* inv_power_tab = nullptr; // 1/P~ by integer |n|^2 (device, float64; 0 at n=0)
+    int ntab = 0;
+
+    float* W = nullptr;  // network weights (device copy)
+    std::vector<float> W_host;  // same, on the host (launch parameters)
+
+    // particle state: displacement from the lattice point, [3][N3]
+    float* disp = nullptr;  // (nsteps+1) checkpoints, [step][3][N3]
+    float* mom = nullptr;   // [3][N3]
+    float* lam_x = nullptr;
+    float* lam_p = nullptr;
+    bool have_forward = false;
+
+    // cell sort
+    uint32_t* keys = nullptr;
+    uint32_t* perm = nullptr;
+    uint32_t* cell_start = nullptr;  // N3 + 1
+    uint32_t* counts = nullptr;      // N3
+    uint32_t* scan_part = nullptr;
+    uint32_t* long_list = nullptr;   // cells whose segment needs the block sort
+    uint32_t* long_count = nullptr;
+    uint32_t* sort_tmp = nullptr;    // N3 scratch for the block sort
+
+    // meshes
+    float* delta = nullptr;
+    float* F = nullptr;     // 3 * N3
+    float* feat = nullptr;  // 3 * N3
+    float* M = nullptr;
+    float* MR = nullptr;
+    float* DR = nullptr;
+    float* rs = nullptr;
+    float* gm = nullptr;    // N3 scratch mesh
+    float* gm2 = nullptr;   // N3 scratch mesh
+    float* gfeat = nullptr; // 3 * N3
+    float* gv = nullptr;    // 81 * N3 network input-gradient scratch
+    float2* cA = nullptr;   // complex work arrays, NH each
+    float2* cB = nullptr;
+    float2* c3 = nullptr;   // 3 * NH
+
+    // reductions
+    double* red_part = nullptr;  // per-block partials
+    double* red_out = nullptr;   // device scalars
+    int red_blocks = 0;
+
+    pmr::LBFGS lb;
+
+    // launch accounting: every kernel launch passes check_launch(); with
+    // timing on, an event is recorded after each launch on the context stream
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<const char*> ev_names;
+    size_t ev_used = 0;
+};
+
+namespace pmr {
+
+// error helpers ----------------------------------------------------------------
+int fail(pmr_ctx* c, int code, const std::string& msg);
+int check_cuda(pmr_ctx* c, cudaError_t e, const char* what);
+int check_launch(pmr_ctx* c, const char* what);
+
+#define PMR_TRY(expr)               \
+    do {                            \
+        int _rc = (expr);           \
+        if (_rc != PMR_OK) return _rc; \
+    } while (0)
+
+// host cosmology (cosmo.cpp) -----------------------------------------------------
+double growth_D(double a, double om);
+double growth_dDda(double a, double om);
+double growth_Gp(double a, double om);
+double growth_Gf(double a, double om);
+double bbks_amplitude(double sigma8, double gamma);
+double bbks_power(double k, double amp, double gamma);
+
+// FFT module (fft.cu) -----------------------------------------------------------
+int fft_init(pmr_ctx* c);
+void fft_free(pmr_ctx* c);
+// real -> half complex (unnormalised)
+int fft_r2c(pmr_ctx* c, const float* in, float2* out);
+// half complex (full k-space) -> real, with 1/N^3; destroys `work` (NH)
+int fft_c2r(pmr_ctx* c, const float2* in, float* out, float2* work);
+// real in -> nout real outs, out_j = irfft(mul_j * rfft(in))
+int conv_1toN(pmr_ctx* c, const float* in, float* const* out, const Mul* mul, int nout);
+// nin real ins -> real out = irfft(sum_i mul_i * rfft(in_i))
+int conv_Nto1(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float* out);
+// k-space in (half array) -> nout real outs, out_j = irfft(mul_j * in)
+int k_to_real(pmr_ctx* c, const float2* in, float* const* out, const Mul* mul, int nout);
+// nin real ins -> k-space out = sum_i mul_i * rfft(in_i)
+int real_to_k(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float2* out);
+
+// PM kernels (pm.cu) ------------------------------------------------------------
+// positions are either explicit absolute positions (lattice == false) or
+// lattice + displacement (lattice == true; q from the particle index)
+int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out);
+int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass,
+          float scale, float offset, float* const* rho);
+int readout(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float* out);
+int readout_grad(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice,
+                 float scale, bool accumulate, float* out);
+int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom);
+int kick_drift(pmr_ctx* c, const float* F, const float* disp_in, float* disp_out, float* mom, float kick,
+               float drift);
+int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
+                    float drift);
+int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad);
+int pm_forward_impl(pmr_ctx* c, const float2* s_k);
+int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state
+int density_from(pmr_ctx* c, const float* disp, float* delta);
+
+// network (nn.cu) ---------------------------------------------------------------
+int nn_features(pmr_ctx* c, const float* delta);  // -> c->feat
+int mlp_forward(pmr_ctx* c, const float* feat, float* M);
+int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat);
+
+// loss (loss.cu) ----------------------------------------------------------------
+int residual_forward(pmr_ctx* c, const float* data, const pmr_anneal* an, double* L_res_dev);
+int residual_backward(pmr_ctx* c, const pmr_anneal* an, float* gM);
+int prior_value(pmr_ctx* c, const float2* s, double* out_dev);
+int prior_grad_add(pmr_ctx* c, const float2* s, float2* grad);
+int reduce_sum_sq(pmr_ctx* c, const float* v, int64_t n, double scale, double* out_dev);
+int check_finite(pmr_ctx* c, const double* v, int n, double* host);
+
+// L-BFGS (lbfgs.cu) -------------------------------------------------------------
+int lbfgs_alloc(pmr_ctx* c);
+void lbfgs_free(pmr_ctx* c);
+int lbfgs_two_loop(pmr_ctx* c, const double* g, const double* S, const double* Y, int k, int head, int m,
+                   int64_t n, const double* rho_host, double* d);
+int dot64(pmr_ctx* c, const double* a, const double* b, int64_t n, double* out_dev);
+int c64_to_f64(pmr_ctx* c, const float2* a, double* out, int64_t nh);
+int f64_to_c64(pmr_ctx* c, const double* a, float2* out, int64_t nh);
+int axpy64(pmr_ctx* c, double* y, const double* x, const double* alpha_dev, double alpha_host, int64_t n,
+           const double* base);
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace pmr

@@ -1,0 +1,500 @@
+// 3D real FFTs on the N^3 mesh as three shared-memory passes (z, y, x),
+// with the Fourier-space multipliers of the method (PM Green's function and
+// gradient, Gaussian smoothing, Zel'dovich displacement, linear power) fused
+// into the x-pass, where every element holds its full (kx, ky, kz) value.
+//
+// Layouts: real [x][y][z]; half complex [x][y][kz], kz < P = N/2 + 1.
+// Forward r2c = z-pass (real rows -> P complex), y-pass, x-pass.
+// Inverse c2r = x-pass, y-pass, z-pass (P complex -> real rows, 1/N^3).
+// Each pass reads and writes the array once (HBM bound); 1D transforms are
+// mixed-radix (4, 3, 2) Stockham autosort in shared memory with float64-built
+// twiddle tables.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pmr {
+
+bool radix_ok(int n) {
+    if (n < 2) return false;
+    while (n % 4 == 0) n /= 4;
+    while (n % 3 == 0) n /= 3;
+    while (n % 2 == 0) n /= 2;
+    return n == 1;
+}
+
+Radix make_radix(int n) {
+    Radix r{};
+    r.n = n;
+    int m = n;
+    while (m % 4 == 0 && m > 4) { r.r[r.nr++] = 4; m /= 4; }
+    while (m % 3 == 0 && m > 1) { r.r[r.nr++] = 3; m /= 3; }
+    if (m == 4) { r.r[r.nr++] = 4; m = 1; }
+    if (m == 2) { r.r[r.nr++] = 2; m = 1; }
+    return r;
+}
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kCols = 8;      // columns (kz) per y/x-pass tile
+constexpr int kRows = 8;      // real rows per z-pass tile
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// R-point DFT in registers; INV uses exp(+2 pi i / R).
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        float2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        // forward: -i * d, inverse: +i * d
+        float2 t3 = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else {  // R == 3
+        const float h = 0.86602540378443864676f;  // sqrt(3)/2
+        float2 a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+        float2 m = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+        // +-i h d
+        float2 r = INV ? make_float2(-h * d.y, h * d.x) : make_float2(h * d.y, -h * d.x);
+        v[0] = cadd(a, s);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+}
+
+// One Stockham stage over `ncols` independent transforms of length n; element
+// (m, c) lives at buf[m*es + c*cs]. COLFAST maps consecutive threads to
+// consecutive columns (es = ncols, cs = 1 layouts).
+template <int R, bool INV, bool COLFAST>
+__device__ __forceinline__ void stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                      const float2* __restrict__ tw, int n, int Ns, int ncols, int es, int cs) {
+    const int nR = n / R;
+    const int W = nR * ncols;
+    const int tstride = n / (Ns * R);
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        int c, j;
+        if (COLFAST) { c = w % ncols; j = w / ncols; }
+        else { j = w % nR; c = w / nR; }
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = src[(j + r * nR) * es + c * cs];
+            if (r > 0) {
+                float2 t = tw[r * k * tstride];
+                if (INV) t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        }
+        dft<R, INV>(v);
+        const int idxD = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es + c * cs] = v[r];
+    }
+}
+
+// Full transform; data starts in a, b is scratch; returns the buffer holding
+// the result. Ends with __syncthreads().
+template <bool INV, bool COLFAST>
+__device__ float2* smem_fft(float2* a, float2* b, const float2* tw, const Radix& rd, int ncols, int es, int cs) {
+    float2* src = a;
+    float2* dst = b;
+    int Ns = 1;
+    for (int s = 0; s < rd.nr; ++s) {
+        const int R = rd.r[s];
+        if (R == 4) stage<4, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
+        else if (R == 2) stage<2, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
+        else stage<3, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
+        __syncthreads();
+        float2* t = src; src = dst; dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+__device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* g_tw, int n) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s_tw[t] = g_tw[t];
+}
+
+// ----------------------------------------------------------------------------- z passes
+
+// Real rows of length N -> P = N/2+1 complex, through one complex FFT of
+// length M = N/2 on z_m = x_2m + i x_2m+1 and the even/odd split
+// X_k = E_k + exp(-2 pi i k / N) O_k.
+__global__ void __launch_bounds__(kThreads) k_z_r2c(const float* __restrict__ in, float2* __restrict__ out,
+                                                      int64_t nrows, int N, Radix rM,
+                                                      const float2* __restrict__ twM, const float2* __restrict__ twN) {
+    extern __shared__ float2 sm[];
+    const int M = N / 2, P = M + 1, ld = M + 1;
+    float2* s_twM = sm;
+    float2* s_twN = s_twM + M;
+    float2* A = s_twN + N;
+    float2* B = A + kRows * ld;
+    load_twiddles(s_twM, twM, M);
+    load_twiddles(s_twN, twN, N);
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int rows = (int)min((int64_t)kRows, nrows - row0);
+    const float2* src = reinterpret_cast<const float2*>(in + row0 * N);
+    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
+        int r = t / M, m = t % M;
+        A[r * ld + m] = (r < rows) ? src[(int64_t)r * M + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* Z = smem_fft<false, false>(A, B, s_twM, rM, kRows, 1, ld);
+    for (int t = threadIdx.x; t < kRows * P; t += blockDim.x) {
+        int r = t / P, k = t % P;
+        if (r >= rows) continue;
+        float2 zk = Z[r * ld + (k % M)];
+        float2 zc = Z[r * ld + ((M - k) % M)];
+        zc.y = -zc.y;
+        float2 e = cscale(cadd(zk, zc), 0.5f);
+        float2 dd = csub(zk, zc);
+        float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
+        out[(row0 + r) * P + k] = cadd(e, cmul(s_twN[k], o));
+    }
+}
+
+// P complex -> real rows with scale; the imaginary parts of X_0 and X_M are
+// ignored (they carry no information for a real signal).
+__global__ void __launch_bounds__(kThreads) k_z_c2r(const float2* __restrict__ in, float* __restrict__ out,
+                                                      int64_t nrows, int N, float scale, Radix rM,
+                                                      const float2* __restrict__ twM, const float2* __restrict__ twN) {
+    extern __shared__ float2 sm[];
+    const int M = N / 2, P = M + 1, ld = M + 1;
+    float2* s_twM = sm;
+    float2* s_twN = s_twM + M;
+    float2* X = s_twN + N;
+    float2* A = X + kRows * ld;
+    float2* B = A + kRows * ld;
+    load_twiddles(s_twM, twM, M);
+    load_twiddles(s_twN, twN, N);
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+    const int rows = (int)min((int64_t)kRows, nrows - row0);
+    for (int t = threadIdx.x; t < kRows * P; t += blockDim.x) {
+        int r = t / P, k = t % P;
+        float2 v = (r < rows) ? in[(row0 + r) * P + k] : make_float2(0.f, 0.f);
+        if (k == 0 || k == M) v.y = 0.f;
+        X[r * ld + k] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
+        int r = t / M, k = t % M;
+        float2 xk = X[r * ld + k];
+        float2 xc = X[r * ld + (M - k)];
+        xc.y = -xc.y;
+        float2 e = cscale(cadd(xk, xc), 0.5f);
+        float2 w = s_twN[k];
+        w.y = -w.y;  // exp(+2 pi i k / N)
+        float2 o = cmul(cscale(csub(xk, xc), 0.5f), w);
+        A[r * ld + k] = make_float2(e.x - o.y, e.y + o.x);  // e + i o
+    }
+    __syncthreads();
+    float2* z = smem_fft<true, false>(A, B, s_twM, rM, kRows, 1, ld);
+    float2* dst = reinterpret_cast<float2*>(out + row0 * N);
+    const float s = scale * 2.0f / (float)N;
+    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
+        int r = t / M, m = t % M;
+        if (r < rows) dst[(int64_t)r * M + m] = cscale(z[r * ld + m], s);
+    }
+}
+
+// ----------------------------------------------------------------------------- y / x passes
+
+struct ColGeom {
+    int n;               // transform length (N)
+    int ncols;           // P
+    int64_t es;          // element stride along the transform axis
+    int64_t os;          // stride of the outer (tile row) index
+};
+
+// Plain column pass (y-pass, or an x-pass without multipliers).
+template <bool INV>
+__global__ void __launch_bounds__(kThreads) k_col(const float2* __restrict__ in, float2* __restrict__ out,
+                                                    ColGeom g, Radix rd, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int n = g.n;
+    float2* s_tw = sm;
+    float2* A = s_tw + n;
+    float2* B = A + n * kCols;
+    load_twiddles(s_tw, tw, n);
+    const int c0 = blockIdx.x * kCols;
+    const int cw = min(kCols, g.ncols - c0);
+    const int64_t base = (int64_t)blockIdx.y * g.os + c0;
+    for (int t = threadIdx.x; t < n * kCols; t += blockDim.x) {
+        int m = t / kCols, c = t % kCols;
+        A[t] = (c < cw) ? in[base + m * g.es + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* R = smem_fft<INV, true>(A, B, s_tw, rd, kCols, kCols, 1);
+    for (int t = threadIdx.x; t < n * kCols; t += blockDim.x) {
+        int m = t / kCols, c = t % kCols;
+        if (c < cw) out[base + m * g.es + c] = R[t];
+    }
+}
+
+struct XFused {
+    const float2* in[3];
+    float2* out[3];
+    int nin, nout;
+    int fwd;  // forward transform along x before the multiply
+    int inv;  // inverse transform along x after it
+    Mul mul[3];
+    const float* ptab;  // sqrt power table for MUL_POWER
+};
+
+__device__ __forceinline__ float2 apply_mul(const Mul& m, float2 v, int nx, int ny, int kz, int N,
+                                            const float* __restrict__ ptab) {
+    const float twopi_n = 6.28318530717958647692f / (float)N;
+    float f = m.scale;
+    if (m.weighted) f *= (kz == 0 || 2 * kz == N) ? 1.0f : 2.0f;
+    if (m.type == MUL_ONE) return cscale(v, f);
+    const int n2 = nx * nx + ny * ny + kz * kz;
+    if (m.type == MUL_POWER) return cscale(v, f * ptab[n2]);
+    const float kx = twopi_n * nx, ky = twopi_n * ny, kzf = twopi_n * kz;
+    const float k2 = kx * kx + ky * ky + kzf * kzf;
+    if (m.type == MUL_GAUSS) return cscale(v, f * expf(-0.5f * k2 * m.R2));
+    // MUL_ODD: i k_j / k^2, zero at k = 0 and on the Nyquist plane of component j
+    const int nj = (m.j == 0) ? nx : (m.j == 1) ? ny : kz;
+    if (n2 == 0 || 2 * abs(nj) == N) return make_float2(0.f, 0.f);
+    const float kj = twopi_n * nj;
+    const float a = f * kj / k2;
+    return make_float2(-a * v.y, a * v.x);
+}
+
+// x-pass with multipliers. Tile: outer index = ky row, columns = kz block,
+// transform axis = x. nin == 1: out_j = [inv] mul_j * [fwd] in_0.
+// nin > 1: out_0 = [inv] sum_i mul_i * [fwd] in_i.
+__global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix rd, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int n = g.n, N = n;
+    float2* s_tw = sm;
+    float2* A = s_tw + n;
+    float2* B = A + n * kCols;
+    float2* K = B + n * kCols;  // kept k-space tile (nin == 1) or accumulator (nin > 1)
+    load_twiddles(s_tw, tw, n);
+    const int c0 = blockIdx.x * kCols;
+    const int cw = min(kCols, g.ncols - c0);
+    const int oy = blockIdx.y;
+    const int ny = (2 * oy <= N) ? oy : oy - N;
+    const int64_t base = (int64_t)oy * g.os + c0;
+    const int T = n * kCols;
+
+    if (p.nin == 1) {
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            int m = t / kCols, c = t % kCols;
+            A[t] = (c < cw) ? p.in[0][base + m * g.es + c] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2* src = A;
+        if (p.fwd) src = smem_fft<false, true>(A, B, s_tw, rd, kCols, kCols, 1);
+        for (int t = threadIdx.x; t < T; t += blockDim.x) K[t] = src[t];
+        __syncthreads();
+        for (int o = 0; o < p.nout; ++o) {
+            for (int t = threadIdx.x; t < T; t += blockDim.x) {
+                int m = t / kCols, c = t % kCols;
+                int nx = (2 * m <= N) ? m : m - N;
+                A[t] = apply_mul(p.mul[o], K[t], nx, ny, c0 + c, N, p.ptab);
+            }
+            __syncthreads();
+            const float2* R = A;
+            if (p.inv) R = smem_fft<true, true>(A, B, s_tw, rd, kCols, kCols, 1);
+            for (int t = threadIdx.x; t < T; t += blockDim.x) {
+                int m = t / kCols, c = t % kCols;
+                if (c < cw) p.out[o][base + m * g.es + c] = R[t];
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int t = threadIdx.x; t < T; t += blockDim.x) K[t] = make_float2(0.f, 0.f);
+        for (int i = 0; i < p.nin; ++i) {
+            for (int t = threadIdx.x; t < T; t += blockDim.x) {
+                int m = t / kCols, c = t % kCols;
+                A[t] = (c < cw) ? p.in[i][base + m * g.es + c] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            const float2* src = A;
+            if (p.fwd) src = smem_fft<false, true>(A, B, s_tw, rd, kCols, kCols, 1);
+            for (int t = threadIdx.x; t < T; t += blockDim.x) {
+                int m = t / kCols, c = t % kCols;
+                int nx = (2 * m <= N) ? m : m - N;
+                K[t] = cadd(K[t], apply_mul(p.mul[i], src[t], nx, ny, c0 + c, N, p.ptab));
+            }
+            __syncthreads();
+        }
+        const float2* R = K;
+        if (p.inv) R = smem_fft<true, true>(K, A, s_tw, rd, kCols, kCols, 1);
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            int m = t / kCols, c = t % kCols;
+            if (c < cw) p.out[0][base + m * g.es + c] = R[t];
+        }
+    }
+}
+
+size_t smem_z(int N, bool c2r) {
+    int M = N / 2, ld = M + 1;
+    return sizeof(float2) * (size_t)(M + N + (c2r ? 3 : 2) * kRows * ld);
+}
+size_t smem_col(int N, int nbuf) { return sizeof(float2) * (size_t)(N + nbuf * N * kCols); }
+
+ColGeom geom_y(const pmr_ctx* c) { return ColGeom{c->N, c->P, (int64_t)c->P, (int64_t)c->N * c->P}; }
+ColGeom geom_x(const pmr_ctx* c) { return ColGeom{c->N, c->P, (int64_t)c->N * c->P, (int64_t)c->P}; }
+
+int launch_z_r2c(pmr_ctx* c, const float* in, float2* out) {
+    int64_t nrows = (int64_t)c->N * c->N;
+    k_z_r2c<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, false), c->stream>>>(in, out, nrows, c->N, c->plan.rM,
+                                                                                c->plan.twM, c->plan.twN);
+    return check_launch(c, "z_r2c");
+}
+
+int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
+    int64_t nrows = (int64_t)c->N * c->N;
+    float scale = (float)(1.0 / ((double)c->N * c->N));
+    k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
+                                                                               c->plan.rM, c->plan.twM, c->plan.twN);
+    return check_launch(c, "z_c2r");
+}
+
+int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
+    dim3 grid(nblocks(g.ncols, kCols), c->N);
+    if (inv) k_col<true><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
+    else k_col<false><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
+    return check_launch(c, "col_pass");
+}
+
+int launch_x_fused(pmr_ctx* c, const XFused& p) {
+    dim3 grid(nblocks(c->P, kCols), c->N);
+    k_x_fused<<<grid, kThreads, smem_col(c->N, 3), c->stream>>>(p, geom_x(c), c->plan.rN, c->plan.twN);
+    // distinct names per variant: their algorithmic bytes differ
+    static const char* names[2][2][4] = {
+        {{"x_mul_1", "x_mul_1", "x_mul_2", "x_mul_3"}, {"x_inv_1", "x_inv_1", "x_inv_2", "x_inv_3"}},
+        {{"x_fwd_1", "x_fwd_1", "x_fwd_2", "x_fwd_3"}, {"x_conv_1", "x_conv_1", "x_conv_2", "x_conv_3"}}};
+    const int width = p.nin > 1 ? p.nin : p.nout;  // inputs (nin > 1) or outputs
+    const char* nm = names[p.fwd ? 1 : 0][p.inv ? 1 : 0][width];
+    return check_launch(c, p.nin > 1 ? (p.inv ? "x_conv_in3" : "x_fwd_in3") : nm);
+}
+
+XFused make_x(const float2* const* in, int nin, float2* const* out, int nout, const Mul* mul, int nmul, bool fwd,
+              bool inv, const pmr_ctx* c) {
+    XFused p{};
+    for (int i = 0; i < nin; ++i) p.in[i] = in[i];
+    for (int i = 0; i < nout; ++i) p.out[i] = out[i];
+    for (int i = 0; i < nmul; ++i) p.mul[i] = mul[i];
+    p.nin = nin;
+    p.nout = nout;
+    p.fwd = fwd;
+    p.inv = inv;
+    p.ptab = c->power_tab;
+    return p;
+}
+
+}  // namespace
+
+int fft_init(pmr_ctx* c) {
+    const int N = c->N, M = N / 2;
+    c->plan.N = N;
+    c->plan.M = M;
+    c->plan.P = M + 1;
+    c->plan.rN = make_radix(N);
+    c->plan.rM = make_radix(M);
+    std::vector<float2> tN(N), tM(M);
+    for (int t = 0; t < N; ++t) {
+        double ang = -2.0 * M_PI * t / N;
+        tN[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    for (int t = 0; t < M; ++t) {
+        double ang = -2.0 * M_PI * t / M;
+        tM[t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->plan.twN, sizeof(float2) * N), "twiddles"));
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->plan.twM, sizeof(float2) * M), "twiddles"));
+    PMR_TRY(check_cuda(c, cudaMemcpy(c->plan.twN, tN.data(), sizeof(float2) * N, cudaMemcpyHostToDevice), "twiddles"));
+    PMR_TRY(check_cuda(c, cudaMemcpy(c->plan.twM, tM.data(), sizeof(float2) * M, cudaMemcpyHostToDevice), "twiddles"));
+    size_t big = smem_col(N, 3);
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_x_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, false)), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, true)), "smem attr"));
+    return PMR_OK;
+}
+
+void fft_free(pmr_ctx* c) {
+    cudaFree(c->plan.twN);
+    cudaFree(c->plan.twM);
+    c->plan.twN = c->plan.twM = nullptr;
+}
+
+int fft_r2c(pmr_ctx* c, const float* in, float2* out) {
+    PMR_TRY(launch_z_r2c(c, in, out));
+    PMR_TRY(launch_col(c, out, out, geom_y(c), false));
+    return launch_col(c, out, out, geom_x(c), false);
+}
+
+int fft_c2r(pmr_ctx* c, const float2* in, float* out, float2* work) {
+    PMR_TRY(launch_col(c, in, work, geom_x(c), true));
+    PMR_TRY(launch_col(c, work, work, geom_y(c), true));
+    return launch_z_c2r(c, work, out);
+}
+
+int conv_1toN(pmr_ctx* c, const float* in, float* const* out, const Mul* mul, int nout) {
+    float2* outs[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
+    PMR_TRY(launch_z_r2c(c, in, c->cA));
+    PMR_TRY(launch_col(c, c->cA, c->cA, geom_y(c), false));
+    const float2* ins[1] = {c->cA};
+    PMR_TRY(launch_x_fused(c, make_x(ins, 1, outs, nout, mul, nout, true, true, c)));
+    for (int j = 0; j < nout; ++j) {
+        PMR_TRY(launch_col(c, outs[j], outs[j], geom_y(c), true));
+        PMR_TRY(launch_z_c2r(c, outs[j], out[j]));
+    }
+    return PMR_OK;
+}
+
+int conv_Nto1(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float* out) {
+    float2* ks[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
+    for (int i = 0; i < nin; ++i) {
+        PMR_TRY(launch_z_r2c(c, in[i], ks[i]));
+        PMR_TRY(launch_col(c, ks[i], ks[i], geom_y(c), false));
+    }
+    const float2* ins[3] = {ks[0], ks[1], ks[2]};
+    float2* outs[1] = {c->cA};
+    PMR_TRY(launch_x_fused(c, make_x(ins, nin, outs, 1, mul, nin, true, true, c)));
+    PMR_TRY(launch_col(c, c->cA, c->cA, geom_y(c), true));
+    return launch_z_c2r(c, c->cA, out);
+}
+
+int k_to_real(pmr_ctx* c, const float2* in, float* const* out, const Mul* mul, int nout) {
+    float2* outs[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
+    const float2* ins[1] = {in};
+    PMR_TRY(launch_x_fused(c, make_x(ins, 1, outs, nout, mul, nout, false, true, c)));
+    for (int j = 0; j < nout; ++j) {
+        PMR_TRY(launch_col(c, outs[j], outs[j], geom_y(c), true));
+        PMR_TRY(launch_z_c2r(c, outs[j], out[j]));
+    }
+    return PMR_OK;
+}
+
+int real_to_k(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float2* out) {
+    float2* ks[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
+    for (int i = 0; i < nin; ++i) {
+        PMR_TRY(launch_z_r2c(c, in[i], ks[i]));
+        PMR_TRY(launch_col(c, ks[i], ks[i], geom_y(c), false));
+    }
+    const float2* ins[3] = {ks[0], ks[1], ks[2]};
+    float2* outs[1] = {out};
+    return launch_x_fused(c, make_x(ins, nin, outs, 1, mul, nin, true, false, c));
+}
+
+}  // namespace pmr

@@ -1,0 +1,518 @@
+// Particle-mesh kernels: cell keys and a deterministic counting sort, CIC
+// paint as a cell-sorted segmented gather (no float atomics, fixed summation
+// order), CIC readout and its position gradient, the fused readout + kick +
+// drift step, Zel'dovich initial conditions, and the adjoints (Sec. 3 forward
+// model; Sec. 4.2 gradients written by hand).
+//
+// Particles carry a float32 displacement from their Lagrangian lattice point q
+// (x = q + disp), so the cell index q + floor(disp) and the CIC fraction
+// disp - floor(disp) keep full float32 precision at any mesh size. The
+// explicit-position form (absolute x, wrapped by fmod) serves the
+// single-step entry points.
+#include "common.cuh"
+
+namespace pmr {
+namespace {
+
+constexpr int kT = 256;
+
+struct Cell {
+    int i[3];    // cell of the lower corner, in [0, N)
+    float d[3];  // fractional offset in [0, 1)
+};
+
+// Explicit positions: w = fmod(u, N) (exact), + N if negative, 0 if it rounds to N.
+__device__ __forceinline__ float wrap_pos(float u, float n) {
+    float w = fmodf(u, n);
+    if (w < 0.f) w += n;
+    if (w >= n) w = 0.f;
+    return w;
+}
+
+__device__ __forceinline__ Cell cell_of(const float* __restrict__ pos, int64_t np, int64_t i, bool lattice, int N) {
+    Cell c;
+    if (lattice) {
+        const int q[3] = {(int)(i / ((int64_t)N * N)), (int)((i / N) % N), (int)(i % N)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float u = pos[a * np + i];
+            float f = floorf(u);
+            c.d[a] = u - f;
+            int ii = (q[a] + (int)f) % N;
+            c.i[a] = ii < 0 ? ii + N : ii;
+        }
+    } else {
+        const float n = (float)N;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float w = wrap_pos(pos[a * np + i], n);
+            float f = floorf(w);
+            c.i[a] = (int)f;
+            c.d[a] = w - f;
+        }
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t key_of(const Cell& c, int N) {
+    return ((uint32_t)c.i[0] * N + c.i[1]) * N + c.i[2];
+}
+
+__device__ __forceinline__ int64_t corner(const Cell& c, int o, int N) {
+    int x = c.i[0] + ((o >> 2) & 1), y = c.i[1] + ((o >> 1) & 1), z = c.i[2] + (o & 1);
+    if (x == N) x = 0;
+    if (y == N) y = 0;
+    if (z == N) z = 0;
+    return ((int64_t)x * N + y) * N + z;
+}
+
+__device__ __forceinline__ float wgt(const Cell& c, int o) {
+    float wx = ((o >> 2) & 1) ? c.d[0] : 1.f - c.d[0];
+    float wy = ((o >> 1) & 1) ? c.d[1] : 1.f - c.d[1];
+    float wz = (o & 1) ? c.d[2] : 1.f - c.d[2];
+    return wx * wy * wz;
+}
+
+// d/dx_a of the corner weight
+__device__ __forceinline__ void dwgt(const Cell& c, int o, float g[3]) {
+    float w[3], s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int bit = (o >> (2 - a)) & 1;
+        w[a] = bit ? c.d[a] : 1.f - c.d[a];
+        s[a] = bit ? 1.f : -1.f;
+    }
+    g[0] = s[0] * w[1] * w[2];
+    g[1] = w[0] * s[1] * w[2];
+    g[2] = w[0] * w[1] * s[2];
+}
+
+// ----------------------------------------------------------------------------- sort
+
+__global__ void k_keys(const float* __restrict__ pos, int64_t np, bool lattice, int N, uint32_t* __restrict__ keys,
+                       uint32_t* __restrict__ counts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    uint32_t k = key_of(cell_of(pos, np, i, lattice, N), N);
+    keys[i] = k;
+    atomicAdd(&counts[k], 1u);  // integer: order-independent
+}
+
+// Exclusive scan, three phases. Phase 1: per-block scan of 4 * kT elements.
+constexpr int kScanPer = 4;
+__global__ void k_scan_local(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                             uint32_t* __restrict__ part) {
+    __shared__ uint32_t warp_tot[kT / 32];
+    const int64_t base = ((int64_t)blockIdx.x * kT + threadIdx.x) * kScanPer;
+    uint32_t v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    // inclusive warp scan of per-thread sums
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = (lane < kT / 32) ? warp_tot[lane] : 0u, ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, ti, d);
+            if (lane >= d) ti += u;
+        }
+        if (lane < kT / 32) warp_tot[lane] = ti - t;  // exclusive
+        if (lane == kT / 32 - 1) part[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[wid] + inc - s;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// Phase 2: exclusive scan of the block totals by one block (serial chunks).
+__global__ void k_scan_part(uint32_t* __restrict__ part, int nb, uint32_t* __restrict__ total_out) {
+    __shared__ uint32_t carry;
+    __shared__ uint32_t wsum[kT / 32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < nb; b0 += kT) {
+        int idx = b0 + threadIdx.x;
+        uint32_t v = idx < nb ? part[idx] : 0u, inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += t;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t t = (lane < kT / 32) ? wsum[lane] : 0u, ti = t;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                uint32_t u = __shfl_up_sync(0xffffffffu, ti, d);
+                if (lane >= d) ti += u;
+            }
+            if (lane < kT / 32) wsum[lane] = ti - t;
+        }
+        __syncthreads();
+        uint32_t ex = carry + wsum[wid] + inc - v;
+        if (idx < nb) part[idx] = ex;
+        __syncthreads();
+        if (threadIdx.x == kT - 1) carry = ex + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t n, const uint32_t* __restrict__ part) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += part[i / (kT * kScanPer)];
+}
+
+__global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t np, const uint32_t* __restrict__ start,
+                          uint32_t* __restrict__ fill, uint32_t* __restrict__ perm) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    uint32_t k = keys[i];
+    uint32_t r = atomicAdd(&fill[k], 1u);
+    perm[start[k] + r] = (uint32_t)i;
+}
+
+// Restore ascending particle index inside each cell segment (atomics above
+// leave it arbitrary): short segments by one thread, long ones queued.
+constexpr int kShort = 16;
+__global__ void k_fix_short(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm, int64_t ncell,
+                            uint32_t* __restrict__ long_list, uint32_t* __restrict__ long_count) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    uint32_t s = start[c], e = start[c + 1], len = e - s;
+    if (len <= 1) return;
+    if (len > kShort) {
+        uint32_t slot = atomicAdd(long_count, 1u);
+        long_list[slot] = (uint32_t)c;
+        return;
+    }
+    uint32_t v[kShort];
+#pragma unroll
+    for (int k = 0; k < kShort; ++k)
+        if (k < (int)len) v[k] = perm[s + k];
+    for (int a = 1; a < (int)len; ++a) {
+        uint32_t x = v[a];
+        int b = a - 1;
+        while (b >= 0 && v[b] > x) { v[b + 1] = v[b]; --b; }
+        v[b + 1] = x;
+    }
+#pragma unroll
+    for (int k = 0; k < kShort; ++k)
+        if (k < (int)len) perm[s + k] = v[k];
+}
+
+// Long segments: one block per listed cell, rank sort (values are distinct).
+__global__ void k_fix_long(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
+                           const uint32_t* __restrict__ long_list, const uint32_t* __restrict__ long_count,
+                           uint32_t* __restrict__ tmp) {
+    const uint32_t nl = *long_count;
+    for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
+        const uint32_t c = long_list[li];
+        const uint32_t s = start[c], len = start[c + 1] - s;
+        for (uint32_t a = threadIdx.x; a < len; a += blockDim.x) {
+            uint32_t va = perm[s + a], rank = 0;
+            for (uint32_t b = 0; b < len; ++b) rank += (perm[s + b] < va);
+            tmp[s + rank] = va;
+        }
+        __syncthreads();
+        for (uint32_t a = threadIdx.x; a < len; a += blockDim.x) perm[s + a] = tmp[s + a];
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- paint / readout
+
+// rho_m(c) = scale * sum_{o in (ox,oy,oz) lex order} sum_{j in bin(c - o), sorted}
+//            mass_m(j) * W_o(x_j) + offset
+template <int NM>
+__global__ void k_paint(const float* __restrict__ pos, int64_t np, bool lattice, int N,
+                        const uint32_t* __restrict__ start, const uint32_t* __restrict__ perm,
+                        const float* __restrict__ mass, float scale, float offset, float* r0, float* r1, float* r2) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N3 = (int64_t)N * N * N;
+    if (c >= N3) return;
+    const int cx = (int)(c / ((int64_t)N * N)), cy = (int)((c / N) % N), cz = (int)(c % N);
+    float acc[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = 0.f;
+#pragma unroll 1
+    for (int o = 0; o < 8; ++o) {
+        const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+        int bx = cx - ox, by = cy - oy, bz = cz - oz;
+        if (bx < 0) bx += N;
+        if (by < 0) by += N;
+        if (bz < 0) bz += N;
+        const int64_t b = ((int64_t)bx * N + by) * N + bz;
+        const uint32_t s = start[b], e = start[b + 1];
+        for (uint32_t j = s; j < e; ++j) {
+            const int64_t i = perm[j];
+            Cell cl = cell_of(pos, np, i, lattice, N);
+            const float w = wgt(cl, o);
+            if (mass == nullptr) {
+                acc[0] += w;
+            } else {
+#pragma unroll
+                for (int m = 0; m < NM; ++m) acc[m] += mass[m * np + i] * w;
+            }
+        }
+    }
+    r0[c] = acc[0] * scale + offset;
+    if (NM > 1) r1[c] = acc[1] * scale + offset;
+    if (NM > 2) r2[c] = acc[2] * scale + offset;
+}
+
+__global__ void k_readout(const float* __restrict__ f, const float* __restrict__ pos, int64_t np, bool lattice, int N,
+                          float* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    Cell cl = cell_of(pos, np, i, lattice, N);
+    float acc = 0.f;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc += wgt(cl, o) * f[corner(cl, o, N)];
+    out[i] = acc;
+}
+
+__global__ void k_readout_grad(const float* __restrict__ f, const float* __restrict__ pos, int64_t np, bool lattice,
+                               int N, float scale, bool accumulate, float* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    Cell cl = cell_of(pos, np, i, lattice, N);
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        float dw[3];
+        dwgt(cl, o, dw);
+        const float v = f[corner(cl, o, N)];
+        g[0] += dw[0] * v;
+        g[1] += dw[1] * v;
+        g[2] += dw[2] * v;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float r = scale * g[a];
+        out[a * np + i] = accumulate ? out[a * np + i] + r : r;
+    }
+}
+
+// ----------------------------------------------------------------------------- stepping
+
+// Forward step: p += kick * R(x) (force read out at x), disp' = disp + drift * p.
+__global__ void k_kick_drift(const float* __restrict__ F, const float* __restrict__ din, float* __restrict__ dout,
+                             float* __restrict__ mom, int64_t np, int N, float kick, float drift) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    Cell cl = cell_of(din, np, i, true, N);
+    float r[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int64_t idx = corner(cl, o, N);
+        const float w = wgt(cl, o);
+        r[0] += w * F[idx];
+        r[1] += w * F[np + idx];
+        r[2] += w * F[2 * np + idx];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float p = mom[a * np + i] + kick * r[a];
+        mom[a * np + i] = p;
+        dout[a * np + i] = din[a * np + i] + drift * p;
+    }
+}
+
+// Adjoint of drift then the direct (weight-gradient) part of the kick adjoint:
+// lam_p += drift * lam_x;  lam_x += kick * sum_j lam_p_j grad_x R_j(x).
+__global__ void k_adj_direct(const float* __restrict__ F, const float* __restrict__ disp, float* __restrict__ lam_x,
+                             float* __restrict__ lam_p, int64_t np, int N, float kick, float drift) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    Cell cl = cell_of(disp, np, i, true, N);
+    float lp[3], lx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lx[a] = lam_x[a * np + i];
+        lp[a] = lam_p[a * np + i] + drift * lx[a];
+        lam_p[a * np + i] = lp[a];
+    }
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        float dw[3];
+        dwgt(cl, o, dw);
+        const int64_t idx = corner(cl, o, N);
+        const float v = lp[0] * F[idx] + lp[1] * F[np + idx] + lp[2] * F[2 * np + idx];
+        g[0] += dw[0] * v;
+        g[1] += dw[1] * v;
+        g[2] += dw[2] * v;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lam_x[a * np + i] = lx[a] + kick * g[a];
+}
+
+// disp = D0 psi, p = Gp0 psi (psi already in disp)
+__global__ void k_za_finish(float* __restrict__ disp, float* __restrict__ mom, int64_t n, float D0, float Gp0) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float psi = disp[i];
+    disp[i] = D0 * psi;
+    mom[i] = Gp0 * psi;
+}
+
+// lam_psi = D0 lam_x + Gp0 lam_p
+__global__ void k_za_adj_combine(const float* __restrict__ lx, const float* __restrict__ lp, float* __restrict__ out,
+                                 int64_t n, float D0, float Gp0) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = D0 * lx[i] + Gp0 * lp[i];
+}
+
+}  // namespace
+
+// ============================================================================= host wrappers
+
+int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out) {
+    const int N = c->N;
+    const int64_t N3 = c->N3;
+    uint32_t* keys = keys_out ? keys_out : c->keys;
+    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
+    k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, keys, c->counts);
+    PMR_TRY(check_launch(c, "keys"));
+    const int64_t per = (int64_t)kT * kScanPer;
+    const int nb = (int)((N3 + per - 1) / per);
+    k_scan_local<<<nb, kT, 0, c->stream>>>(c->counts, c->cell_start, N3, c->scan_part);
+    PMR_TRY(check_launch(c, "scan_local"));
+    k_scan_part<<<1, kT, 0, c->stream>>>(c->scan_part, nb, c->cell_start + N3);
+    PMR_TRY(check_launch(c, "scan_part"));
+    k_scan_add<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->cell_start, N3, c->scan_part);
+    PMR_TRY(check_launch(c, "scan_add"));
+    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
+    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->long_count, 0, sizeof(uint32_t), c->stream), "memset"));
+    k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, c->cell_start, c->counts, c->perm);
+    PMR_TRY(check_launch(c, "scatter"));
+    k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->cell_start, c->perm, N3, c->long_list, c->long_count);
+    PMR_TRY(check_launch(c, "fix_short"));
+    k_fix_long<<<304, kT, 0, c->stream>>>(c->cell_start, c->perm, c->long_list, c->long_count, c->sort_tmp);
+    return check_launch(c, "fix_long");
+}
+
+int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,
+          float offset, float* const* rho) {
+    const unsigned g = nblocks(c->N3, kT);
+    if (nmass <= 1)
+        k_paint<1><<<g, kT, 0, c->stream>>>(pos, np, lattice, c->N, c->cell_start, c->perm, mass, scale, offset,
+                                             rho[0], nullptr, nullptr);
+    else
+        k_paint<3><<<g, kT, 0, c->stream>>>(pos, np, lattice, c->N, c->cell_start, c->perm, mass, scale, offset,
+                                             rho[0], rho[1], rho[2]);
+    return check_launch(c, nmass <= 1 ? "paint" : "paint3");
+}
+
+int readout(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float* out) {
+    k_readout<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, out);
+    return check_launch(c, "readout");
+}
+
+int readout_grad(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float scale,
+                 bool accumulate, float* out) {
+    k_readout_grad<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, scale, accumulate, out);
+    return check_launch(c, "readout_grad");
+}
+
+int density_from(pmr_ctx* c, const float* disp, float* delta) {
+    PMR_TRY(cell_sort(c, disp, c->N3, true, nullptr));
+    float* outs[1] = {delta};
+    // unit-mass particles, one per cell: rho_bar = 1
+    return paint(c, disp, c->N3, true, nullptr, 1, 1.0f, -1.0f, outs);
+}
+
+int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
+    Mul mul[3];
+    for (int j = 0; j < 3; ++j) mul[j] = Mul{MUL_ODD, j, 1.0f, 0.f, 0};
+    float* outs[3] = {disp, disp + c->N3, disp + 2 * c->N3};
+    PMR_TRY(k_to_real(c, s_k, outs, mul, 3));
+    k_za_finish<<<nblocks(3 * c->N3, kT), kT, 0, c->stream>>>(disp, mom, 3 * c->N3, (float)c->D0, (float)c->Gp0);
+    return check_launch(c, "za_finish");
+}
+
+int kick_drift(pmr_ctx* c, const float* F, const float* din, float* dout, float* mom, float kick, float drift) {
+    k_kick_drift<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, kick, drift);
+    return check_launch(c, "kick_drift");
+}
+
+int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
+                    float drift) {
+    k_adj_direct<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, disp, lam_x, lam_p, c->N3, c->N, kick, drift);
+    return check_launch(c, "adj_direct");
+}
+
+// grad_s = sum_j conj(i k_j / k^2) (w / N^3) rfft(D0 lam_x_j + Gp0 lam_p_j)
+int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad) {
+    float* tmp = c->F;  // 3 meshes of scratch
+    k_za_adj_combine<<<nblocks(3 * c->N3, kT), kT, 0, c->stream>>>(lam_x, lam_p, tmp, 3 * c->N3, (float)c->D0,
+                                                                     (float)c->Gp0);
+    PMR_TRY(check_launch(c, "za_adj_combine"));
+    Mul mul[3];
+    const float inv_n3 = (float)(1.0 / (double)c->N3);
+    for (int j = 0; j < 3; ++j) mul[j] = Mul{MUL_ODD, j, -inv_n3, 0.f, 1};
+    const float* ins[3] = {tmp, tmp + c->N3, tmp + 2 * c->N3};
+    return real_to_k(c, ins, mul, 3, grad);
+}
+
+int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
+    const int64_t N3 = c->N3;
+    PMR_TRY(za_ics(c, s_k, c->disp, c->mom));
+    const float om15 = (float)(1.5 * c->cfg.omega_m);
+    Mul fm[3];
+    for (int j = 0; j < 3; ++j) fm[j] = Mul{MUL_ODD, j, om15, 0.f, 0};
+    float* Fj[3] = {c->F, c->F + N3, c->F + 2 * N3};
+    for (int s = 0; s < c->cfg.nsteps; ++s) {
+        const float* din = c->disp + (int64_t)s * 3 * N3;
+        float* dout = c->disp + (int64_t)(s + 1) * 3 * N3;
+        PMR_TRY(density_from(c, din, c->delta));
+        PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
+        PMR_TRY(kick_drift(c, c->F, din, dout, c->mom, (float)c->kick[s], (float)c->drift[s]));
+    }
+    c->have_forward = true;
+    return PMR_OK;
+}
+
+// Reverse sweep. On entry lam_x holds dL/dx at the final positions and lam_p = 0.
+int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
+    const int64_t N3 = c->N3;
+    const float om15 = (float)(1.5 * c->cfg.omega_m);
+    Mul fm[3], fmT[3];
+    for (int j = 0; j < 3; ++j) {
+        fm[j] = Mul{MUL_ODD, j, om15, 0.f, 0};
+        fmT[j] = Mul{MUL_ODD, j, -om15, 0.f, 0};  // conj of an imaginary multiplier
+    }
+    float* Fj[3] = {c->F, c->F + N3, c->F + 2 * N3};
+    float* Gj[3] = {c->gfeat, c->gfeat + N3, c->gfeat + 2 * N3};
+    for (int s = c->cfg.nsteps - 1; s >= 0; --s) {
+        const float* d = c->disp + (int64_t)s * 3 * N3;
+        PMR_TRY(density_from(c, d, c->delta));  // also leaves the cell sort of x_s
+        PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
+        PMR_TRY(adj_kick_direct(c, c->F, d, c->lam_x, c->lam_p, (float)c->kick[s], (float)c->drift[s]));
+        PMR_TRY(paint(c, d, N3, true, c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
+        const float* gins[3] = {Gj[0], Gj[1], Gj[2]};
+        PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
+        PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
+    }
+    return za_adjoint(c, c->lam_x, c->lam_p, grad);
+}
+
+}  // namespace pmr

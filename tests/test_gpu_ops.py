@@ -1,0 +1,138 @@
+"""GPU parity of the single steps of the path (C ABI) against the FP64 oracle.
+
+Tolerances: bit-exact for cell keys, sort order and segment offsets; relative
+L2 <= 1e-5 for float32 fields; 1e-4 for gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import loss as oloss
+from oracle import pm as opm
+from paper_1805_02247_gb300 import synth
+
+from gpu_util import context, f32, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.mark.parametrize("N,np_,lo,hi", [(8, 512, -8.0, 16.0), (16, 3000, -3.0, 19.0), (32, 32**3, 0.0, 32.0),
+                                         (24, 100, 0.0, 24.0)])
+def test_cell_sort_bit_exact(N, np_, lo, hi):
+    ctx, _ = context(N=N)
+    x = synth.uniform_positions(N, np_, seed=N + np_, lo=lo, hi=hi)
+    if np_ >= 16:
+        e = synth.edge_positions(N)
+        x[:, : e.shape[1]] = e
+    keys, perm, start = ctx.cell_sort(to_dev(x))
+    want_keys = opm.cell_keys(x, N)
+    want_perm, want_start = opm.sort_by_cell(want_keys, N)
+    assert np.array_equal(to_np(keys).view(np.uint32), want_keys)
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+
+
+def test_cell_sort_crowded_cells():
+    # many particles in few cells exercises the long-segment path of the stable sort
+    N = 8
+    x = synth.uniform_positions(N, 400, seed=3, lo=2.0, hi=2.9)
+    ctx, _ = context(N=N)
+    keys, perm, start = ctx.cell_sort(to_dev(x))
+    want_perm, want_start = opm.sort_by_cell(opm.cell_keys(x, N), N)
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+
+
+@pytest.mark.parametrize("N,np_", [(16, 4096), (32, 20000), (16, 0)])
+def test_paint_parity_and_mass_conservation(N, np_):
+    ctx, _ = context(N=N)
+    x = synth.uniform_positions(N, max(np_, 1), seed=5, lo=-N, hi=2 * N)[:, :np_]
+    rho = to_np(ctx.paint(to_dev(x)))
+    if np_ == 0:
+        assert not rho.any()
+        return
+    want = opm.paint(f32(x), N)
+    assert rel_l2(rho, want) <= FIELD_TOL
+    assert abs(rho.sum(dtype=np.float64) - np_) <= 1e-6 * np_
+    m = synth.gaussian_vector(np_, seed=6)
+    rho_m = to_np(ctx.paint(to_dev(x), to_dev(m)))
+    assert rel_l2(rho_m, opm.paint(f32(x), N, mass=f32(m))) <= FIELD_TOL
+    # deterministic: same bits twice
+    assert np.array_equal(rho, to_np(ctx.paint(to_dev(x))))
+
+
+def test_readout_and_grad_parity():
+    N = 16
+    ctx, _ = context(N=N)
+    x = synth.uniform_positions(N, 5000, seed=7, lo=-N, hi=2 * N)
+    g = synth.gaussian_vector((N, N, N), seed=8)
+    r = to_np(ctx.readout(to_dev(g), to_dev(x)))
+    assert rel_l2(r, opm.readout(f32(g), f32(x))) <= FIELD_TOL
+    rg = to_np(ctx.readout_grad(to_dev(g), to_dev(x)))
+    assert rel_l2(rg, opm.readout_grad(f32(g), f32(x))) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96])
+def test_rfft_irfft_parity(N):
+    ctx, _ = context(N=N)
+    f = synth.gaussian_vector((N, N, N), seed=N)
+    k = to_np(ctx.rfft(to_dev(f)))
+    assert rel_l2(k, np.fft.rfftn(f32(f))) <= FIELD_TOL
+    # inverse of an arbitrary (non-Hermitian) half array: imaginary parts of
+    # self-conjugate entries are ignored, as by the oracle's irfftn
+    u = synth.gaussian_vector((N, N, N // 2 + 1), seed=N + 1) + 1j * synth.gaussian_vector((N, N, N // 2 + 1), seed=N + 2)
+    got = to_np(ctx.irfft(to_dev(u)))
+    assert rel_l2(got, opm.irfft3(f32(u))) <= FIELD_TOL
+
+
+def test_force_and_smooth_parity():
+    N = 32
+    ctx, cfg = context(N=N, L=100.0)
+    d = synth.gaussian_vector((N, N, N), seed=11)
+    F = to_np(ctx.force(to_dev(d)))
+    assert rel_l2(F, opm.force(f32(d), cfg.omega_m)) <= FIELD_TOL
+    for R in (0.0, 1.0, 4.0):
+        sm = to_np(ctx.smooth(to_dev(d), R))
+        assert rel_l2(sm, opm.smooth(f32(d), R / (100.0 / N))) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("N,L", [(32, 100.0), (24, 400.0)])
+def test_linear_field_and_za_parity(N, L):
+    ctx, cfg = context(N=N, L=L)
+    setup = opm.PMSetup(N=N, L=L, nsteps=3)
+    white = synth.white_noise(N, 0)
+    s = to_np(ctx.linear_field(to_dev(white), 1.0))
+    want = opm.linear_field(f32(white), setup)
+    assert rel_l2(s, want) <= FIELD_TOL
+    s_in = f32(want)
+    disp, mom = ctx.za_ics(to_dev(s_in))
+    x_want, p_want = opm.za_ics(s_in, setup)
+    assert rel_l2(to_np(disp), x_want - opm.lattice(N)) <= FIELD_TOL
+    assert rel_l2(to_np(mom), p_want) <= FIELD_TOL
+
+
+def test_growth_factors_match_oracle():
+    from oracle import cosmo
+    from paper_1805_02247_gb300 import pmrecon
+    _, cfg = context(N=8)
+    for a in (0.1, 0.35, 0.7, 1.0):
+        D, Gp, Gf = pmrecon.growth(cfg, a)
+        assert D == pytest.approx(cosmo.D(a), rel=1e-11)
+        assert Gp == pytest.approx(cosmo.Gp(a), rel=1e-10)
+        assert Gf == pytest.approx(cosmo.Gf(a), rel=1e-11)
+
+
+def test_lbfgs_direction_parity():
+    from oracle import lbfgs as olb
+    ctx, _ = context(N=8)
+    rng = np.random.default_rng(3)
+    n, k = 1000, 6
+    S = [rng.standard_normal(n) for _ in range(k)]
+    Y = [s + 0.3 * rng.standard_normal(n) for s in S]
+    g = rng.standard_normal(n)
+    d = ctx.lbfgs_direction(torch.tensor(g, device="cuda"), torch.tensor(np.stack(S), device="cuda"),
+                            torch.tensor(np.stack(Y), device="cuda"))
+    assert rel_l2(to_np(d), olb.two_loop(g, S, Y)) <= 1e-12

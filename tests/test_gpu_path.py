@@ -1,0 +1,123 @@
+"""GPU parity of the whole path through the C ABI against the FP64 oracle:
+pm_forward / pm_adjoint, nn_halo_map and its adjoint, loss_and_grad, recon_step.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import lbfgs as olb
+from oracle import loss as oloss
+from oracle import nn as onn
+from oracle import pm as opm
+from paper_1805_02247_gb300 import synth
+
+from gpu_util import context, f32, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _problem(N, L, nsteps, amp=1.0):
+    setup = opm.PMSetup(N=N, L=L, nsteps=nsteps)
+    s = f32(amp * opm.linear_field(f32(synth.white_noise(N, 0)), setup))
+    return setup, s
+
+
+@pytest.mark.parametrize("N,L,nsteps", [(16, 100.0, 2), (32, 100.0, 3), (24, 400.0, 5)])
+def test_pm_forward_parity(N, L, nsteps):
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s = _problem(N, L, nsteps)
+    delta = to_np(ctx.pm_forward(to_dev(s)))
+    assert rel_l2(delta, opm.final_density(s, setup)) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("N,L,nsteps", [(16, 100.0, 2), (32, 100.0, 3)])
+def test_pm_adjoint_parity(N, L, nsteps):
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s = _problem(N, L, nsteps)
+    g = synth.gaussian_vector((N, N, N), seed=21)
+    ctx.pm_forward(to_dev(s))
+    got = to_np(ctx.pm_adjoint(to_dev(g)))
+    x_fin, cps, _ = opm.pm_forward(s, setup)
+    want = opm.final_density_T(cps, x_fin, f32(g), setup)
+    assert rel_l2(got, want) <= GRAD_TOL
+
+
+def test_pm_adjoint_needs_forward():
+    from paper_1805_02247_gb300.pmrecon import PMRError
+    ctx, _ = context(N=8)
+    with pytest.raises(PMRError, match="ESTATE"):
+        ctx.pm_adjoint(torch.zeros(8, 8, 8, device="cuda"))
+
+
+def test_nn_halo_map_and_adjoint_parity():
+    N, L = 32, 100.0
+    ctx, _ = context(N=N, L=L)
+    setup = opm.PMSetup(N=N, L=L, nsteps=3)
+    ls = oloss.LossSetup()
+    w = synth.xavier_weights(1)
+    delta = f32(2.0 * synth.gaussian_vector((N, N, N), seed=31))
+    M = to_np(ctx.nn_halo_map(to_dev(delta)))
+    assert rel_l2(M, oloss.nn_halo_map(delta, w, setup, ls)) <= FIELD_TOL
+    gM = f32(synth.gaussian_vector((N, N, N), seed=32))
+    gd = to_np(ctx.nn_halo_map_adjoint(to_dev(delta), to_dev(gM)))
+    assert rel_l2(gd, oloss.nn_halo_map_T(gM, delta, w, setup, ls)) <= GRAD_TOL
+
+
+def _data(N, L, nsteps):
+    setup = opm.PMSetup(N=N, L=L, nsteps=nsteps)
+    w = synth.xavier_weights(1)
+    return f32(oloss.synthetic_data(f32(synth.white_noise(N, 2)), f32(synth.scatter_noise(N, 2)), w, setup,
+                                    oloss.LossSetup()))
+
+
+@pytest.mark.parametrize("N,L,nsteps,R_sm,M0", [(32, 100.0, 3, 4.0, 1e8), (16, 100.0, 2, 0.0, 1e11),
+                                                (24, 400.0, 5, 2.0, 1e12)])
+def test_loss_and_grad_parity(N, L, nsteps, R_sm, M0):
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
+    w = synth.xavier_weights(1)
+    want, gwant = oloss.loss_and_grad(s, data, w, setup, oloss.LossSetup(), oloss.Anneal(R_sm=R_sm, M0=M0))
+    assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
+    assert parts[1] == pytest.approx(want["prior"], rel=FIELD_TOL)
+    assert parts[2] == pytest.approx(want["residual"], rel=FIELD_TOL)
+    assert rel_l2(to_np(g), gwant) <= GRAD_TOL
+
+
+def test_loss_nan_is_reported():
+    from paper_1805_02247_gb300.pmrecon import PMRError
+    N = 16
+    ctx, _ = context(N=N)
+    _, s = _problem(N, 100.0, 3)
+    data = np.full((N, N, N), np.nan, np.float32)
+    with pytest.raises(PMRError, match="ENAN"):
+        ctx.loss_and_grad(to_dev(s), to_dev(data), 0.0, 1e8)
+
+
+def test_recon_step_follows_oracle_lbfgs():
+    N, L, nsteps = 16, 100.0, 2
+    R_sm, M0 = 4.0, 1e8
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s0 = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    w = synth.xavier_weights(1)
+    ls, an = oloss.LossSetup(), oloss.Anneal(R_sm=R_sm, M0=M0)
+
+    def fun(x):
+        parts, g = oloss.loss_and_grad(x, data, w, setup, ls, an)
+        return parts["loss"], g
+
+    st = olb.LBFGSState(x=s0.copy())
+    s_dev = to_dev(s0)
+    d_dev = to_dev(data)
+    for it in range(4):
+        status, conv_o, _ = olb.step(fun, st)
+        parts, conv_g = ctx.recon_step(s_dev, d_dev, R_sm, M0)
+        assert status == "ok"
+        assert parts[0] == pytest.approx(st.f, rel=1e-5), it
+        assert rel_l2(to_np(s_dev), st.x) <= 1e-4, it
+        assert conv_g == conv_o
