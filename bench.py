@@ -341,7 +341,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--N", type=int, default=WORK["N"], help="mesh side (profiling of small cases only)")
+    ap.add_argument("--nsteps", type=int, default=WORK["nsteps"], help="PM steps (profiling of small cases only)")
     args = ap.parse_args()
+    WORK["N"], WORK["nsteps"] = args.N, args.nsteps
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
             for (int t = threadIdx.x; t < T; t += blockDim.x) {
                 int m = t / kCols, c = t % kCols;
                 int nx = (2 * m <= N) ? m : m - N;
-                A[t] = apply_mul(p.mul[o], K[t], nx, ny, c0 + c, N, p.ptab);
+                // padding columns (kz > N/2) stay zero and never index the power table
+                A[t] = (c < cw) ? apply_mul(p.mul[o], K[t], nx, ny, c0 + c, N, p.ptab) : make_float2(0.f, 0.f);
             }
             __syncthreads();
             const float2* R = A;
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
             for (int t = threadIdx.x; t < T; t += blockDim.x) {
                 int m = t / kCols, c = t % kCols;
                 int nx = (2 * m <= N) ? m : m - N;
-                K[t] = cadd(K[t], apply_mul(p.mul[i], src[t], nx, ny, c0 + c, N, p.ptab));
+                if (c < cw) K[t] = cadd(K[t], apply_mul(p.mul[i], src[t], nx, ny, c0 + c, N, p.ptab));
             }
             __syncthreads();
         }

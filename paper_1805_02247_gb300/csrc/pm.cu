@@ -390,8 +390,10 @@ int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* 
     const int64_t N3 = c->N3;
     uint32_t* keys = keys_out ? keys_out : c->keys;
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
-    k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, keys, c->counts);
-    PMR_TRY(check_launch(c, "keys"));
+    if (np > 0) {
+        k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, keys, c->counts);
+        PMR_TRY(check_launch(c, "keys"));
+    }
     const int64_t per = (int64_t)kT * kScanPer;
     const int nb = (int)((N3 + per - 1) / per);
     k_scan_local<<<nb, kT, 0, c->stream>>>(c->counts, c->cell_start, N3, c->scan_part);
@@ -402,8 +404,10 @@ int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* 
     PMR_TRY(check_launch(c, "scan_add"));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->long_count, 0, sizeof(uint32_t), c->stream), "memset"));
-    k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, c->cell_start, c->counts, c->perm);
-    PMR_TRY(check_launch(c, "scatter"));
+    if (np > 0) {
+        k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, c->cell_start, c->counts, c->perm);
+        PMR_TRY(check_launch(c, "scatter"));
+    }
     k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->cell_start, c->perm, N3, c->long_list, c->long_count);
     PMR_TRY(check_launch(c, "fix_short"));
     k_fix_long<<<304, kT, 0, c->stream>>>(c->cell_start, c->perm, c->long_list, c->long_count, c->sort_tmp);

@@ -127,7 +127,7 @@ def test_growth_factors_match_oracle():
 
 def test_lbfgs_direction_parity():
     from oracle import lbfgs as olb
-    ctx, _ = context(N=8)
+    ctx, _ = context(N=16)
     rng = np.random.default_rng(3)
     n, k = 1000, 6
     S = [rng.standard_normal(n) for _ in range(k)]
