@@ -156,6 +156,27 @@ int pmr_cell_sort(pmr_ctx* ctx, const float* x, int64_t np, uint32_t* keys, uint
  * mass: float32[np] or NULL for unit mass. rho: float32 mesh. */
 int pmr_paint(pmr_ctx* ctx, const float* x, int64_t np, const float* mass, float* rho);
 
+/* The same deterministic CIC paint as pmr_paint(), for callers that cannot
+ * allocate device memory. The paper has no counterpart: this entry point exists
+ * for the library's users. pmr_paint() needs a context, and pmr_create() calls
+ * cudaMalloc; code that runs while a CUDA graph is being captured, framework
+ * plug-ins whose host owns every device allocation, and loops that must not
+ * let cudaMalloc/cudaFree synchronise the device cannot make that call. This
+ * variant allocates nothing: its sorting scratch (about 6.3 MB) is one fixed
+ * array in device memory that every GPU loading the library holds until the
+ * process exits. Limits: N^3 <= 262144 (N <= 64) and np <= 262144; larger
+ * sizes return PMR_EINVAL. The first call on a device looks up the array's
+ * device address (with that device current), so make that first call before
+ * any stream capture. All calls share the one array, whose contents are left
+ * from the previous call: calls whose work overlaps on the GPU (different
+ * streams, or the same stream from several host threads without ordering)
+ * race and must be serialised by the caller.
+ * x: float32 [3][np] absolute positions (same wrap rule as pmr_cell_sort);
+ * mass: float32[np] or NULL for unit mass; rho: float32 [N][N][N] output;
+ * stream: cudaStream_t or NULL. Errors: PMR_EINVAL, PMR_ECUDA (message from
+ * pmr_last_error(NULL)). */
+int pmr_paint_noalloc(int N, const float* x, int64_t np, const float* mass, float* rho, void* stream);
+
 /* CIC interpolation of a mesh at np positions (the transpose of paint). */
 int pmr_readout(pmr_ctx* ctx, const float* field, const float* x, int64_t np, float* out);
 

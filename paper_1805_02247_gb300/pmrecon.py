@@ -60,6 +60,7 @@ _SIGS = {
     "pmr_lbfgs_reset": (ctypes.c_int, [_P]),
     "pmr_cell_sort": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "pmr_paint": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "pmr_paint_noalloc": (ctypes.c_int, [ctypes.c_int, _P, _I64, _P, _P, _P]),
     "pmr_readout": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
     "pmr_readout_grad": (ctypes.c_int, [_P, _P, _P, _I64, _P]),
     "pmr_rfft": (ctypes.c_int, [_P, _P, _P]),
