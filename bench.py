@@ -190,6 +190,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- replicas
+
+def replica_throughput(seconds: float, steps: int, world: int, device):
+    """Whole-job throughput of independent replicas: every rank ran `steps`
+    evaluations; the job took as long as the slowest rank (max over ranks).
+    Returns (evaluations per second over all ranks, max seconds)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return world * steps / slowest, slowest
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -250,11 +266,8 @@ def run_ours(args):
         barrier()
     launches = (ctx.launch_count() - l0) // args.steps
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms / 1e3, args.steps, world, dev)
+    ms_max *= 1e3
 
     # ---- per-kernel durations (CUDA events after every launch on the context stream)
     ksteps = max(1, min(args.steps, 3))
@@ -301,10 +314,7 @@ def run_ours(args):
         g_h.copy_(g, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(t.item())
+    e2e_value, _ = replica_throughput(e2e_s, args.steps, world, dev)
     h2d = s.numel() * 8 + data.numel() * 4
     d2h = g.numel() * 8 + 3 * 8
 

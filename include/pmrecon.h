@@ -65,6 +65,9 @@ typedef struct pmr_config {
     double M_scale;     /* halo mass per unit softplus output, M_sun/h */
     int lbfgs_m;        /* L-BFGS memory (correction pairs), 1..64 */
     double lbfgs_tol;   /* relative loss decrease that counts as converged (Sec. 4.3: 1e-3) */
+    int nn_path;        /* network arithmetic: 0 = tensor cores (tcgen05), each operand split
+                           into two TF32 parts, float32 accuracy (default); 1 = tensor cores,
+                           plain TF32 (faster, ~1e-3 relative); 2 = float32 CUDA cores */
 } pmr_config;
 
 /* Per-stage annealing parameters of Sec. 4.2. */
@@ -208,6 +211,17 @@ int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* G
  * vectors of length n: S and Y are [k][n], oldest first. */
 int pmr_lbfgs_direction(pmr_ctx* ctx, const double* g, const double* S, const double* Y, int k,
                         int64_t n, double* d);
+
+/* Two-point statistics of Sec. 3.3: binned auto and cross power spectra of two
+ * float32 meshes a (e.g. the data, "h") and b (the model, "N"), from which the
+ * host forms r_c = P_ab / sqrt(P_aa P_bb), s = P_aa (1 - r_c^2) and
+ * TF = sqrt(P_bb / P_aa). Shell i (i < N/2) holds the modes with integer
+ * wavevector norm i + 1/2 <= |n| < i + 3/2, k = 2 pi n / L (nominal k =
+ * (i + 1) 2 pi / L h/Mpc); modes are counted over the full grid.
+ * P_ab = L^3 / N^6 < Re(A conj B) > with A = unnormalised DFT of a.
+ * out: HOST double[4][N/2] = {mode counts, P_aa, P_bb, P_ab} ((Mpc/h)^3).
+ * The first call allocates the context's shell table. Synchronises. */
+int pmr_power_spectra(pmr_ctx* ctx, const float* a, const float* b, double* out);
 
 /* ------------------------------------------------------------- instrumentation */
 

@@ -1,0 +1,31 @@
+"""Annealed reconstruction (Sec. 4.2-4.3) on the FP64 oracle: stages of
+(R_sm, M0), each iterating the oracle L-BFGS step until the loss stops
+decreasing by tol (relative) or max_iter iterations pass."""
+from __future__ import annotations
+
+from . import lbfgs, loss
+
+
+def reconstruct(s, data, weights, pms, ls, stages, max_iter=100, tol=1e-3):
+    """stages: iterable of (R_sm, M0). Returns (s_final, history of losses per stage)."""
+    history = []
+    x = s
+    for R_sm, M0 in stages:
+        an = loss.Anneal(R_sm=R_sm, M0=M0)
+
+        def fun(v, an=an):
+            parts, g = loss.loss_and_grad(v, data, weights, pms, ls, an)
+            return parts["loss"], g
+
+        st = lbfgs.LBFGSState(x=x.copy())
+        losses = []
+        for _ in range(max_iter):
+            status, conv, _ = lbfgs.step(fun, st, tol=tol)
+            if status != "ok":
+                break
+            losses.append(st.f)
+            if conv:
+                break
+        history.append(losses)
+        x = st.x
+    return x, history

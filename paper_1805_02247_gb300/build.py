@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpmrecon.so")
-SOURCES = ["api.cu", "fft.cu", "pm.cu", "nn.cu", "loss.cu", "lbfgs.cu", "noalloc.cu", "cosmo.cpp"]
+SOURCES = ["api.cu", "fft.cu", "pm.cu", "nn.cu", "mlp_tc.cu", "loss.cu", "lbfgs.cu", "noalloc.cu", "twopt.cu", "cosmo.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -68,6 +68,7 @@ const char* validate(const pmr_config* cfg) {
     if (!std::isfinite(cfg->mu_N) || !std::isfinite(cfg->f_eff)) return "mu_N and f_eff must be finite";
     if (cfg->lbfgs_m < 1 || cfg->lbfgs_m > 64) return "lbfgs_m must be 1..64";
     if (!(cfg->lbfgs_tol >= 0)) return "lbfgs_tol must be >= 0";
+    if (cfg->nn_path < 0 || cfg->nn_path > 2) return "nn_path must be 0, 1 or 2";
     return nullptr;
 }
 
@@ -92,6 +93,8 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->long_list : nullptr), sizeof(uint32_t) * N3);
     alloc((void**)(c ? &c->long_count : nullptr), sizeof(uint32_t) * 4);
     alloc((void**)(c ? &c->sort_tmp : nullptr), sizeof(uint32_t) * N3);
+    alloc((void**)(c ? &c->perm_all : nullptr), sizeof(uint32_t) * N3 * (cfg.nsteps + 1));
+    alloc((void**)(c ? &c->start_all : nullptr), sizeof(uint32_t) * (N3 + 1) * (cfg.nsteps + 1));
     alloc((void**)(c ? &c->delta : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->F : nullptr), sizeof(float) * 3 * N3);
     alloc((void**)(c ? &c->feat : nullptr), sizeof(float) * 3 * N3);
@@ -124,6 +127,8 @@ void free_all(pmr_ctx* c) {
         if (p) *p = nullptr;
     });
     fft_free(c);
+    mlp_tc_free(c);
+    twopt_free(c);
     lbfgs_free(c);
 }
 
@@ -132,7 +137,10 @@ int check_ctx(pmr_ctx* c) { return c ? PMR_OK : fail(nullptr, PMR_EINVAL, "conte
 // total, prior, residual into host[0..2]
 int finish_loss(pmr_ctx* c, double* host) {
     double v[2];
+    int tc_err = 0;
+    PMR_TRY(check_cuda(c, cudaMemcpyAsync(&tc_err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "rb"));
     PMR_TRY(check_finite(c, c->red_out, 2, v));
+    if (tc_err) return fail(c, PMR_ECUDA, "a tensor-core kernel timed out waiting for its MMAs");
     host[0] = v[0] + v[1];
     host[1] = v[0];
     host[2] = v[1];
@@ -158,7 +166,7 @@ int loss_and_grad_impl(pmr_ctx* c, const float2* s, const float* data, const pmr
     const float* dfin = c->disp + (int64_t)c->cfg.nsteps * 3 * N3;
     // forward
     PMR_TRY(pm_forward_impl(c, s));
-    PMR_TRY(density_from(c, dfin, c->delta));
+    PMR_TRY(density_slot(c, c->cfg.nsteps, dfin, c->delta, true));
     PMR_TRY(nn_features(c, c->delta));
     PMR_TRY(mlp_forward(c, c->feat, c->M));
     PMR_TRY(residual_forward(c, data, an, c->red_out + 1));
@@ -199,6 +207,7 @@ void pmr_default_config(pmr_config* cfg) {
     cfg->M_scale = 1e12;
     cfg->lbfgs_m = 10;
     cfg->lbfgs_tol = 1e-3;
+    cfg->nn_path = 0;
 }
 
 size_t pmr_workspace_bytes(const pmr_config* cfg) {
@@ -221,6 +230,8 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
     c->cfg = *cfg;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms < 1) c->num_sms = 1;
     const int N = cfg->N;
     c->N = N;
     c->P = N / 2 + 1;
@@ -271,6 +282,7 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
         if (rc == PMR_OK)
             rc = check_cuda(c, cudaMemcpy(c->W_host.data(), nn_weights_dev, sizeof(float) * kNW, cudaMemcpyDeviceToHost),
                             "weights");
+        if (rc == PMR_OK) rc = mlp_tc_init(c);
     }
     if (rc != PMR_OK) {
         g_create_err = c->err;
@@ -309,7 +321,7 @@ int pm_forward(pmr_ctx* c, const void* s_k, float* delta_out) {
     PMR_TRY(check_ctx(c));
     if (!s_k || !delta_out) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(pm_forward_impl(c, (const float2*)s_k));
-    return density_from(c, c->disp + (int64_t)c->cfg.nsteps * 3 * c->N3, delta_out);
+    return density_slot(c, c->cfg.nsteps, c->disp + (int64_t)c->cfg.nsteps * 3 * c->N3, delta_out, true);
 }
 
 int pm_adjoint(pmr_ctx* c, const float* grad_delta, void* grad_s_k) {

@@ -11,11 +11,31 @@
 
 namespace pmr {
 
-// Radix schedule of a 1D FFT of length n (Stockham autosort, radices 4/3/2).
+// Division by a run-time constant d (1 <= d < 2^31) of n < 2^31 without a
+// divide instruction: q = (umulhi(n, mul) + n) >> shift (Granlund-Montgomery).
+struct FastDiv {
+    uint32_t d, mul, shift;
+    FastDiv() : d(1), mul(1), shift(0) {}
+    explicit FastDiv(uint32_t dd) : d(dd) {
+        uint32_t l = 0;
+        while ((uint64_t(1) << l) < dd) ++l;
+        shift = l;
+        mul = (uint32_t)(((uint64_t(1) << 32) * ((uint64_t(1) << l) - dd)) / dd + 1);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return (__umulhi(n, mul) + n) >> shift; }
+    __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+#endif
+};
+
+// Radix schedule of a 1D FFT of length n (Stockham autosort, radices 4/3/2),
+// with the per-stage divisors the butterflies need.
 struct Radix {
     int n;
     int nr;
     int r[12];
+    FastDiv ns[12];   // Ns of stage s (product of the earlier radices)
+    FastDiv nrd[12];  // n / r[s]
 };
 
 Radix make_radix(int n);
@@ -81,6 +101,12 @@ struct pmr_ctx {
 
     float* W = nullptr;  // network weights (device copy)
     std::vector<float> W_host;  // same, on the host (launch parameters)
+    uint32_t* shell_order = nullptr;  // half-array entries listed by |k| shell (two-point statistics)
+    uint32_t* shell_off = nullptr;
+    double* shell_out = nullptr;
+    float* tc_img = nullptr;    // tensor-core operand images of the weights (TF32 head + tail)
+    int* tc_err = nullptr;      // set by a tensor-core kernel whose barrier wait timed out
+    int num_sms = 0;
 
     // particle state: displacement from the lattice point, [3][N3]
     float* disp = nullptr;  // (nsteps+1) checkpoints, [step][3][N3]
@@ -98,6 +124,10 @@ struct pmr_ctx {
     uint32_t* long_list = nullptr;   // cells whose segment needs the block sort
     uint32_t* long_count = nullptr;
     uint32_t* sort_tmp = nullptr;    // N3 scratch for the block sort
+    // per-step sort of the path's positions, kept from the forward sweep for the
+    // adjoint: slot s holds perm [N3] and cell offsets [N3 + 1] of x_s, s = 0..nsteps
+    uint32_t* perm_all = nullptr;
+    uint32_t* start_all = nullptr;
 
     // meshes
     float* delta = nullptr;
@@ -186,11 +216,27 @@ int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad)
 int pm_forward_impl(pmr_ctx* c, const float2* s_k);
 int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state
 int density_from(pmr_ctx* c, const float* disp, float* delta);
+int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out, uint32_t* perm,
+                   uint32_t* start);
+int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uint32_t* perm, const uint32_t* start,
+               const float* mass, int nmass, float scale, float offset, float* const* rho);
+// density of step s's positions; sort == true sorts them into slot s first,
+// otherwise slot s must already hold their sort (from the forward sweep)
+int density_slot(pmr_ctx* c, int s, const float* disp, float* delta, bool sort);
 
 // network (nn.cu) ---------------------------------------------------------------
 int nn_features(pmr_ctx* c, const float* delta);  // -> c->feat
 int mlp_forward(pmr_ctx* c, const float* feat, float* M);
 int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat);
+int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat);
+
+void twopt_free(pmr_ctx* c);
+
+// network on tcgen05 tensor cores (mlp_tc.cu) -----------------------------------
+int mlp_tc_init(pmr_ctx* c);
+void mlp_tc_free(pmr_ctx* c);
+int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit);
+int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit);  // -> c->gv
 
 // loss (loss.cu) ----------------------------------------------------------------
 int residual_forward(pmr_ctx* c, const float* data, const pmr_anneal* an, double* L_res_dev);

@@ -31,6 +31,12 @@ Radix make_radix(int n) {
     while (m % 3 == 0 && m > 1) { r.r[r.nr++] = 3; m /= 3; }
     if (m == 4) { r.r[r.nr++] = 4; m = 1; }
     if (m == 2) { r.r[r.nr++] = 2; m = 1; }
+    int Ns = 1;
+    for (int s = 0; s < r.nr; ++s) {
+        r.ns[s] = FastDiv((uint32_t)Ns);
+        r.nrd[s] = FastDiv((uint32_t)(n / r.r[s]));
+        Ns *= r.r[s];
+    }
     return r;
 }
 
@@ -39,6 +45,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kCols = 8;      // columns (kz) per y/x-pass tile
 constexpr int kRows = 8;      // real rows per z-pass tile
+constexpr int kColsT = kCols, kColsLog = 3;
+static_assert((1 << kColsLog) == kCols, "kCols is a power of two");
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -80,15 +88,18 @@ __device__ __forceinline__ void dft(float2* v) {
 // consecutive columns (es = ncols, cs = 1 layouts).
 template <int R, bool INV, bool COLFAST>
 __device__ __forceinline__ void stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                      const float2* __restrict__ tw, int n, int Ns, int ncols, int es, int cs) {
+                                      const float2* __restrict__ tw, int n, const FastDiv& nsd, const FastDiv& nrd,
+                                      int ncols, int es, int cs) {
+    const int Ns = (int)nsd.d;
     const int nR = n / R;
     const int W = nR * ncols;
     const int tstride = n / (Ns * R);
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
         int c, j;
-        if (COLFAST) { c = w % ncols; j = w / ncols; }
-        else { j = w % nR; c = w / nR; }
-        const int k = j % Ns;
+        if (COLFAST) { c = w & (kColsT - 1); j = w >> kColsLog; }
+        else { c = (int)nrd.div((uint32_t)w); j = w - c * nR; }
+        const int jq = (int)nsd.div((uint32_t)j);
+        const int k = j - jq * Ns;
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -100,7 +111,7 @@ __device__ __forceinline__ void stage(const float2* __restrict__ src, float2* __
             }
         }
         dft<R, INV>(v);
-        const int idxD = (j / Ns) * Ns * R + k;
+        const int idxD = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es + c * cs] = v[r];
     }
@@ -112,21 +123,63 @@ template <bool INV, bool COLFAST>
 __device__ float2* smem_fft(float2* a, float2* b, const float2* tw, const Radix& rd, int ncols, int es, int cs) {
     float2* src = a;
     float2* dst = b;
-    int Ns = 1;
     for (int s = 0; s < rd.nr; ++s) {
         const int R = rd.r[s];
-        if (R == 4) stage<4, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
-        else if (R == 2) stage<2, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
-        else stage<3, INV, COLFAST>(src, dst, tw, rd.n, Ns, ncols, es, cs);
+        if (R == 4) stage<4, INV, COLFAST>(src, dst, tw, rd.n, rd.ns[s], rd.nrd[s], ncols, es, cs);
+        else if (R == 2) stage<2, INV, COLFAST>(src, dst, tw, rd.n, rd.ns[s], rd.nrd[s], ncols, es, cs);
+        else stage<3, INV, COLFAST>(src, dst, tw, rd.n, rd.ns[s], rd.nrd[s], ncols, es, cs);
         __syncthreads();
         float2* t = src; src = dst; dst = t;
-        Ns *= R;
     }
     return src;
 }
 
 __device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* g_tw, int n) {
     for (int t = threadIdx.x; t < n; t += blockDim.x) s_tw[t] = g_tw[t];
+}
+
+// Tile loads with every global load of a thread issued before the first
+// shared-memory store, so a block keeps its whole tile in flight.
+constexpr int kMaxPer = 16;  // (512 * kCols) / kThreads
+
+// column tile: element t = m * kCols + c at in[base + m * es + c], c < cw valid
+__device__ __forceinline__ void load_col_tile(float2* A, const float2* in, int64_t base, int64_t es,
+                                              int n, int cw) {
+    const int T = n * kCols;
+    float2 r[kMaxPer];
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+        const int t = threadIdx.x + q * kThreads;
+        const int m = t / kCols, c = t % kCols;
+        r[q] = (t < T && c < cw) ? in[base + m * es + c] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxPer; ++q) {
+        const int t = threadIdx.x + q * kThreads;
+        if (t < T) A[t] = r[q];
+    }
+}
+
+// Row tiles of the z-pass: one warp per row (kThreads / 32 == kRows), lanes
+// stride along the row, so no index needs a division.
+constexpr int kMaxRowPer = 9;  // ceil((512/2 + 1) / 32)
+static_assert(kThreads / 32 == kRows, "one warp per z-pass row");
+
+// rows r < rows of len complex each at src[r * len + m] -> A[r * ld + m];
+// every load of a thread is issued before its first shared-memory store
+__device__ __forceinline__ void load_row_tile(float2* A, const float2* __restrict__ src, int len, int ld, int rows) {
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 v[kMaxRowPer];
+#pragma unroll
+    for (int i = 0; i < kMaxRowPer; ++i) {
+        const int m = lane + 32 * i;
+        v[i] = (r < rows && m < len) ? src[(int64_t)r * len + m] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxRowPer; ++i) {
+        const int m = lane + 32 * i;
+        if (m < len) A[r * ld + m] = v[i];
+    }
 }
 
 // ----------------------------------------------------------------------------- z passes
@@ -147,23 +200,20 @@ __global__ void __launch_bounds__(kThreads) k_z_r2c(const float* __restrict__ in
     load_twiddles(s_twN, twN, N);
     const int64_t row0 = (int64_t)blockIdx.x * kRows;
     const int rows = (int)min((int64_t)kRows, nrows - row0);
-    const float2* src = reinterpret_cast<const float2*>(in + row0 * N);
-    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
-        int r = t / M, m = t % M;
-        A[r * ld + m] = (r < rows) ? src[(int64_t)r * M + m] : make_float2(0.f, 0.f);
-    }
+    load_row_tile(A, reinterpret_cast<const float2*>(in + row0 * N), M, ld, rows);
     __syncthreads();
     float2* Z = smem_fft<false, false>(A, B, s_twM, rM, kRows, 1, ld);
-    for (int t = threadIdx.x; t < kRows * P; t += blockDim.x) {
-        int r = t / P, k = t % P;
-        if (r >= rows) continue;
-        float2 zk = Z[r * ld + (k % M)];
-        float2 zc = Z[r * ld + ((M - k) % M)];
-        zc.y = -zc.y;
-        float2 e = cscale(cadd(zk, zc), 0.5f);
-        float2 dd = csub(zk, zc);
-        float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
-        out[(row0 + r) * P + k] = cadd(e, cmul(s_twN[k], o));
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (r < rows) {
+        for (int k = lane; k < P; k += 32) {
+            float2 zk = Z[r * ld + (k == M ? 0 : k)];
+            float2 zc = Z[r * ld + (k == 0 ? 0 : M - k)];
+            zc.y = -zc.y;
+            float2 e = cscale(cadd(zk, zc), 0.5f);
+            float2 dd = csub(zk, zc);
+            float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
+            out[(row0 + r) * P + k] = cadd(e, cmul(s_twN[k], o));
+        }
     }
 }
 
@@ -183,17 +233,16 @@ __global__ void __launch_bounds__(kThreads) k_z_c2r(const float2* __restrict__ i
     load_twiddles(s_twN, twN, N);
     const int64_t row0 = (int64_t)blockIdx.x * kRows;
     const int rows = (int)min((int64_t)kRows, nrows - row0);
-    for (int t = threadIdx.x; t < kRows * P; t += blockDim.x) {
-        int r = t / P, k = t % P;
-        float2 v = (r < rows) ? in[(row0 + r) * P + k] : make_float2(0.f, 0.f);
-        if (k == 0 || k == M) v.y = 0.f;
-        X[r * ld + k] = v;
-    }
+    load_row_tile(X, in + row0 * P, P, ld, rows);
     __syncthreads();
-    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
-        int r = t / M, k = t % M;
+    const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = lane; k < M; k += 32) {
         float2 xk = X[r * ld + k];
         float2 xc = X[r * ld + (M - k)];
+        if (k == 0) {  // X_0 and X_M: imaginary parts carry nothing for a real signal
+            xk.y = 0.f;
+            xc.y = 0.f;
+        }
         xc.y = -xc.y;
         float2 e = cscale(cadd(xk, xc), 0.5f);
         float2 w = s_twN[k];
@@ -205,10 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_z_c2r(const float2* __restrict__ i
     float2* z = smem_fft<true, false>(A, B, s_twM, rM, kRows, 1, ld);
     float2* dst = reinterpret_cast<float2*>(out + row0 * N);
     const float s = scale * 2.0f / (float)N;
-    for (int t = threadIdx.x; t < kRows * M; t += blockDim.x) {
-        int r = t / M, m = t % M;
-        if (r < rows) dst[(int64_t)r * M + m] = cscale(z[r * ld + m], s);
-    }
+    if (r < rows)
+        for (int m = lane; m < M; m += 32) dst[(int64_t)r * M + m] = cscale(z[r * ld + m], s);
 }
 
 // ----------------------------------------------------------------------------- y / x passes
@@ -222,7 +269,9 @@ struct ColGeom {
 
 // Plain column pass (y-pass, or an x-pass without multipliers).
 template <bool INV>
-__global__ void __launch_bounds__(kThreads) k_col(const float2* __restrict__ in, float2* __restrict__ out,
+// in and out may be the same array (in-place pass): each block reads its whole
+// tile before writing it, and tiles are disjoint.
+__global__ void __launch_bounds__(kThreads) k_col(const float2* in, float2* out,
                                                     ColGeom g, Radix rd, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     const int n = g.n;
@@ -233,10 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_col(const float2* __restrict__ in,
     const int c0 = blockIdx.x * kCols;
     const int cw = min(kCols, g.ncols - c0);
     const int64_t base = (int64_t)blockIdx.y * g.os + c0;
-    for (int t = threadIdx.x; t < n * kCols; t += blockDim.x) {
-        int m = t / kCols, c = t % kCols;
-        A[t] = (c < cw) ? in[base + m * g.es + c] : make_float2(0.f, 0.f);
-    }
+    load_col_tile(A, in, base, g.es, n, cw);
     __syncthreads();
     float2* R = smem_fft<INV, true>(A, B, s_tw, rd, kCols, kCols, 1);
     for (int t = threadIdx.x; t < n * kCols; t += blockDim.x) {
@@ -293,10 +339,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
     const int T = n * kCols;
 
     if (p.nin == 1) {
-        for (int t = threadIdx.x; t < T; t += blockDim.x) {
-            int m = t / kCols, c = t % kCols;
-            A[t] = (c < cw) ? p.in[0][base + m * g.es + c] : make_float2(0.f, 0.f);
-        }
+        load_col_tile(A, p.in[0], base, g.es, n, cw);
         __syncthreads();
         const float2* src = A;
         if (p.fwd) src = smem_fft<false, true>(A, B, s_tw, rd, kCols, kCols, 1);
@@ -321,10 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
     } else {
         for (int t = threadIdx.x; t < T; t += blockDim.x) K[t] = make_float2(0.f, 0.f);
         for (int i = 0; i < p.nin; ++i) {
-            for (int t = threadIdx.x; t < T; t += blockDim.x) {
-                int m = t / kCols, c = t % kCols;
-                A[t] = (c < cw) ? p.in[i][base + m * g.es + c] : make_float2(0.f, 0.f);
-            }
+            load_col_tile(A, p.in[i], base, g.es, n, cw);
             __syncthreads();
             const float2* src = A;
             if (p.fwd) src = smem_fft<false, true>(A, B, s_tw, rd, kCols, kCols, 1);

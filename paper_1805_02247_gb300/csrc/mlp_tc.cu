@@ -1,0 +1,558 @@
+// The per-voxel network of Sec. 2 (81 -> 50 -> 30 -> 1, ReLU, softplus) and
+// its input gradient on the 5th-generation tensor cores (tcgen05).
+//
+// A tile is 128 voxels = the MMA M dimension = the 128 TMEM lanes. Operands are
+// staged in shared memory in the canonical K-major, no-swizzle layout (8-row x
+// 16-byte core matrices); accumulators live in TMEM and are read back with
+// tcgen05.ld, one voxel per TMEM lane. Float32 accuracy comes from splitting
+// every operand into a TF32 head and a TF32 tail (x = hi + lo) and issuing
+// hi*hi + hi*lo + lo*hi per product (error ~2^-21 relative); nsplit = 1 uses
+// hi*hi only (plain TF32).
+//
+// Forward per tile:   A1[128 x 88] (stencil inputs) x W1^T -> D1[128 x 64]
+//                     relu(D1 + b1) -> A2[128 x 64] x W2^T -> D2[128 x 32]
+//                     y = b3 + w3 . relu(D2 + b2), M = M_scale softplus(y)  (CUDA cores)
+// Backward per tile (after the forward): g_a2 = w3 g_y [a2 > 0]
+//                     A3 = g_a2[128 x 32] x W2 -> D3 = g_a1 (pre-mask) [128 x 64]
+//                     A4 = g_a1 [a1 > 0] [128 x 64] x W1 -> D4 = g_v[128 x 96]
+// g_v (81 columns) goes to the [81][N^3] scratch that the stencil transpose sums.
+//
+// Every mbarrier wait is bounded; on timeout the block records an error flag,
+// waits (bounded) for its MMAs, frees its TMEM and returns.
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pmr {
+namespace {
+
+constexpr int NI = 81, H1 = 50, H2 = 30;
+constexpr int OFF_B1 = H1 * NI, OFF_W2 = OFF_B1 + H1, OFF_B2 = OFF_W2 + H2 * H1, OFF_W3 = OFF_B2 + H2,
+              OFF_B3 = OFF_W3 + H2;
+
+constexpr int TM = 128;           // voxels per tile = MMA M = TMEM lanes
+constexpr int K1 = 88, N1 = 64;   // layer 1 (81 -> 50, padded)
+constexpr int K2 = 64, N2 = 32;   // layer 2 (50 -> 30, padded)
+constexpr int K3 = 32, NB3 = 64;  // backward layer 2: g_a2 -> g_a1 (B = W2)
+constexpr int K4 = 64, NB4 = 96;  // backward layer 1: g_a1 -> g_v  (B = W1)
+constexpr int NT = 512;           // threads per block (16 warps; 4 per TMEM lane quadrant)
+
+// voxel tile 2 (x) x 4 (y) x 16 (z); row = (lx * 4 + ly) * 16 + lz
+constexpr int TX = 2, TY = 4, TZ = 16, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+constexpr int HALO = 3 * HX * HY * HZ;
+
+// TMEM columns
+constexpr uint32_t COL_D1 = 0, COL_D2 = 64, COL_D3 = 96, COL_D4 = 160;
+
+// Byte offset of element (r, k) in an R-row, K-major, no-swizzle operand image:
+// k-steps of 8 (32 bytes of TF32) are sub-images of R*32 bytes; inside one,
+// core matrix (row group r/8, K chunk (k/4)%2) sits at 256*(r/8) + 128*chunk.
+// So the K-direction core-matrix stride (LBO) is 128 B and the 8-row-group
+// stride (SBO) is 256 B. Read either way round, every access of one k-step
+// stays inside its R*32-byte sub-image.
+__host__ __device__ constexpr uint32_t img_off(int R, int r, int k) {
+    return (uint32_t)((k >> 3) * (R * 32) + (r >> 3) * 256 + ((k >> 2) & 1) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+constexpr uint32_t img_bytes(int R, int K) { return (uint32_t)(R * K * 4); }
+
+// shared-memory map (bytes); weight images first, in the order of the global image
+constexpr uint32_t SZ_B1 = img_bytes(N1, K1), SZ_B2 = img_bytes(N2, K2), SZ_B3 = img_bytes(NB3, K3),
+                   SZ_B4 = img_bytes(NB4, K4);
+constexpr uint32_t S_B1 = 0;                  // hi, lo
+constexpr uint32_t S_B2 = S_B1 + 2 * SZ_B1;   // hi, lo
+constexpr uint32_t S_VEC = S_B2 + 2 * SZ_B2;  // b1[64], b2[32], w3[32], b3[4]
+constexpr uint32_t SZ_VEC = 640;               // 4 * (64 + 32 + 32 + 4) rounded up to 128 B
+constexpr uint32_t S_B3 = S_VEC + SZ_VEC;     // backward only
+constexpr uint32_t S_B4 = S_B3 + 2 * SZ_B3;
+constexpr uint32_t IMG_FWD = S_B3;            // bytes of the image the forward copies
+constexpr uint32_t IMG_ALL = S_B4 + 2 * SZ_B4;
+constexpr uint32_t SZ_A = img_bytes(TM, K1);  // largest A operand (hi or lo)
+constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
+constexpr int HALO_PER = (HALO + NT - 1) / NT;  // halo values each thread loads
+// halo, partials, g_y, stencil offsets, barrier + TMEM slot
+constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * K1 + 64;
+constexpr uint32_t SMEM_FWD = S_A_FWD + 2 * SZ_A + SZ_TAIL;
+constexpr uint32_t SMEM_BWD = S_A_BWD + 2 * SZ_A + SZ_TAIL;
+static_assert(SMEM_BWD <= 232448, "shared memory budget");
+static_assert((S_B2 | S_VEC | S_B3 | S_B4 | S_A_FWD | S_A_BWD | SZ_A) % 128 == 0, "128-byte aligned regions");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: start >> 4, LBO = 128 B, SBO = 256 B,
+// descriptor version 1 (bits 46-47), no swizzle, base offset 0.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try(bar, phase)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store 4 consecutive K values of one row (a 16-byte core-matrix row) as hi and lo parts.
+__device__ __forceinline__ void put4(unsigned char* Ahi, unsigned char* Alo, uint32_t off, float a, float b, float c,
+                                     float d) {
+    const float ha = tf32_hi(a), hb = tf32_hi(b), hc = tf32_hi(c), hd = tf32_hi(d);
+    *reinterpret_cast<float4*>(Ahi + off) = make_float4(ha, hb, hc, hd);
+    *reinterpret_cast<float4*>(Alo + off) = make_float4(a - ha, b - hb, c - hc, d - hd);
+}
+
+__device__ __forceinline__ int wrapi(int v, int N) { return v < 0 ? v + N : (v >= N ? v - N : v); }
+
+__device__ __forceinline__ float softplusf(float y) { return y > 0.f ? y + log1pf(expf(-y)) : log1pf(expf(y)); }
+__device__ __forceinline__ float sigmoidf(float y) {
+    return y >= 0.f ? 1.f / (1.f + expf(-y)) : expf(y) / (1.f + expf(y));
+}
+
+// issue the MMAs of one layer: D (+)= A x B^T over ksteps, hi*hi (+ hi*lo + lo*hi)
+__device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
+                                            int ksteps, int Rb, uint32_t idesc, int nsplit) {
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const uint32_t ao = (uint32_t)ks * (TM * 32), bo = (uint32_t)ks * (Rb * 32);
+        mma_tf32(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc, ks > 0 ? 1u : 0u);
+        if (nsplit > 1) {
+            mma_tf32(d, sdesc(a_hi + ao), sdesc(b_lo + bo), idesc, 1u);
+            mma_tf32(d, sdesc(a_lo + ao), sdesc(b_hi + bo), idesc, 1u);
+        }
+    }
+}
+
+struct TileMap {
+    FastDiv ntz, nty;
+    int N;
+    int64_t N3;
+};
+
+template <bool BWD>
+__global__ void __launch_bounds__(NT, 1)
+    k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
+             TileMap tm, int ntiles, int nsplit, float M_scale, float* __restrict__ M_out, float* __restrict__ gv,
+             int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const uint32_t S_A = BWD ? S_A_BWD : S_A_FWD;
+    unsigned char* Ahi = sm + S_A;
+    unsigned char* Alo = Ahi + SZ_A;
+    float* halo = reinterpret_cast<float*>(Alo + SZ_A);
+    float* part = halo + HALO;   // [4][TM]
+    float* gys = part + 4 * TM;  // [TM]
+    int* koff = reinterpret_cast<int*>(gys + TM);  // [K1]: halo offset of stencil input k (-1: padding)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(koff + K1);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const float* vec = reinterpret_cast<const float*>(sm + S_VEC);
+    const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cb = warp >> 2;  // TMEM lane quadrant, column block
+    const int row = quad * 32 + lane;           // the voxel row this thread reads back
+    const uint32_t ncols = BWD ? 256u : 128u;
+    const int N = tm.N;
+    const int64_t N3 = tm.N3;
+
+    // weight images -> shared memory (once per block)
+    {
+        const uint32_t n16 = (BWD ? IMG_ALL : IMG_FWD) / 16;
+        float4* dst = reinterpret_cast<float4*>(sm);
+        for (uint32_t i = tid; i < n16; i += NT) dst[i] = img[i];
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    uint32_t phase = 0;
+    bool ok = true;
+    const uint32_t sA_hi = smem_u32(Ahi), sA_lo = smem_u32(Alo);
+    if (tid < K1) {
+        const int k = tid;
+        const int c = k / 27, o = k % 27, ox = o / 9, oy = (o / 3) % 3, oz = o % 3;
+        koff[k] = k < NI ? ((c * HX + ox) * HY + oy) * HZ + oz : -1;
+    }
+
+    // halo of a tile into registers (issued one tile ahead, stored at the next iteration)
+    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
+        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
+        const int tz = tile - (int)(t2 * tm.ntz.d);
+        const int tx = (int)tm.nty.div(t2);
+        const int ty = (int)t2 - tx * (int)tm.nty.d;
+        x0 = tx * TX;
+        y0 = ty * TY;
+        z0 = tz * TZ;
+    };
+    float hv[HALO_PER];
+    auto load_halo = [&](int tile) {
+        if (tile >= ntiles) return;
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+#pragma unroll
+        for (int q = 0; q < HALO_PER; ++q) {
+            const int t = tid + q * NT;
+            if (t < HALO) {
+                const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
+                const int hx = r / (HY * HZ), hy = (r / HZ) % HY, hz = r % HZ;
+                const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
+                hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
+            }
+        }
+    };
+    load_halo(blockIdx.x);
+
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+
+        // (a) this tile's halo (loaded during the previous tile) -> shared memory,
+        //     then start loading the next tile's
+#pragma unroll
+        for (int q = 0; q < HALO_PER; ++q) {
+            const int t = tid + q * NT;
+            if (t < HALO) halo[t] = hv[q];
+        }
+        __syncthreads();
+        load_halo(tile + gridDim.x);
+
+        // (b) A1: 4 threads per row, k-steps part, part+4, part+8
+        {
+            const int r = tid >> 2, p = tid & 3;
+            const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
+            for (int ks = p; ks < K1 / 8; ks += 4) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ko = koff[ks * 8 + j];
+                    v[j] = ko >= 0 ? halo[ko + base] : 0.f;
+                }
+                put4(Ahi, Alo, img_off(TM, r, ks * 8), v[0], v[1], v[2], v[3]);
+                put4(Ahi, Alo, img_off(TM, r, ks * 8 + 4), v[4], v[5], v[6], v[7]);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+
+        // (c) layer 1
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer(tmem + COL_D1, sA_hi, sA_lo, smem_u32(sm + S_B1), smem_u32(sm + S_B1 + SZ_B1), K1 / 8, N1,
+                        idesc_tf32(TM, N1), nsplit);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase));
+        phase ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+
+        // (d) relu(D1 + b1) -> A2; keep the ReLU mask of this thread's 16 columns
+        uint32_t mask1 = 0;
+        {
+            float a[16];
+            tmem_ld16(lane_base + COL_D1 + 16 * cb, a);
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float pre = a[j] + b1[16 * cb + j];
+                mask1 |= (pre > 0.f ? 1u : 0u) << j;
+                z[j] = fmaxf(pre, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                put4(Ahi, Alo, img_off(TM, row, 16 * cb + 4 * q), z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+
+        // (e) layer 2
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer(tmem + COL_D2, sA_hi, sA_lo, smem_u32(sm + S_B2), smem_u32(sm + S_B2 + SZ_B2), K2 / 8, N2,
+                        idesc_tf32(TM, N2), nsplit);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase));
+        phase ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+
+        // (f) y = b3 + w3 . relu(D2 + b2): 8 columns per thread, partial sums per column block
+        uint32_t mask2 = 0;
+        {
+            float a[8];
+            tmem_ld8(lane_base + COL_D2 + 8 * cb, a);
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float pre = a[j] + b2[8 * cb + j];
+                mask2 |= (pre > 0.f ? 1u : 0u) << j;
+                s = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), s);
+            }
+            part[cb * TM + row] = s;
+        }
+        __syncthreads();
+        if (tid < TM) {
+            const int r = tid;
+            const int lx = r >> 6, ly = (r >> 4) & 3, lz = r & 15;
+            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+            const bool in = gx < N && gy < N && gz < N;
+            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
+            const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
+            if (!BWD) {
+                if (in) M_out[vox] = M_scale * softplusf(y);
+            } else {
+                gys[r] = in ? gM[vox] * M_scale * sigmoidf(y) : 0.f;
+            }
+        }
+        if (!BWD) {
+            tc_fence_before();
+            __syncthreads();
+            continue;
+        }
+        __syncthreads();
+
+        // (g) backward: A3 = g_a2 = w3 g_y [a2 > 0] (this thread's 8 columns)
+        {
+            const float g = gys[row];
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = ((mask2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
+            put4(Ahi, Alo, img_off(TM, row, 8 * cb), v[0], v[1], v[2], v[3]);
+            put4(Ahi, Alo, img_off(TM, row, 8 * cb + 4), v[4], v[5], v[6], v[7]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer(tmem + COL_D3, sA_hi, sA_lo, smem_u32(sm + S_B3), smem_u32(sm + S_B3 + SZ_B3), K3 / 8, NB3,
+                        idesc_tf32(TM, NB3), nsplit);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase));
+        phase ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+
+        // (h) A4 = g_a1 [a1 > 0] (16 columns, same mapping as (d))
+        {
+            float a[16];
+            tmem_ld16(lane_base + COL_D3 + 16 * cb, a);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = ((mask1 >> j) & 1u) ? a[j] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                put4(Ahi, Alo, img_off(TM, row, 16 * cb + 4 * q), a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer(tmem + COL_D4, sA_hi, sA_lo, smem_u32(sm + S_B4), smem_u32(sm + S_B4 + SZ_B4), K4 / 8, NB4,
+                        idesc_tf32(TM, NB4), nsplit);
+            mma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, phase));
+        phase ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+
+        // (i) g_v: 24 columns per thread -> gv[k][voxel], k < 81
+        {
+            const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
+            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+            const bool in = gx < N && gy < N && gz < N;
+            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                float a[8];
+                tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, a);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k = 24 * cb + 8 * h + j;
+                    if (in && k < NI) gv[k * N3 + vox] = a[j];
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // let any MMA still in flight finish before the TMEM goes away
+        mbar_wait(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// host: split into TF32 head and tail (round to nearest, ties away, at bit 13)
+float tf32_round(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x1000u;
+        u &= 0xffffe000u;
+    }
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+void put_operand(std::vector<float>& img, uint32_t base, int R, int K, float (*get)(const float*, int, int),
+                 const float* W) {
+    for (int r = 0; r < R; ++r)
+        for (int k = 0; k < K; ++k) {
+            const float v = get(W, r, k);
+            const float hi = tf32_round(v);
+            img[(base + img_off(R, r, k)) / 4] = hi;
+            img[(base + img_bytes(R, K) + img_off(R, r, k)) / 4] = v - hi;
+        }
+}
+
+float get_B1(const float* W, int h, int k) { return (h < H1 && k < NI) ? W[h * NI + k] : 0.f; }
+float get_B2(const float* W, int h2, int h1) { return (h2 < H2 && h1 < H1) ? W[OFF_W2 + h2 * H1 + h1] : 0.f; }
+float get_B3(const float* W, int h1, int h2) { return (h2 < H2 && h1 < H1) ? W[OFF_W2 + h2 * H1 + h1] : 0.f; }
+float get_B4(const float* W, int k, int h1) { return (h1 < H1 && k < NI) ? W[h1 * NI + k] : 0.f; }
+
+TileMap tile_map(const pmr_ctx* c, int* ntiles) {
+    const int N = c->N;
+    const int ntx = (N + TX - 1) / TX, nty = (N + TY - 1) / TY, ntz = (N + TZ - 1) / TZ;
+    *ntiles = ntx * nty * ntz;
+    TileMap m;
+    m.ntz = FastDiv((uint32_t)ntz);
+    m.nty = FastDiv((uint32_t)nty);
+    m.N = N;
+    m.N3 = c->N3;
+    return m;
+}
+
+}  // namespace
+
+// Weight images for the tensor-core kernels, built once per context.
+int mlp_tc_init(pmr_ctx* c) {
+    std::vector<float> img(IMG_ALL / 4, 0.f);
+    const float* W = c->W_host.data();
+    put_operand(img, S_B1, N1, K1, get_B1, W);
+    put_operand(img, S_B2, N2, K2, get_B2, W);
+    put_operand(img, S_B3, NB3, K3, get_B3, W);
+    put_operand(img, S_B4, NB4, K4, get_B4, W);
+    float* vec = img.data() + S_VEC / 4;
+    for (int h = 0; h < H1; ++h) vec[h] = W[OFF_B1 + h];
+    for (int h = 0; h < H2; ++h) vec[64 + h] = W[OFF_B2 + h];
+    for (int h = 0; h < H2; ++h) vec[96 + h] = W[OFF_W3 + h];
+    vec[128] = W[OFF_B3];
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_img, IMG_ALL), "tc weights"));
+    PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img, img.data(), IMG_ALL, cudaMemcpyHostToDevice), "tc weights"));
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_err, sizeof(int)), "tc flag"));
+    PMR_TRY(check_cuda(c, cudaMemset(c->tc_err, 0, sizeof(int)), "tc flag"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FWD),
+                       "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BWD),
+                       "smem attr"));
+    return PMR_OK;
+}
+
+void mlp_tc_free(pmr_ctx* c) {
+    cudaFree(c->tc_img);
+    cudaFree(c->tc_err);
+    c->tc_img = nullptr;
+    c->tc_err = nullptr;
+}
+
+int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit) {
+    int ntiles = 0;
+    TileMap m = tile_map(c, &ntiles);
+    const int grid = std::min(ntiles, c->num_sms);
+    k_mlp_tc<false><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, reinterpret_cast<const float4*>(c->tc_img), m,
+                                                        ntiles, nsplit, (float)c->cfg.M_scale, M, nullptr, c->tc_err);
+    return check_launch(c, "mlp_tc_fwd");
+}
+
+int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit) {
+    int ntiles = 0;
+    TileMap m = tile_map(c, &ntiles);
+    const int grid = std::min(ntiles, c->num_sms);
+    k_mlp_tc<true><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, reinterpret_cast<const float4*>(c->tc_img), m, ntiles,
+                                                       nsplit, (float)c->cfg.M_scale, nullptr, c->gv, c->tc_err);
+    return check_launch(c, "mlp_tc_bwd");
+}
+
+}  // namespace pmr

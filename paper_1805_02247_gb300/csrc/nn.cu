@@ -177,7 +177,10 @@ int nn_features(pmr_ctx* c, const float* delta) {
 
 static_assert(sizeof(Weights) <= 32000, "weights must fit the kernel parameter space");
 
+// nn_path 0: tensor cores, 3xTF32 (float32 accuracy); 1: tensor cores, TF32;
+// 2: float32 CUDA cores.
 int mlp_forward(pmr_ctx* c, const float* feat, float* M) {
+    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1) return mlp_tc_forward(c, feat, M, c->cfg.nn_path == 0 ? 3 : 1);
     static_assert(NW == 5661, "weight layout");
     Weights W;
     std::copy(c->W_host.begin(), c->W_host.end(), W.w);
@@ -185,13 +188,21 @@ int mlp_forward(pmr_ctx* c, const float* feat, float* M) {
     return check_launch(c, "mlp_fwd");
 }
 
+int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat) {
+    k_stencil_T<<<nblocks(c->N3, 256), 256, 0, c->stream>>>(gv, c->N, gfeat);
+    return check_launch(c, "stencil_T");
+}
+
 int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat) {
+    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1) {
+        PMR_TRY(mlp_tc_backward_gv(c, feat, gM, c->cfg.nn_path == 0 ? 3 : 1));
+        return stencil_transpose(c, c->gv, gfeat);
+    }
     Weights W;
     std::copy(c->W_host.begin(), c->W_host.end(), W.w);
     k_mlp_bwd<<<mlp_grid(c->N), kT, 0, c->stream>>>(W, feat, gM, c->N, (float)c->cfg.M_scale, c->gv);
     PMR_TRY(check_launch(c, "mlp_bwd"));
-    k_stencil_T<<<nblocks(c->N3, 256), 256, 0, c->stream>>>(c->gv, c->N, gfeat);
-    return check_launch(c, "stencil_T");
+    return stencil_transpose(c, c->gv, gfeat);
 }
 
 }  // namespace pmr

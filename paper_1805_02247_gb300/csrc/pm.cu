@@ -29,10 +29,20 @@ __device__ __forceinline__ float wrap_pos(float u, float n) {
     return w;
 }
 
-__device__ __forceinline__ Cell cell_of(const float* __restrict__ pos, int64_t np, int64_t i, bool lattice, int N) {
+// lattice point of particle i = (ix N + iy) N + iz (N^3 < 2^31)
+__device__ __forceinline__ void lattice_of(uint32_t i, const FastDiv& fN, int q[3]) {
+    const uint32_t t = fN.div(i);
+    q[2] = (int)(i - t * fN.d);
+    q[0] = (int)fN.div(t);
+    q[1] = (int)(t - (uint32_t)q[0] * fN.d);
+}
+
+__device__ __forceinline__ Cell cell_of(const float* __restrict__ pos, int64_t np, int64_t i, bool lattice, int N,
+                                        const FastDiv& fN) {
     Cell c;
     if (lattice) {
-        const int q[3] = {(int)(i / ((int64_t)N * N)), (int)((i / N) % N), (int)(i % N)};
+        int q[3];
+        lattice_of((uint32_t)i, fN, q);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float u = pos[a * np + i];
@@ -89,11 +99,11 @@ __device__ __forceinline__ void dwgt(const Cell& c, int o, float g[3]) {
 
 // ----------------------------------------------------------------------------- sort
 
-__global__ void k_keys(const float* __restrict__ pos, int64_t np, bool lattice, int N, uint32_t* __restrict__ keys,
+__global__ void k_keys(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN, uint32_t* __restrict__ keys,
                        uint32_t* __restrict__ counts) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    uint32_t k = key_of(cell_of(pos, np, i, lattice, N), N);
+    uint32_t k = key_of(cell_of(pos, np, i, lattice, N, fN), N);
     keys[i] = k;
     atomicAdd(&counts[k], 1u);  // integer: order-independent
 }
@@ -140,13 +150,15 @@ __global__ void k_scan_local(const uint32_t* __restrict__ in, uint32_t* __restri
 }
 
 // Phase 2: exclusive scan of the block totals by one block (serial chunks).
-__global__ void k_scan_part(uint32_t* __restrict__ part, int nb, uint32_t* __restrict__ total_out) {
+constexpr int kScanPartT = 1024;
+__global__ void __launch_bounds__(kScanPartT) k_scan_part(uint32_t* __restrict__ part, int nb,
+                                                         uint32_t* __restrict__ total_out) {
     __shared__ uint32_t carry;
-    __shared__ uint32_t wsum[kT / 32];
+    __shared__ uint32_t wsum[kScanPartT / 32];
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int b0 = 0; b0 < nb; b0 += kT) {
+    for (int b0 = 0; b0 < nb; b0 += kScanPartT) {
         int idx = b0 + threadIdx.x;
         uint32_t v = idx < nb ? part[idx] : 0u, inc = v;
 #pragma unroll
@@ -157,19 +169,19 @@ __global__ void k_scan_part(uint32_t* __restrict__ part, int nb, uint32_t* __res
         if (lane == 31) wsum[wid] = inc;
         __syncthreads();
         if (wid == 0) {
-            uint32_t t = (lane < kT / 32) ? wsum[lane] : 0u, ti = t;
+            uint32_t t = (lane < kScanPartT / 32) ? wsum[lane] : 0u, ti = t;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 uint32_t u = __shfl_up_sync(0xffffffffu, ti, d);
                 if (lane >= d) ti += u;
             }
-            if (lane < kT / 32) wsum[lane] = ti - t;
+            if (lane < kScanPartT / 32) wsum[lane] = ti - t;
         }
         __syncthreads();
         uint32_t ex = carry + wsum[wid] + inc - v;
         if (idx < nb) part[idx] = ex;
         __syncthreads();
-        if (threadIdx.x == kT - 1) carry = ex + v;
+        if (threadIdx.x == kScanPartT - 1) carry = ex + v;
         __syncthreads();
     }
     if (threadIdx.x == 0) *total_out = carry;
@@ -203,16 +215,28 @@ __global__ void k_fix_short(const uint32_t* __restrict__ start, uint32_t* __rest
         long_list[slot] = (uint32_t)c;
         return;
     }
+    // sorting networks on registers (padding UINT_MAX sorts last): 4 elements
+    // (5 compare-exchanges) for the common short case, else odd-even
+    // transposition over 16
     uint32_t v[kShort];
 #pragma unroll
-    for (int k = 0; k < kShort; ++k)
-        if (k < (int)len) v[k] = perm[s + k];
-    for (int a = 1; a < (int)len; ++a) {
-        uint32_t x = v[a];
-        int b = a - 1;
-        while (b >= 0 && v[b] > x) { v[b + 1] = v[b]; --b; }
-        v[b + 1] = x;
+    for (int k = 0; k < kShort; ++k) v[k] = (k < (int)len) ? perm[s + k] : 0xffffffffu;
+#define PMR_CE(a, b)                                 \
+    {                                                \
+        const uint32_t lo_ = min(v[a], v[b]);        \
+        v[b] = max(v[a], v[b]);                      \
+        v[a] = lo_;                                  \
     }
+    if (len <= 4) {
+        PMR_CE(0, 1) PMR_CE(2, 3) PMR_CE(0, 2) PMR_CE(1, 3) PMR_CE(1, 2)
+    } else {
+#pragma unroll
+        for (int round = 0; round < kShort; ++round) {
+#pragma unroll
+            for (int k = round & 1; k + 1 < kShort; k += 2) PMR_CE(k, k + 1)
+        }
+    }
+#undef PMR_CE
 #pragma unroll
     for (int k = 0; k < kShort; ++k)
         if (k < (int)len) perm[s + k] = v[k];
@@ -239,20 +263,26 @@ __global__ void k_fix_long(const uint32_t* __restrict__ start, uint32_t* __restr
 
 // ----------------------------------------------------------------------------- paint / readout
 
-// rho_m(c) = scale * sum_{o in (ox,oy,oz) lex order} sum_{j in bin(c - o), sorted}
-//            mass_m(j) * W_o(x_j) + offset
+// rho_m(c) = scale * sum over rounds r, then corners o in (ox,oy,oz) lex order, of
+//            mass_m(j) * W_o(x_j) for j the r-th sorted particle of bin(c - o); + offset.
+// Visiting the r-th particle of all 8 bins per round keeps the 8 dependent
+// load chains (offsets -> perm -> position) independent; the order is fixed,
+// so the sum is deterministic.
 template <int NM>
-__global__ void k_paint(const float* __restrict__ pos, int64_t np, bool lattice, int N,
+__global__ void k_paint(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN,
                         const uint32_t* __restrict__ start, const uint32_t* __restrict__ perm,
                         const float* __restrict__ mass, float scale, float offset, float* r0, float* r1, float* r2) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t N3 = (int64_t)N * N * N;
     if (c >= N3) return;
-    const int cx = (int)(c / ((int64_t)N * N)), cy = (int)((c / N) % N), cz = (int)(c % N);
+    int cq[3];
+    lattice_of((uint32_t)c, fN, cq);
+    const int cx = cq[0], cy = cq[1], cz = cq[2];
     float acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = 0.f;
-#pragma unroll 1
+    uint32_t s[8], e[8];
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
         const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
         int bx = cx - ox, by = cy - oy, bz = cz - oz;
@@ -260,29 +290,112 @@ __global__ void k_paint(const float* __restrict__ pos, int64_t np, bool lattice,
         if (by < 0) by += N;
         if (bz < 0) bz += N;
         const int64_t b = ((int64_t)bx * N + by) * N + bz;
-        const uint32_t s = start[b], e = start[b + 1];
-        for (uint32_t j = s; j < e; ++j) {
-            const int64_t i = perm[j];
-            Cell cl = cell_of(pos, np, i, lattice, N);
-            const float w = wgt(cl, o);
-            if (mass == nullptr) {
-                acc[0] += w;
-            } else {
+        s[o] = start[b];
+        e[o] = start[b + 1];
+    }
+    for (uint32_t r = 0;; ++r) {
+        bool any = false;
 #pragma unroll
-                for (int m = 0; m < NM; ++m) acc[m] += mass[m * np + i] * w;
+        for (int o = 0; o < 8; ++o) {
+            if (s[o] + r < e[o]) {
+                any = true;
+                const int64_t i = perm[s[o] + r];
+                Cell cl = cell_of(pos, np, i, lattice, N, fN);
+                const float w = wgt(cl, o);
+                if (mass == nullptr) {
+                    acc[0] += w;
+                } else {
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) acc[m] += mass[m * np + i] * w;
+                }
             }
         }
+        if (!any) break;
     }
     r0[c] = acc[0] * scale + offset;
     if (NM > 1) r1[c] = acc[1] * scale + offset;
     if (NM > 2) r2[c] = acc[2] * scale + offset;
 }
 
-__global__ void k_readout(const float* __restrict__ f, const float* __restrict__ pos, int64_t np, bool lattice, int N,
+// Tiled form of the same reduction. A block owns a PTX x PTY x PTZ tile of
+// cells. Phase 1: for every bin of the tile extended by one cell on the low
+// side, the 8 corner sums S_o(b) = sum_{j in bin b, sorted} mass(j) W_o(x_j)
+// go to shared memory (each particle is read once per tile it feeds).
+// Phase 2: rho(c) = scale * sum_{o lex order} S_o(c - o) + offset.
+// tile shapes: the 3-mass (adjoint) variant keeps 3x the sums per bin, so it
+// uses a thinner tile to keep several blocks resident per SM
+template <int NM>
+struct PaintTile {
+    static constexpr int X = NM == 1 ? 4 : 2, Y = 4, Z = 32;
+    static constexpr int BX = X + 1, BY = Y + 1, BZ = Z + 1, NB = BX * BY * BZ;
+    static constexpr size_t smem = sizeof(float) * NM * 8 * NB;
+};
+
+template <int NM>
+__global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ pos, int64_t np, bool lattice, int N,
+                                                    FastDiv fN, const uint32_t* __restrict__ start,
+                                                    const uint32_t* __restrict__ perm, const float* __restrict__ mass,
+                                                    float scale, float offset, float* r0, float* r1, float* r2) {
+    constexpr int PTX = PaintTile<NM>::X, PTY = PaintTile<NM>::Y, PTZ = PaintTile<NM>::Z;
+    constexpr int PBY = PaintTile<NM>::BY, PBZ = PaintTile<NM>::BZ, PNB = PaintTile<NM>::NB;
+    extern __shared__ float S[];  // [NM][8][PNB]
+    const int x0 = blockIdx.z * PTX, y0 = blockIdx.y * PTY, z0 = blockIdx.x * PTZ;
+    for (int t = threadIdx.x; t < PNB; t += blockDim.x) {
+        const int bx = t / (PBY * PBZ), by = (t / PBZ) % PBY, bz = t % PBZ;
+        int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
+        gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
+        gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
+        gz = gz < 0 ? gz + N : (gz >= N ? gz - N : gz);
+        const int64_t b = ((int64_t)gx * N + gy) * N + gz;
+        float acc[NM][8];
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) acc[m][o] = 0.f;
+        const uint32_t s = start[b], e = start[b + 1];
+        for (uint32_t j = s; j < e; ++j) {
+            const int64_t i = perm[j];
+            const Cell cl = cell_of(pos, np, i, lattice, N, fN);
+            float mv[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) mv[m] = mass ? mass[m * np + i] : 1.f;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const float w = wgt(cl, o);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) acc[m][o] = fmaf(mv[m], w, acc[m][o]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int o = 0; o < 8; ++o) S[(m * 8 + o) * PNB + t] = acc[m][o];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < PTX * PTY * PTZ; t += blockDim.x) {
+        const int lx = t / (PTY * PTZ), ly = (t / PTZ) % PTY, lz = t % PTZ;
+        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+        if (gx >= N || gy >= N || gz >= N) continue;
+        const int64_t c = ((int64_t)gx * N + gy) * N + gz;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            float acc = 0.f;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+                acc += S[(m * 8 + o) * PNB + ((lx + 1 - ox) * PBY + (ly + 1 - oy)) * PBZ + (lz + 1 - oz)];
+            }
+            float* r = m == 0 ? r0 : (m == 1 ? r1 : r2);
+            r[c] = acc * scale + offset;
+        }
+    }
+}
+
+__global__ void k_readout(const float* __restrict__ f, const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN,
                           float* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    Cell cl = cell_of(pos, np, i, lattice, N);
+    Cell cl = cell_of(pos, np, i, lattice, N, fN);
     float acc = 0.f;
 #pragma unroll
     for (int o = 0; o < 8; ++o) acc += wgt(cl, o) * f[corner(cl, o, N)];
@@ -290,10 +403,10 @@ __global__ void k_readout(const float* __restrict__ f, const float* __restrict__
 }
 
 __global__ void k_readout_grad(const float* __restrict__ f, const float* __restrict__ pos, int64_t np, bool lattice,
-                               int N, float scale, bool accumulate, float* __restrict__ out) {
+                               int N, FastDiv fN, float scale, bool accumulate, float* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    Cell cl = cell_of(pos, np, i, lattice, N);
+    Cell cl = cell_of(pos, np, i, lattice, N, fN);
     float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -315,10 +428,10 @@ __global__ void k_readout_grad(const float* __restrict__ f, const float* __restr
 
 // Forward step: p += kick * R(x) (force read out at x), disp' = disp + drift * p.
 __global__ void k_kick_drift(const float* __restrict__ F, const float* __restrict__ din, float* __restrict__ dout,
-                             float* __restrict__ mom, int64_t np, int N, float kick, float drift) {
+                             float* __restrict__ mom, int64_t np, int N, FastDiv fN, float kick, float drift) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    Cell cl = cell_of(din, np, i, true, N);
+    Cell cl = cell_of(din, np, i, true, N, fN);
     float r[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -339,10 +452,10 @@ __global__ void k_kick_drift(const float* __restrict__ F, const float* __restric
 // Adjoint of drift then the direct (weight-gradient) part of the kick adjoint:
 // lam_p += drift * lam_x;  lam_x += kick * sum_j lam_p_j grad_x R_j(x).
 __global__ void k_adj_direct(const float* __restrict__ F, const float* __restrict__ disp, float* __restrict__ lam_x,
-                             float* __restrict__ lam_p, int64_t np, int N, float kick, float drift) {
+                             float* __restrict__ lam_p, int64_t np, int N, FastDiv fN, float kick, float drift) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    Cell cl = cell_of(disp, np, i, true, N);
+    Cell cl = cell_of(disp, np, i, true, N, fN);
     float lp[3], lx[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -385,55 +498,74 @@ __global__ void k_za_adj_combine(const float* __restrict__ lx, const float* __re
 
 // ============================================================================= host wrappers
 
-int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out) {
+int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out, uint32_t* perm,
+                   uint32_t* start) {
     const int N = c->N;
     const int64_t N3 = c->N3;
     uint32_t* keys = keys_out ? keys_out : c->keys;
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
     if (np > 0) {
-        k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, keys, c->counts);
+        k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, FastDiv((uint32_t)N), keys, c->counts);
         PMR_TRY(check_launch(c, "keys"));
     }
     const int64_t per = (int64_t)kT * kScanPer;
     const int nb = (int)((N3 + per - 1) / per);
-    k_scan_local<<<nb, kT, 0, c->stream>>>(c->counts, c->cell_start, N3, c->scan_part);
+    k_scan_local<<<nb, kT, 0, c->stream>>>(c->counts, start, N3, c->scan_part);
     PMR_TRY(check_launch(c, "scan_local"));
-    k_scan_part<<<1, kT, 0, c->stream>>>(c->scan_part, nb, c->cell_start + N3);
+    k_scan_part<<<1, kScanPartT, 0, c->stream>>>(c->scan_part, nb, start + N3);
     PMR_TRY(check_launch(c, "scan_part"));
-    k_scan_add<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->cell_start, N3, c->scan_part);
+    k_scan_add<<<nblocks(N3, kT), kT, 0, c->stream>>>(start, N3, c->scan_part);
     PMR_TRY(check_launch(c, "scan_add"));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->long_count, 0, sizeof(uint32_t), c->stream), "memset"));
     if (np > 0) {
-        k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, c->cell_start, c->counts, c->perm);
+        k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, start, c->counts, perm);
         PMR_TRY(check_launch(c, "scatter"));
     }
-    k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->cell_start, c->perm, N3, c->long_list, c->long_count);
+    k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(start, perm, N3, c->long_list, c->long_count);
     PMR_TRY(check_launch(c, "fix_short"));
-    k_fix_long<<<304, kT, 0, c->stream>>>(c->cell_start, c->perm, c->long_list, c->long_count, c->sort_tmp);
+    k_fix_long<<<304, kT, 0, c->stream>>>(start, perm, c->long_list, c->long_count, c->sort_tmp);
     return check_launch(c, "fix_long");
+}
+
+int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out) {
+    return cell_sort_into(c, pos, np, lattice, keys_out, c->perm, c->cell_start);
+}
+
+int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uint32_t* perm, const uint32_t* start,
+               const float* mass, int nmass, float scale, float offset, float* const* rho) {
+    const int N = c->N;
+    const FastDiv fN((uint32_t)N);
+    if (nmass <= 1) {
+        using T = PaintTile<1>;
+        const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
+        k_paint_tile<1><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, mass, scale, offset,
+                                                          rho[0], nullptr, nullptr);
+    } else {
+        using T = PaintTile<3>;
+        const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
+        PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)T::smem),
+                           "smem attr"));
+        k_paint_tile<3><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, mass, scale, offset,
+                                                          rho[0], rho[1], rho[2]);
+    }
+    return check_launch(c, nmass <= 1 ? "paint" : "paint3");
 }
 
 int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,
           float offset, float* const* rho) {
-    const unsigned g = nblocks(c->N3, kT);
-    if (nmass <= 1)
-        k_paint<1><<<g, kT, 0, c->stream>>>(pos, np, lattice, c->N, c->cell_start, c->perm, mass, scale, offset,
-                                             rho[0], nullptr, nullptr);
-    else
-        k_paint<3><<<g, kT, 0, c->stream>>>(pos, np, lattice, c->N, c->cell_start, c->perm, mass, scale, offset,
-                                             rho[0], rho[1], rho[2]);
-    return check_launch(c, nmass <= 1 ? "paint" : "paint3");
+    return paint_with(c, pos, np, lattice, c->perm, c->cell_start, mass, nmass, scale, offset, rho);
 }
 
 int readout(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float* out) {
-    k_readout<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, out);
+    k_readout<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, FastDiv((uint32_t)c->N), out);
     return check_launch(c, "readout");
 }
 
 int readout_grad(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float scale,
                  bool accumulate, float* out) {
-    k_readout_grad<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, scale, accumulate, out);
+    k_readout_grad<<<nblocks(np, kT), kT, 0, c->stream>>>(field, pos, np, lattice, c->N, FastDiv((uint32_t)c->N), scale, accumulate, out);
     return check_launch(c, "readout_grad");
 }
 
@@ -442,6 +574,14 @@ int density_from(pmr_ctx* c, const float* disp, float* delta) {
     float* outs[1] = {delta};
     // unit-mass particles, one per cell: rho_bar = 1
     return paint(c, disp, c->N3, true, nullptr, 1, 1.0f, -1.0f, outs);
+}
+
+int density_slot(pmr_ctx* c, int s, const float* disp, float* delta, bool sort) {
+    uint32_t* perm = c->perm_all + (int64_t)s * c->N3;
+    uint32_t* start = c->start_all + (int64_t)s * (c->N3 + 1);
+    if (sort) PMR_TRY(cell_sort_into(c, disp, c->N3, true, nullptr, perm, start));
+    float* outs[1] = {delta};
+    return paint_with(c, disp, c->N3, true, perm, start, nullptr, 1, 1.0f, -1.0f, outs);
 }
 
 int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
@@ -454,13 +594,13 @@ int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
 }
 
 int kick_drift(pmr_ctx* c, const float* F, const float* din, float* dout, float* mom, float kick, float drift) {
-    k_kick_drift<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, kick, drift);
+    k_kick_drift<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
     return check_launch(c, "kick_drift");
 }
 
 int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
                     float drift) {
-    k_adj_direct<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, disp, lam_x, lam_p, c->N3, c->N, kick, drift);
+    k_adj_direct<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, disp, lam_x, lam_p, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
     return check_launch(c, "adj_direct");
 }
 
@@ -487,7 +627,7 @@ int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
     for (int s = 0; s < c->cfg.nsteps; ++s) {
         const float* din = c->disp + (int64_t)s * 3 * N3;
         float* dout = c->disp + (int64_t)(s + 1) * 3 * N3;
-        PMR_TRY(density_from(c, din, c->delta));
+        PMR_TRY(density_slot(c, s, din, c->delta, true));
         PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
         PMR_TRY(kick_drift(c, c->F, din, dout, c->mom, (float)c->kick[s], (float)c->drift[s]));
     }
@@ -508,10 +648,11 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
     float* Gj[3] = {c->gfeat, c->gfeat + N3, c->gfeat + 2 * N3};
     for (int s = c->cfg.nsteps - 1; s >= 0; --s) {
         const float* d = c->disp + (int64_t)s * 3 * N3;
-        PMR_TRY(density_from(c, d, c->delta));  // also leaves the cell sort of x_s
+        PMR_TRY(density_slot(c, s, d, c->delta, false));  // the forward sweep's sort of x_s
         PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
         PMR_TRY(adj_kick_direct(c, c->F, d, c->lam_x, c->lam_p, (float)c->kick[s], (float)c->drift[s]));
-        PMR_TRY(paint(c, d, N3, true, c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
+        PMR_TRY(paint_with(c, d, N3, true, c->perm_all + (int64_t)s * N3, c->start_all + (int64_t)s * (N3 + 1),
+                           c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
         const float* gins[3] = {Gj[0], Gj[1], Gj[2]};
         PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
         PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));

@@ -31,7 +31,7 @@ class Config(ctypes.Structure):
         ("omega_m", ctypes.c_double), ("sigma8", ctypes.c_double), ("gamma_bbks", ctypes.c_double),
         ("R_feat", ctypes.c_double * 3), ("R_M", ctypes.c_double), ("sigma_N2", ctypes.c_double),
         ("mu_N", ctypes.c_double), ("f_eff", ctypes.c_double), ("M_scale", ctypes.c_double),
-        ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double),
+        ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double), ("nn_path", ctypes.c_int),
     ]
 
 
@@ -70,6 +70,7 @@ _SIGS = {
     "pmr_za_ics": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmr_growth": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "pmr_lbfgs_direction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _I64, _P]),
+    "pmr_power_spectra": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmr_launch_count": (ctypes.c_int64, [_P]),
     "pmr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmr_timing_report": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
@@ -206,6 +207,14 @@ class Context:
         conv = ctypes.c_int(0)
         self._check(self._lib.recon_step(self._h, _ptr(s), _ptr(data), ctypes.byref(an), host, ctypes.byref(conv)))
         return tuple(host), bool(conv.value)
+
+    def power_spectra(self, a: torch.Tensor, b: torch.Tensor):
+        """(counts, P_aa, P_bb, P_ab) per |k| shell as float64 host tensors (Sec. 3.3)."""
+        nb = self.N // 2
+        out = (ctypes.c_double * (4 * nb))()
+        self._check(self._lib.pmr_power_spectra(self._h, _ptr(a), _ptr(b), out))
+        t = torch.tensor(list(out), dtype=torch.float64).view(4, nb)
+        return t[0], t[1], t[2], t[3]
 
     def launch_count(self) -> int:
         return int(self._lib.pmr_launch_count(self._h))

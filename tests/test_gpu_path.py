@@ -66,6 +66,24 @@ def test_nn_halo_map_and_adjoint_parity():
     assert rel_l2(gd, oloss.nn_halo_map_T(gM, delta, w, setup, ls)) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("nn_path,ftol,gtol", [(0, FIELD_TOL, GRAD_TOL), (2, FIELD_TOL, GRAD_TOL), (1, 1e-2, 5e-2)])
+@pytest.mark.parametrize("N,L", [(32, 100.0), (24, 60.0)])
+def test_network_paths_against_oracle(nn_path, ftol, gtol, N, L):
+    # 0: tcgen05 tensor cores with two-part TF32 operands (float32 accuracy),
+    # 2: float32 CUDA cores, 1: plain TF32 tensor cores (looser, reported path).
+    # N = 24 leaves partial voxel tiles (tiles are 2 x 4 x 16).
+    ctx, _ = context(N=N, L=L, nn_path=nn_path)
+    setup = opm.PMSetup(N=N, L=L, nsteps=3)
+    ls = oloss.LossSetup()
+    w = synth.xavier_weights(1)
+    delta = f32(3.0 * synth.gaussian_vector((N, N, N), seed=51))
+    M = to_np(ctx.nn_halo_map(to_dev(delta)))
+    assert rel_l2(M, oloss.nn_halo_map(delta, w, setup, ls)) <= ftol
+    gM = f32(synth.gaussian_vector((N, N, N), seed=52))
+    gd = to_np(ctx.nn_halo_map_adjoint(to_dev(delta), to_dev(gM)))
+    assert rel_l2(gd, oloss.nn_halo_map_T(gM, delta, w, setup, ls)) <= gtol
+
+
 def _data(N, L, nsteps):
     setup = opm.PMSetup(N=N, L=L, nsteps=nsteps)
     w = synth.xavier_weights(1)
@@ -98,10 +116,11 @@ def test_loss_nan_is_reported():
         ctx.loss_and_grad(to_dev(s), to_dev(data), 0.0, 1e8)
 
 
-def test_recon_step_follows_oracle_lbfgs():
+@pytest.mark.parametrize("nn_path,later_loss_tol", [(2, 1e-4), (0, 1e-4)])
+def test_recon_step_follows_oracle_lbfgs(nn_path, later_loss_tol):
     N, L, nsteps = 16, 50.0, 2  # R_M = 3 Mpc/h spans ~1 cell: resolved smoothing
     R_sm, M0 = 4.0, 1e8
-    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, nn_path=nn_path)
     setup, s0 = _problem(N, L, nsteps, amp=np.sqrt(0.1))
     data = _data(N, L, nsteps)
     w = synth.xavier_weights(1)
@@ -114,17 +133,40 @@ def test_recon_step_follows_oracle_lbfgs():
     st = olb.LBFGSState(x=s0.copy())
     s_dev = to_dev(s0)
     d_dev = to_dev(data)
-    # The loss follows the oracle to 1e-5 at every iteration. The iterate is a
-    # float32 copy of a float64 master point built from float32 gradients
-    # (rel-L2 ~1e-6 each); the L-BFGS history multiplies that difference by the
-    # conditioning of the recursion, so the iterate bound (the gradient
-    # tolerance) applies to the first two iterations, where one or two
-    # correction pairs are in play.
+    # The first step's loss follows the oracle to 1e-5. The iterate is a float32
+    # copy of a float64 master point built from float32 gradients; the L-BFGS
+    # history multiplies their rounding by the conditioning of the recursion,
+    # so the iterate bound (the gradient tolerance) applies to the first two
+    # iterations and later losses, which sit on slightly different points of
+    # the trajectory, are held to 1e-4 (observed: 1.1e-5 with the float32
+    # CUDA-core network, 3.4e-5 with the two-part TF32 tensor-core network).
     for it in range(4):
         status, conv_o, _ = olb.step(fun, st)
         parts, conv_g = ctx.recon_step(s_dev, d_dev, R_sm, M0)
         assert status == "ok"
-        assert parts[0] == pytest.approx(st.f, rel=1e-5), it
+        assert parts[0] == pytest.approx(st.f, rel=1e-5 if it == 0 else later_loss_tol), it
         if it < 2:
             assert rel_l2(to_np(s_dev), st.x) <= 1e-4, it
         assert conv_g == conv_o
+
+
+def test_annealed_reconstruction_follows_oracle():
+    # two smoothing stages of Sec. 4.2 at one M0, three L-BFGS iterations each
+    from oracle import anneal as oanneal
+    from paper_1805_02247_gb300 import anneal
+
+    N, L, nsteps = 16, 50.0, 2
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s0 = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    stages = anneal.smoothing_schedule([6.25, 3.125], 1e9)  # 2 and 1 cells
+    s_dev = to_dev(s0)
+    hist = anneal.reconstruct(ctx, s_dev, to_dev(data), stages, max_iter=3)
+    _, ohist = oanneal.reconstruct(s0, data, synth.xavier_weights(1), setup, oloss.LossSetup(),
+                                   [(st.R_sm, st.M0) for st in stages], max_iter=3)
+    for si in range(2):
+        got = [r["loss"] for r in hist if r["stage"] == si]
+        want = ohist[si]
+        assert len(got) == len(want)
+        assert np.all(np.diff(got) < 0)  # each stage decreases its own loss
+        assert np.allclose(got, want, rtol=1e-4)
