@@ -68,12 +68,18 @@ typedef struct pmr_config {
     int nn_path;        /* network arithmetic: 0 = tensor cores (tcgen05), each operand split
                            into two TF32 parts, float32 accuracy (default); 1 = tensor cores,
                            plain TF32 (faster, ~1e-3 relative); 2 = float32 CUDA cores */
+    int head;           /* 0 = one network with a softplus output, M = M_scale ln(1 + e^y);
+                           1 = the paper's two networks (Sec. 2.1), M = M_scale *
+                           logistic(y, a) * NNm(f), NNm = 3-20-10-1 ELU net on the voxel's
+                           three fields; its 301 weights follow the 5661 of pmr_create */
 } pmr_config;
 
 /* Per-stage annealing parameters of Sec. 4.2. */
 typedef struct pmr_anneal {
-    double R_sm; /* Gaussian smoothing of the residual, Mpc/h; 0 = none */
-    double M0;   /* nuisance mass added inside the log, M_sun/h (Eq. var) */
+    double R_sm;       /* Gaussian smoothing of the residual, Mpc/h; 0 = none */
+    double M0;         /* nuisance mass added inside the log, M_sun/h (Eq. var) */
+    double a_logistic; /* sharpness of the logistic position output (Eq. logistic;
+                          annealed 1, 2, 3); used when head == 1 */
 } pmr_anneal;
 
 typedef struct pmr_ctx pmr_ctx;
@@ -92,7 +98,9 @@ size_t pmr_workspace_bytes(const pmr_config* cfg);
  * (float64), and copies the network weights.
  * nn_weights_dev: device float32[5661] laid out W1[50][81], b1[50], W2[30][50],
  *   b2[30], w3[30], b3; input index c*27 + (ox+1)*9 + (oy+1)*3 + (oz+1) for
- *   field c and neighbour offset (ox,oy,oz) (Sec. 2.1-2.2). Copied.
+ *   field c and neighbour offset (ox,oy,oz) (Sec. 2.1-2.2); with head == 1,
+ *   float32[5962]: the same followed by the mass network's Wm1[20][3], bm1[20],
+ *   Wm2[10][20], bm2[10], wm3[10], bm3. Copied.
  * stream: a cudaStream_t (NULL = legacy default stream). */
 int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream, pmr_ctx** out);
 int pmr_destroy(pmr_ctx* ctx);
@@ -119,11 +127,13 @@ int pm_adjoint(pmr_ctx* ctx, const float* grad_delta, void* grad_s_k);
 
 /* Network halo-mass map (Sec. 2): delta -> three Gaussian-smoothed fields ->
  * per-voxel 81-50-30-1 ReLU network on the 3x3x3 neighbourhood -> M_scale *
- * softplus(y). delta, mass_out: float32 meshes. */
-int nn_halo_map(pmr_ctx* ctx, const float* delta, float* mass_out);
+ * softplus(y), or with head == 1 M_scale * logistic(y, a) * NNm (Sec. 2.1).
+ * an: only a_logistic is read (NULL means a = 3). delta, mass_out: float32 meshes. */
+int nn_halo_map(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, float* mass_out);
 
 /* Adjoint of nn_halo_map at delta: grad_delta = (dM/d delta)^T grad_mass. */
-int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const float* grad_mass, float* grad_delta);
+int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, const float* grad_mass,
+                        float* grad_delta);
 
 /* Loss of Eq. (loss) at s(k) and its gradient (Sec. 4.1-4.2).
  * data_mass: float32 mesh of the observed halo mass M^data (unsmoothed).
@@ -135,9 +145,11 @@ int loss_and_grad(pmr_ctx* ctx, const void* s_k, const float* data_mass, const p
 
 /* One L-BFGS iteration (Sec. 4.2) on s(k) in place: two-loop direction from the
  * context's history (float64 on the device), Armijo backtracking (step 1,
- * halved up to 20 times, c1 = 1e-4), history update. The first call after
- * pmr_lbfgs_reset() (or after the annealing parameters change) evaluates the
- * gradient at s first and searches along -g/|g|.
+ * halved up to 20 times, c1 = 1e-4), history update. The initial inverse
+ * Hessian is gamma D with D = P~(k)/w_k, the Gaussian prior's exact inverse
+ * Hessian, and gamma = s^T y / y^T D y of the newest pair. The first call after
+ * pmr_lbfgs_reset() (or after any annealing parameter changes) evaluates the
+ * gradient at s first and searches along -D g.
  * loss_out: HOST double[3] of the accepted point. converged: HOST int, set to 1
  * when (L_old - L_new) < lbfgs_tol * |L_old| (Sec. 4.3 stop rule). Synchronises. */
 int recon_step(pmr_ctx* ctx, void* s_k, const float* data_mass, const pmr_anneal* an,

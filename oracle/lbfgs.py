@@ -3,10 +3,16 @@
 The paper names L-BFGS and its stop rule (the loss per degree of freedom stops
 decreasing by 0.1% between iterations, Sec. 4.3) but not its memory, initial
 Hessian or line search. Readings:
-* memory m = 10 correction pairs; H0 = gamma I with gamma = s^T y / y^T y of the
-  newest pair; a pair is stored only if s^T y > 1e-10 |s| |y|;
-* first iteration (empty memory) searches along -g / |g|; a non-descent
-  direction clears the memory and falls back to the same;
+* memory m = 10 correction pairs; a pair is stored only if s^T y > 1e-10 |s| |y|;
+* initial inverse Hessian: for the reconstruction, a diagonal D = P~(k) / w_k,
+  the exact inverse Hessian of the Gaussian prior of Eq. (priorpdf) (zero at
+  k = 0), so the search runs in whitened variables. The first step is -D g;
+  later ones scale it as gamma D with gamma = s^T y / y^T D y of the newest pair
+  (the usual scaling of the initial matrix, Nocedal & Wright Sec. 7.2, with the
+  preconditioner D in place of I), which lets unit steps pass the line search
+  once the data term dominates the curvature. Without a diagonal, H0 = gamma I
+  with gamma = s^T y / y^T y and the first step is -g / |g|. A non-descent
+  direction clears the memory and falls back to the first step;
 * backtracking Armijo line search: step 1, halved up to 20 times, accepted when
   L(s + t d) <= L(s) + c1 t g.d with c1 = 1e-4; failure is an error;
 * converged when (L_old - L_new) / |L_old| < tol (tol = 1e-3).
@@ -28,8 +34,11 @@ def dot(a: np.ndarray, b: np.ndarray) -> float:
     return float(np.sum(a * b))
 
 
-def two_loop(g: np.ndarray, S: list, Y: list) -> np.ndarray:
-    """Direction d = -H g from the stored pairs (oldest first in S, Y)."""
+def two_loop(g: np.ndarray, S: list, Y: list, H0=None) -> np.ndarray:
+    """Direction d = -H g from the stored pairs (oldest first in S, Y).
+
+    H0: real diagonal D of the initial inverse Hessian (same shape as g), used
+    as gamma D, or None for gamma I."""
     q = g.copy()
     alphas = []
     for s, y in zip(reversed(S), reversed(Y)):
@@ -37,8 +46,10 @@ def two_loop(g: np.ndarray, S: list, Y: list) -> np.ndarray:
         a = rho * dot(s, q)
         q = q - a * y
         alphas.append((a, rho))
-    gamma = dot(S[-1], Y[-1]) / dot(Y[-1], Y[-1])
-    r = gamma * q
+    if H0 is None:
+        r = dot(S[-1], Y[-1]) / dot(Y[-1], Y[-1]) * q
+    else:
+        r = dot(S[-1], Y[-1]) / dot(Y[-1], H0 * Y[-1]) * (H0 * q)
     for (s, y), (a, rho) in zip(zip(S, Y), reversed(alphas)):
         b = rho * dot(y, r)
         r = r + (a - b) * s
@@ -54,7 +65,7 @@ class LBFGSState:
     Y: list = field(default_factory=list)
 
 
-def step(fun, st: LBFGSState, m: int = 10, c1: float = 1e-4, max_ls: int = 20, tol: float = 1e-3):
+def step(fun, st: LBFGSState, m: int = 10, c1: float = 1e-4, max_ls: int = 20, tol: float = 1e-3, H0=None):
     """One L-BFGS iteration. fun(x) -> (f, g). Returns (status, converged, n_evals)."""
     evals = 0
     if st.g is None:
@@ -62,12 +73,12 @@ def step(fun, st: LBFGSState, m: int = 10, c1: float = 1e-4, max_ls: int = 20, t
         evals += 1
     g = st.g
     if st.S:
-        d = two_loop(g, st.S, st.Y)
+        d = two_loop(g, st.S, st.Y, H0)
         gd = dot(g, d)
         if not gd < 0:
             st.S.clear(); st.Y.clear()
     if not st.S:
-        d = -g / np.sqrt(dot(g, g))
+        d = -g / np.sqrt(dot(g, g)) if H0 is None else -H0 * g
         gd = dot(g, d)
     t = 1.0
     for _ in range(max_ls):

@@ -34,12 +34,30 @@ class LossSetup:
     mu_N: float = 0.0
     f_eff: float = 1.0
     M_scale: float = 1e12  # M_sun/h per unit network output
+    head: str = "softplus"  # or "two_net": logistic(NNp, a) x NNm (Sec. 2.1)
 
 
 @dataclass(frozen=True)
 class Anneal:
     R_sm: float  # Mpc/h
     M0: float  # M_sun/h
+    a: float = 3.0  # logistic sharpness of the two-network head (annealed 1, 2, 3 in Sec. 4.2)
+
+
+def _head_forward(f, weights, ls: LossSetup, a: float):
+    if ls.head == "two_net":
+        w = np.asarray(weights)
+        return nn.two_net_forward(f, w[:nn.N_H1 * nn.N_IN + nn.N_H1 + nn.N_H2 * nn.N_H1 + 2 * nn.N_H2 + 1],
+                                  w[-nn.N_MASS_WEIGHTS:], ls.M_scale, a)
+    return nn.mlp_forward(f, weights, ls.M_scale)[0]
+
+
+def _head_backward(gM, f, weights, ls: LossSetup, a: float):
+    if ls.head == "two_net":
+        w = np.asarray(weights)
+        return nn.two_net_backward(gM, f, w[:nn.N_H1 * nn.N_IN + nn.N_H1 + nn.N_H2 * nn.N_H1 + 2 * nn.N_H2 + 1],
+                                   w[-nn.N_MASS_WEIGHTS:], ls.M_scale, a)
+    return nn.mlp_backward(gM, f, weights, ls.M_scale)
 
 
 def features(delta: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarray:
@@ -52,15 +70,15 @@ def features_T(g_fields: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarr
     return sum(pm.smooth(g_fields[c], R / cell) for c, R in enumerate(ls.R_feat))
 
 
-def nn_halo_map(delta: np.ndarray, weights: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarray:
+def nn_halo_map(delta: np.ndarray, weights: np.ndarray, pms: pm.PMSetup, ls: LossSetup, a: float = 3.0) -> np.ndarray:
     """Final overdensity -> network halo-mass field M_NN."""
-    M, _ = nn.mlp_forward(features(delta, pms, ls), weights, ls.M_scale)
-    return M
+    return _head_forward(features(delta, pms, ls), weights, ls, a)
 
 
-def nn_halo_map_T(g_M: np.ndarray, delta: np.ndarray, weights: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarray:
+def nn_halo_map_T(g_M: np.ndarray, delta: np.ndarray, weights: np.ndarray, pms: pm.PMSetup, ls: LossSetup,
+                  a: float = 3.0) -> np.ndarray:
     f = features(delta, pms, ls)
-    return features_T(nn.mlp_backward(g_M, f, weights, ls.M_scale), pms, ls)
+    return features_T(_head_backward(g_M, f, weights, ls, a), pms, ls)
 
 
 def prior(s: np.ndarray, P: np.ndarray) -> float:
@@ -68,6 +86,13 @@ def prior(s: np.ndarray, P: np.ndarray) -> float:
     w = pm.half_weights(N)
     mask = P > 0
     return 0.5 * float(np.sum((w * np.abs(s) ** 2)[mask] / P[mask]))
+
+
+def prior_inverse_hessian(pms: pm.PMSetup) -> np.ndarray:
+    """Diagonal of the prior's inverse Hessian over the half-array entries,
+    P~(k) / w_k (0 at k = 0): the initial L-BFGS inverse Hessian (lbfgs.py)."""
+    P = pm.power_half(pms)
+    return P / pm.half_weights(pms.N)
 
 
 def prior_grad(s: np.ndarray, P: np.ndarray) -> np.ndarray:
@@ -102,7 +127,7 @@ def residual_grad(cache, pms: pm.PMSetup, ls: LossSetup, an: Anneal) -> np.ndarr
 
 def loss(s, data_M, weights, pms: pm.PMSetup, ls: LossSetup, an: Anneal) -> dict:
     delta = pm.final_density(s, pms)
-    M_nn = nn_halo_map(delta, weights, pms, ls)
+    M_nn = nn_halo_map(delta, weights, pms, ls, an.a)
     L_res, _ = residual_terms(M_nn, data_M, pms, ls, an)
     L_pri = prior(s, pm.power_half(pms))
     return {"loss": L_pri + L_res, "prior": L_pri, "residual": L_res}
@@ -114,20 +139,20 @@ def loss_and_grad(s, data_M, weights, pms: pm.PMSetup, ls: LossSetup, an: Anneal
     x_fin, checkpoints, _ = pm.pm_forward(s, pms)
     delta = pm.density(x_fin, N)
     f = features(delta, pms, ls)
-    M_nn, _ = nn.mlp_forward(f, weights, ls.M_scale)
+    M_nn = _head_forward(f, weights, ls, an.a)
     L_res, cache = residual_terms(M_nn, data_M, pms, ls, an)
     P = pm.power_half(pms)
     L_pri = prior(s, P)
     g_M = residual_grad(cache, pms, ls, an)
-    g_delta = features_T(nn.mlp_backward(g_M, f, weights, ls.M_scale), pms, ls)
+    g_delta = features_T(_head_backward(g_M, f, weights, ls, an.a), pms, ls)
     g_s = pm.final_density_T(checkpoints, x_fin, g_delta, pms) + prior_grad(s, P)
     g_s[0, 0, 0] = 0
     return {"loss": L_pri + L_res, "prior": L_pri, "residual": L_res}, g_s
 
 
 def synthetic_data(white_true: np.ndarray, scatter: np.ndarray, weights, pms: pm.PMSetup, ls: LossSetup,
-                   sigma_ln: float = 0.3) -> np.ndarray:
+                   sigma_ln: float = 0.3, a: float = 3.0) -> np.ndarray:
     """Data mass field: the model on the true linear field times log-normal scatter exp(sigma g)."""
     s_true = pm.linear_field(white_true, pms)
-    M = nn_halo_map(pm.final_density(s_true, pms), weights, pms, ls)
+    M = nn_halo_map(pm.final_density(s_true, pms), weights, pms, ls, a)
     return M * np.exp(sigma_ln * np.asarray(scatter, np.float64))

@@ -77,6 +77,89 @@ def mlp_forward(fields: np.ndarray, weights: np.ndarray, M_scale: float):
     return M.reshape(N, N, N), (a1, a2, y)
 
 
+# ----------------------------------------------------------------------------- the paper's two-network head
+#
+# Sec. 2: model = NNp x NNm. NNp is the 81-50-30-1 ReLU trunk above with a
+# logistic output of sharpness a (Eq. logistic); NNm is a 3-20-10-1 network
+# with ELU hidden units (Eq. elu) and a linear output, fed with the three
+# fields at the voxel itself (Sec. 2.2). M = M_scale * logistic(y_p, a) * m.
+# Mass-net weights (flat, after the 5661 of NNp): Wm1[20][3], bm1[20],
+# Wm2[10][20], bm2[10], wm3[10], bm3.
+
+NM_IN, NM_H1, NM_H2 = 3, 20, 10
+N_MASS_WEIGHTS = NM_H1 * NM_IN + NM_H1 + NM_H2 * NM_H1 + NM_H2 + NM_H2 + 1
+
+
+def unpack_mass(w: np.ndarray):
+    w = np.asarray(w, np.float64)
+    o = 0
+    W1 = w[o:o + NM_H1 * NM_IN].reshape(NM_H1, NM_IN); o += NM_H1 * NM_IN
+    b1 = w[o:o + NM_H1]; o += NM_H1
+    W2 = w[o:o + NM_H2 * NM_H1].reshape(NM_H2, NM_H1); o += NM_H2 * NM_H1
+    b2 = w[o:o + NM_H2]; o += NM_H2
+    w3 = w[o:o + NM_H2]; o += NM_H2
+    b3 = w[o]; o += 1
+    assert o == w.size
+    return W1, b1, W2, b2, w3, b3
+
+
+def elu(x):
+    return np.where(x > 0, x, np.expm1(np.minimum(x, 0.0)))
+
+
+def elu_grad(x):
+    return np.where(x > 0, 1.0, np.exp(np.minimum(x, 0.0)))
+
+
+def logistic(x, a):
+    return expit(a * x)
+
+
+def _trunk_logit(fields, wp):
+    W1, b1, W2, b2, w3, b3 = unpack(wp)
+    v = stencil_gather(fields)
+    a1 = W1 @ v + b1[:, None]
+    a2 = W2 @ relu(a1) + b2[:, None]
+    return w3 @ relu(a2) + b3, (a1, a2)
+
+
+def _mass_net(fields, wm):
+    W1, b1, W2, b2, w3, b3 = unpack_mass(wm)
+    u = fields.reshape(3, -1)
+    h1 = W1 @ u + b1[:, None]
+    h2 = W2 @ elu(h1) + b2[:, None]
+    return w3 @ elu(h2) + b3, (u, h1, h2)
+
+
+def two_net_forward(fields, wp, wm, M_scale, a):
+    """M = M_scale * logistic(y_p, a) * NNm(fields at the voxel)."""
+    N = fields.shape[1]
+    y, _ = _trunk_logit(fields, wp)
+    m, _ = _mass_net(fields, wm)
+    return (M_scale * logistic(y, a) * m).reshape(N, N, N)
+
+
+def two_net_backward(gM, fields, wp, wm, M_scale, a):
+    N = fields.shape[1]
+    W1, b1, W2, b2, w3, b3 = unpack(wp)
+    y, (a1, a2) = _trunk_logit(fields, wp)
+    m, (u, h1, h2) = _mass_net(fields, wm)
+    p = logistic(y, a)
+    g = gM.ravel() * M_scale
+    # position net
+    gy = g * m * a * p * (1.0 - p)
+    ga2 = np.outer(w3, gy) * (a2 > 0)
+    ga1 = (W2.T @ ga2) * (a1 > 0)
+    out = stencil_gather_T(W1.T @ ga1, N)
+    # mass net, on the voxel's own three values
+    V1, c1, V2, c2, v3, c3 = unpack_mass(wm)
+    gm = g * p
+    gh2 = np.outer(v3, gm) * elu_grad(h2)
+    gh1 = (V2.T @ gh2) * elu_grad(h1)
+    out += (V1.T @ gh1).reshape(3, N, N, N)
+    return out
+
+
 def mlp_backward(gM: np.ndarray, fields: np.ndarray, weights: np.ndarray, M_scale: float) -> np.ndarray:
     """Gradient of <gM, M(fields)> w.r.t. the three input fields."""
     N = fields.shape[1]

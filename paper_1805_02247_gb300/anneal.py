@@ -17,8 +17,9 @@ from .pmrecon import Context, PMRError
 
 @dataclass(frozen=True)
 class Stage:
-    R_sm: float  # residual smoothing, Mpc/h
-    M0: float    # M_sun/h
+    R_sm: float     # residual smoothing, Mpc/h
+    M0: float       # M_sun/h
+    a: float = 3.0  # logistic sharpness of the two-network head (unused by the single-network head)
 
 
 def paper_schedule(cell: float) -> list[Stage]:
@@ -26,6 +27,17 @@ def paper_schedule(cell: float) -> list[Stage]:
     M0 = 1e12 with N_sm = 4, 2, 1, 0.5, 0 cells, then M0 = 1e11 with N_sm = 1, 0.5, 0."""
     stages = [Stage(n * cell, 1e12) for n in (4, 2, 1, 0.5, 0)]
     stages += [Stage(n * cell, 1e11) for n in (1, 0.5, 0)]
+    return stages
+
+
+def two_network_schedule(cell: float) -> list[Stage]:
+    """Sec. 4.3 with the two-network head: the logistic sharpness steps through
+    a = 1, 2, 3; at each a the smoothing runs N_sm = 4, 2, 1, 0.5, 0 cells with
+    M0 = 1e12, and the last a finishes with M0 = 1e11 at N_sm = 1, 0.5, 0."""
+    stages = []
+    for a in (1.0, 2.0, 3.0):
+        stages += [Stage(n * cell, 1e12, a) for n in (4, 2, 1, 0.5, 0)]
+    stages += [Stage(n * cell, 1e11, 3.0) for n in (1, 0.5, 0)]
     return stages
 
 
@@ -47,7 +59,7 @@ def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=Non
         for it in range(max_iter):
             t0 = time.perf_counter()
             try:
-                parts, conv = ctx.recon_step(s, data, st.R_sm, st.M0)
+                parts, conv = ctx.recon_step(s, data, st.R_sm, st.M0, st.a)
             except PMRError as e:
                 if e.code == -5:  # PMR_ELINESEARCH: no decrease left at this stage
                     break

@@ -49,7 +49,11 @@ int check_launch(pmr_ctx* c, const char* what) {
 
 namespace {
 
-constexpr int kNW = 5661;
+constexpr int kNW = 5661 + kMassWeights;  // trunk + mass network (the latter only with head == 1)
+
+int n_weights(const pmr_config* cfg) { return 5661 + (cfg->head == 1 ? kMassWeights : 0); }
+
+float logistic_a(const pmr_anneal* an) { return an ? (float)an->a_logistic : 3.0f; }
 
 const char* validate(const pmr_config* cfg) {
     if (!cfg) return "config is NULL";
@@ -69,6 +73,7 @@ const char* validate(const pmr_config* cfg) {
     if (cfg->lbfgs_m < 1 || cfg->lbfgs_m > 64) return "lbfgs_m must be 1..64";
     if (!(cfg->lbfgs_tol >= 0)) return "lbfgs_tol must be >= 0";
     if (cfg->nn_path < 0 || cfg->nn_path > 2) return "nn_path must be 0, 1 or 2";
+    if (cfg->head < 0 || cfg->head > 1) return "head must be 0 or 1";
     return nullptr;
 }
 
@@ -168,12 +173,12 @@ int loss_and_grad_impl(pmr_ctx* c, const float2* s, const float* data, const pmr
     PMR_TRY(pm_forward_impl(c, s));
     PMR_TRY(density_slot(c, c->cfg.nsteps, dfin, c->delta, true));
     PMR_TRY(nn_features(c, c->delta));
-    PMR_TRY(mlp_forward(c, c->feat, c->M));
+    PMR_TRY(mlp_forward(c, c->feat, c->M, logistic_a(an)));
     PMR_TRY(residual_forward(c, data, an, c->red_out + 1));
     PMR_TRY(prior_value(c, s, c->red_out));
     // adjoint
     PMR_TRY(residual_backward(c, an, c->gm2));
-    PMR_TRY(mlp_backward(c, c->feat, c->gm2, c->gfeat));
+    PMR_TRY(mlp_backward(c, c->feat, c->gm2, c->gfeat, logistic_a(an)));
     PMR_TRY(features_T(c, c->gfeat, c->gm));
     PMR_TRY(readout_grad(c, c->gm, dfin, N3, true, 1.0f, false, c->lam_x));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->lam_p, 0, sizeof(float) * 3 * N3, c->stream), "memset"));
@@ -208,6 +213,7 @@ void pmr_default_config(pmr_config* cfg) {
     cfg->lbfgs_m = 10;
     cfg->lbfgs_tol = 1e-3;
     cfg->nn_path = 0;
+    cfg->head = 0;
 }
 
 size_t pmr_workspace_bytes(const pmr_config* cfg) {
@@ -277,10 +283,13 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
                             "table");
     }
     if (rc == PMR_OK) {
-        c->W_host.resize(kNW);
-        rc = check_cuda(c, cudaMemcpy(c->W, nn_weights_dev, sizeof(float) * kNW, cudaMemcpyDeviceToDevice), "weights");
+        const int nw = n_weights(cfg);
+        c->W_host.assign(kNW, 0.0f);
+        rc = check_cuda(c, cudaMemset(c->W, 0, sizeof(float) * kNW), "weights");
         if (rc == PMR_OK)
-            rc = check_cuda(c, cudaMemcpy(c->W_host.data(), nn_weights_dev, sizeof(float) * kNW, cudaMemcpyDeviceToHost),
+            rc = check_cuda(c, cudaMemcpy(c->W, nn_weights_dev, sizeof(float) * nw, cudaMemcpyDeviceToDevice), "weights");
+        if (rc == PMR_OK)
+            rc = check_cuda(c, cudaMemcpy(c->W_host.data(), nn_weights_dev, sizeof(float) * nw, cudaMemcpyDeviceToHost),
                             "weights");
         if (rc == PMR_OK) rc = mlp_tc_init(c);
     }
@@ -334,18 +343,19 @@ int pm_adjoint(pmr_ctx* c, const float* grad_delta, void* grad_s_k) {
     return pm_adjoint_impl(c, (float2*)grad_s_k);
 }
 
-int nn_halo_map(pmr_ctx* c, const float* delta, float* mass_out) {
+int nn_halo_map(pmr_ctx* c, const float* delta, const pmr_anneal* an, float* mass_out) {
     PMR_TRY(check_ctx(c));
     if (!delta || !mass_out) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(nn_features(c, delta));
-    return mlp_forward(c, c->feat, mass_out);
+    return mlp_forward(c, c->feat, mass_out, logistic_a(an));
 }
 
-int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const float* grad_mass, float* grad_delta) {
+int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const pmr_anneal* an, const float* grad_mass,
+                        float* grad_delta) {
     PMR_TRY(check_ctx(c));
     if (!delta || !grad_mass || !grad_delta) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(nn_features(c, delta));
-    PMR_TRY(mlp_backward(c, c->feat, grad_mass, c->gfeat));
+    PMR_TRY(mlp_backward(c, c->feat, grad_mass, c->gfeat, logistic_a(an)));
     return features_T(c, c->gfeat, grad_delta);
 }
 
@@ -372,7 +382,7 @@ int recon_step(pmr_ctx* c, void* s_k_v, const float* data, const pmr_anneal* an,
     LBFGS& L = c->lb;
     const int64_t n = L.n;
     double host[3];
-    if (!L.have_f || an->R_sm != L.an.R_sm || an->M0 != L.an.M0) {
+    if (!L.have_f || an->R_sm != L.an.R_sm || an->M0 != L.an.M0 || an->a_logistic != L.an.a_logistic) {
         L.k = 0;
         L.head = 0;
         PMR_TRY(loss_and_grad_impl(c, s_k, data, an, host, L.gk));
@@ -385,7 +395,7 @@ int recon_step(pmr_ctx* c, void* s_k_v, const float* data, const pmr_anneal* an,
     double sc[3];
     double gd = 0.0;
     if (L.k > 0) {
-        PMR_TRY(lbfgs_two_loop(c, L.g, L.S, L.Y, L.k, L.head, L.m, n, L.rho_host.data(), L.d));
+        PMR_TRY(lbfgs_two_loop(c, L.g, L.S, L.Y, L.k, L.head, L.m, n, L.rho_host.data(), L.d, true));
         PMR_TRY(dot64(c, L.g, L.d, n, L.scal + 2));
         PMR_TRY(check_cuda(c, cudaMemcpyAsync(sc, L.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "rb"));
         PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
@@ -396,14 +406,13 @@ int recon_step(pmr_ctx* c, void* s_k_v, const float* data, const pmr_anneal* an,
         }
     }
     if (L.k == 0) {
-        PMR_TRY(dot64(c, L.g, L.g, n, L.scal + 2));
+        // first step: -H0 g with H0 = diag(P~ / w), the prior's inverse Hessian
+        PMR_TRY(prior_h0_apply(c, L.d, L.g, -1.0));
+        PMR_TRY(dot64(c, L.g, L.d, n, L.scal + 2));
         PMR_TRY(check_cuda(c, cudaMemcpyAsync(sc, L.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "rb"));
         PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
-        const double gn = std::sqrt(sc[0]);
-        if (!(gn > 0)) return fail(c, PMR_ELINESEARCH, "zero gradient");
-        PMR_TRY(check_cuda(c, cudaMemsetAsync(L.d, 0, sizeof(double) * n, c->stream), "memset"));
-        PMR_TRY(axpy64(c, L.d, L.g, nullptr, -1.0 / gn, n, nullptr));
-        gd = -gn;
+        gd = sc[0];
+        if (!(gd < 0)) return fail(c, PMR_ELINESEARCH, "zero gradient");
     }
     const double c1 = 1e-4;
     double t = 1.0, fnew = 0.0;
@@ -594,7 +603,7 @@ int pmr_lbfgs_direction(pmr_ctx* c, const double* g, const double* S, const doub
         PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
         rho[t] = 1.0 / sy[t];
     }
-    return lbfgs_two_loop(c, g, S, Y, k, 0, k, n, rho.data(), d);
+    return lbfgs_two_loop(c, g, S, Y, k, 0, k, n, rho.data(), d, false);
 }
 
 }  // extern "C"

@@ -28,6 +28,59 @@ struct FastDiv {
 #endif
 };
 
+// The mass network of the paper's two-network head (Sec. 2.1): 3 -> 20 -> 10
+// -> 1, ELU hidden units, linear output, on the three fields at the voxel.
+// Weights (301): Wm1[20][3] @0, bm1[20] @60, Wm2[10][20] @80, bm2[10] @280,
+// wm3[10] @290, bm3 @300.
+constexpr int kMassWeights = 301;
+#ifdef __CUDACC__
+__device__ __forceinline__ float elu_f(float x) { return x > 0.f ? x : expm1f(x); }
+__device__ __forceinline__ float elu_grad_f(float x) { return x > 0.f ? 1.f : expf(x); }
+
+// m = NNm(f0, f1, f2); with GRAD also g_c = gm * dm/df_c. Only the 10
+// second-layer values stay live; first-layer units are recomputed as needed.
+// Inlined, with scalar outputs, so no stack array or call sits in the kernels.
+__device__ __forceinline__ float mass_net_l1(const float* __restrict__ w, float f0, float f1, float f2, int j) {
+    return w[60 + j] + w[3 * j] * f0 + w[3 * j + 1] * f1 + w[3 * j + 2] * f2;
+}
+
+template <bool GRAD>
+__device__ __forceinline__ float mass_net(const float* __restrict__ w, float f0, float f1, float f2, float gm,
+                                          float& g0, float& g1, float& g2) {
+    float p2[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) p2[i] = w[280 + i];
+#pragma unroll 1
+    for (int j = 0; j < 20; ++j) {
+        const float h = elu_f(mass_net_l1(w, f0, f1, f2, j));
+#pragma unroll
+        for (int i = 0; i < 10; ++i) p2[i] = fmaf(w[80 + 20 * i + j], h, p2[i]);
+    }
+    float m = w[300];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) m = fmaf(w[290 + i], elu_f(p2[i]), m);
+    if (GRAD) {
+#pragma unroll
+        for (int i = 0; i < 10; ++i) p2[i] = gm * w[290 + i] * elu_grad_f(p2[i]);  // now d/d(pre-activation 2)
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 1
+        for (int j = 0; j < 20; ++j) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i < 10; ++i) s = fmaf(w[80 + 20 * i + j], p2[i], s);
+            s *= elu_grad_f(mass_net_l1(w, f0, f1, f2, j));
+            a0 = fmaf(w[3 * j], s, a0);
+            a1 = fmaf(w[3 * j + 1], s, a1);
+            a2 = fmaf(w[3 * j + 2], s, a2);
+        }
+        g0 = a0;
+        g1 = a1;
+        g2 = a2;
+    }
+    return m;
+}
+#endif
+
 // Radix schedule of a 1D FFT of length n (Stockham autosort, radices 4/3/2),
 // with the per-stage divisors the butterflies need.
 struct Radix {
@@ -226,8 +279,9 @@ int density_slot(pmr_ctx* c, int s, const float* disp, float* delta, bool sort);
 
 // network (nn.cu) ---------------------------------------------------------------
 int nn_features(pmr_ctx* c, const float* delta);  // -> c->feat
-int mlp_forward(pmr_ctx* c, const float* feat, float* M);
-int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat);
+// a: logistic sharpness of the two-network head (ignored by the softplus head)
+int mlp_forward(pmr_ctx* c, const float* feat, float* M, float a);
+int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat, float a);
 int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat);
 
 void twopt_free(pmr_ctx* c);
@@ -235,8 +289,8 @@ void twopt_free(pmr_ctx* c);
 // network on tcgen05 tensor cores (mlp_tc.cu) -----------------------------------
 int mlp_tc_init(pmr_ctx* c);
 void mlp_tc_free(pmr_ctx* c);
-int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit);
-int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit);  // -> c->gv
+int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit, float a);
+int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit, float a);  // -> c->gv
 
 // loss (loss.cu) ----------------------------------------------------------------
 int residual_forward(pmr_ctx* c, const float* data, const pmr_anneal* an, double* L_res_dev);
@@ -250,7 +304,9 @@ int check_finite(pmr_ctx* c, const double* v, int n, double* host);
 int lbfgs_alloc(pmr_ctx* c);
 void lbfgs_free(pmr_ctx* c);
 int lbfgs_two_loop(pmr_ctx* c, const double* g, const double* S, const double* Y, int k, int head, int m,
-                   int64_t n, const double* rho_host, double* d);
+                   int64_t n, const double* rho_host, double* d, bool prior_h0);
+// y = scale * diag(P~ / w) x over the half-array reals (the prior's inverse Hessian)
+int prior_h0_apply(pmr_ctx* c, double* y, const double* x, double scale);
 int dot64(pmr_ctx* c, const double* a, const double* b, int64_t n, double* out_dev);
 int c64_to_f64(pmr_ctx* c, const float2* a, double* out, int64_t nh);
 int f64_to_c64(pmr_ctx* c, const double* a, float2* out, int64_t nh);

@@ -82,7 +82,30 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, con
 
 constexpr int kGrid = 4 * 152;
 
+// y = scale * D x with D = P~(k) / w_k on every (real, imaginary) entry of the
+// half array (0 at k = 0): the Gaussian prior's inverse Hessian.
+__global__ void k_prior_h0(double* __restrict__ y, const double* __restrict__ x, int64_t nreal, int N, FastDiv fP,
+                           FastDiv fN, const double* __restrict__ inv_pow, double scale) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(j >> 1);
+        const uint32_t t = fP.div(i);
+        const int kz = (int)(i - t * fP.d);
+        const uint32_t ixu = fN.div(t);
+        const int iy = (int)(t - ixu * fN.d), ix = (int)ixu;
+        const int nx = 2 * ix <= N ? ix : ix - N, ny = 2 * iy <= N ? iy : iy - N;
+        const double ip = inv_pow[nx * nx + ny * ny + kz * kz];
+        const double w = (kz == 0 || 2 * kz == N) ? 1.0 : 2.0;
+        y[j] = ip > 0.0 ? scale * x[j] / (w * ip) : 0.0;
+    }
+}
+
 }  // namespace
+
+int prior_h0_apply(pmr_ctx* c, double* y, const double* x, double scale) {
+    k_prior_h0<<<kGrid, kT, 0, c->stream>>>(y, x, 2 * c->NH, c->N, FastDiv((uint32_t)c->P), FastDiv((uint32_t)c->N),
+                                             c->inv_power_tab, scale);
+    return check_launch(c, "prior_h0");
+}
 
 int dot64(pmr_ctx* c, const double* a, const double* b, int64_t n, double* out_dev) {
     k_dot_part<<<kB, kT, 0, c->stream>>>(a, b, n, c->red_part);
@@ -110,7 +133,7 @@ int axpy64(pmr_ctx* c, double* y, const double* x, const double* alpha_dev, doub
 // d = -H g. S, Y are rings of capacity m: pair t (0 = oldest) sits in slot (head + t) % m.
 // rho_host[slot] = 1 / (s.y) of that slot.
 int lbfgs_two_loop(pmr_ctx* c, const double* g, const double* S, const double* Y, int k, int head, int m, int64_t n,
-                   const double* rho_host, double* d) {
+                   const double* rho_host, double* d, bool prior_h0) {
     double* q = d;
     double* sc = c->lb.scal;  // [0]: dot, [1]: dot2
     PMR_TRY(check_cuda(c, cudaMemcpyAsync(q, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy"));
@@ -122,10 +145,22 @@ int lbfgs_two_loop(pmr_ctx* c, const double* g, const double* S, const double* Y
         PMR_TRY(check_launch(c, "two_loop_0"));
     }
     const int newest = (head + k - 1) % m;
-    PMR_TRY(dot64(c, S + (int64_t)newest * n, Y + (int64_t)newest * n, n, sc));
-    PMR_TRY(dot64(c, Y + (int64_t)newest * n, Y + (int64_t)newest * n, n, sc + 1));
-    k_two_loop_axpy<<<kGrid, kT, 0, c->stream>>>(q, q, n, 2, sc, sc + 1, 0.0, nullptr);
-    PMR_TRY(check_launch(c, "two_loop_scale"));
+    if (prior_h0) {
+        // r = gamma D q, gamma = s^T y / y^T D y of the newest pair; lb.yk is free
+        // scratch here (it holds the candidate pair only after the line search)
+        double* Dy = c->lb.yk;
+        PMR_TRY(prior_h0_apply(c, Dy, Y + (int64_t)newest * n, 1.0));
+        PMR_TRY(dot64(c, S + (int64_t)newest * n, Y + (int64_t)newest * n, n, sc));
+        PMR_TRY(dot64(c, Y + (int64_t)newest * n, Dy, n, sc + 1));
+        PMR_TRY(prior_h0_apply(c, q, q, 1.0));
+        k_two_loop_axpy<<<kGrid, kT, 0, c->stream>>>(q, q, n, 2, sc, sc + 1, 0.0, nullptr);
+        PMR_TRY(check_launch(c, "two_loop_scale"));
+    } else {
+        PMR_TRY(dot64(c, S + (int64_t)newest * n, Y + (int64_t)newest * n, n, sc));
+        PMR_TRY(dot64(c, Y + (int64_t)newest * n, Y + (int64_t)newest * n, n, sc + 1));
+        k_two_loop_axpy<<<kGrid, kT, 0, c->stream>>>(q, q, n, 2, sc, sc + 1, 0.0, nullptr);
+        PMR_TRY(check_launch(c, "two_loop_scale"));
+    }
     for (int t = 0; t < k; ++t) {
         const int slot = (head + t) % m;
         PMR_TRY(dot64(c, Y + (int64_t)slot * n, q, n, sc));

@@ -61,8 +61,9 @@ constexpr uint32_t SZ_B1 = img_bytes(N1, K1), SZ_B2 = img_bytes(N2, K2), SZ_B3 =
                    SZ_B4 = img_bytes(NB4, K4);
 constexpr uint32_t S_B1 = 0;                  // hi, lo
 constexpr uint32_t S_B2 = S_B1 + 2 * SZ_B1;   // hi, lo
-constexpr uint32_t S_VEC = S_B2 + 2 * SZ_B2;  // b1[64], b2[32], w3[32], b3[4]
-constexpr uint32_t SZ_VEC = 640;               // 4 * (64 + 32 + 32 + 4) rounded up to 128 B
+constexpr uint32_t S_VEC = S_B2 + 2 * SZ_B2;  // b1[64], b2[32], w3[32], b3[4], mass network[301]
+constexpr uint32_t VEC_MASS = 160;             // float offset of the mass-network weights
+constexpr uint32_t SZ_VEC = 1920;              // 4 * (160 + 301) rounded up to 128 B
 constexpr uint32_t S_B3 = S_VEC + SZ_VEC;     // backward only
 constexpr uint32_t S_B4 = S_B3 + 2 * SZ_B3;
 constexpr uint32_t IMG_FWD = S_B3;            // bytes of the image the forward copies
@@ -70,8 +71,8 @@ constexpr uint32_t IMG_ALL = S_B4 + 2 * SZ_B4;
 constexpr uint32_t SZ_A = img_bytes(TM, K1);  // largest A operand (hi or lo)
 constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
 constexpr int HALO_PER = (HALO + NT - 1) / NT;  // halo values each thread loads
-// halo, partials, g_y, stencil offsets, barrier + TMEM slot
-constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * K1 + 64;
+// halo, partials, g_y, centre-value gradients, stencil offsets, barrier + TMEM slot
+constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * 3 * TM + 4 * K1 + 64;
 constexpr uint32_t SMEM_FWD = S_A_FWD + 2 * SZ_A + SZ_TAIL;
 constexpr uint32_t SMEM_BWD = S_A_BWD + 2 * SZ_A + SZ_TAIL;
 static_assert(SMEM_BWD <= 232448, "shared memory budget");
@@ -191,8 +192,8 @@ struct TileMap {
 template <bool BWD>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
-             TileMap tm, int ntiles, int nsplit, float M_scale, float* __restrict__ M_out, float* __restrict__ gv,
-             int* __restrict__ err) {
+             TileMap tm, int ntiles, int nsplit, float M_scale, int head, float a, float* __restrict__ M_out,
+             float* __restrict__ gv, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const uint32_t S_A = BWD ? S_A_BWD : S_A_FWD;
     unsigned char* Ahi = sm + S_A;
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(NT, 1)
     float* halo = reinterpret_cast<float*>(Alo + SZ_A);
     float* part = halo + HALO;   // [4][TM]
     float* gys = part + 4 * TM;  // [TM]
-    int* koff = reinterpret_cast<int*>(gys + TM);  // [K1]: halo offset of stencil input k (-1: padding)
+    float* gcen = gys + TM;      // [3][TM]: gradient w.r.t. the voxel's own three values (mass network)
+    int* koff = reinterpret_cast<int*>(gcen + 3 * TM);  // [K1]: halo offset of stencil input k (-1: padding)
     uint64_t* bar = reinterpret_cast<uint64_t*>(koff + K1);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const float* vec = reinterpret_cast<const float*>(sm + S_VEC);
@@ -370,7 +372,25 @@ __global__ void __launch_bounds__(NT, 1)
             const bool in = gx < N && gy < N && gz < N;
             const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
             const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
-            if (!BWD) {
+            if (head == 1) {
+                // two-network head (Sec. 2.1): M = M_scale logistic(y, a) NNm(f), f = the voxel's own values
+                float f[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
+                const float p = sigmoidf(a * y);
+                if (!BWD) {
+                    float u0, u1, u2;
+                    if (in) M_out[vox] = M_scale * p * mass_net<false>(vec + VEC_MASS, f[0], f[1], f[2], 0.f, u0, u1, u2);
+                } else {
+                    const float g = in ? gM[vox] * M_scale : 0.f;
+                    float g0, g1, g2;
+                    const float m = mass_net<true>(vec + VEC_MASS, f[0], f[1], f[2], g * p, g0, g1, g2);
+                    gys[r] = g * m * a * p * (1.f - p);
+                    gcen[r] = g0;
+                    gcen[TM + r] = g1;
+                    gcen[2 * TM + r] = g2;
+                }
+            } else if (!BWD) {
                 if (in) M_out[vox] = M_scale * softplusf(y);
             } else {
                 gys[r] = in ? gM[vox] * M_scale * sigmoidf(y) : 0.f;
@@ -443,7 +463,9 @@ __global__ void __launch_bounds__(NT, 1)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int k = 24 * cb + 8 * h + j;
-                    if (in && k < NI) gv[k * N3 + vox] = a[j];
+                    float v = a[j];
+                    if (head == 1 && k < NI && k % 27 == 13) v += gcen[(k / 27) * TM + row];  // mass network's input
+                    if (in && k < NI) gv[k * N3 + vox] = v;
                 }
             }
         }
@@ -519,6 +541,7 @@ int mlp_tc_init(pmr_ctx* c) {
     for (int h = 0; h < H2; ++h) vec[64 + h] = W[OFF_B2 + h];
     for (int h = 0; h < H2; ++h) vec[96 + h] = W[OFF_W3 + h];
     vec[128] = W[OFF_B3];
+    for (int i = 0; i < kMassWeights; ++i) vec[VEC_MASS + i] = W[OFF_B3 + 1 + i];  // zeros unless head == 1
     PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_img, IMG_ALL), "tc weights"));
     PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img, img.data(), IMG_ALL, cudaMemcpyHostToDevice), "tc weights"));
     PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_err, sizeof(int)), "tc flag"));
@@ -537,21 +560,23 @@ void mlp_tc_free(pmr_ctx* c) {
     c->tc_err = nullptr;
 }
 
-int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit) {
+int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit, float a) {
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
     const int grid = std::min(ntiles, c->num_sms);
     k_mlp_tc<false><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, reinterpret_cast<const float4*>(c->tc_img), m,
-                                                        ntiles, nsplit, (float)c->cfg.M_scale, M, nullptr, c->tc_err);
+                                                        ntiles, nsplit, (float)c->cfg.M_scale, c->cfg.head, a, M,
+                                                        nullptr, c->tc_err);
     return check_launch(c, "mlp_tc_fwd");
 }
 
-int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit) {
+int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit, float a) {
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
     const int grid = std::min(ntiles, c->num_sms);
     k_mlp_tc<true><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, reinterpret_cast<const float4*>(c->tc_img), m, ntiles,
-                                                       nsplit, (float)c->cfg.M_scale, nullptr, c->gv, c->tc_err);
+                                                       nsplit, (float)c->cfg.M_scale, c->cfg.head, a, nullptr, c->gv,
+                                                       c->tc_err);
     return check_launch(c, "mlp_tc_bwd");
 }
 

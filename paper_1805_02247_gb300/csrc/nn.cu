@@ -19,7 +19,7 @@ constexpr int OFF_B1 = H1 * NI, OFF_W2 = OFF_B1 + H1, OFF_B2 = OFF_W2 + H2 * H1,
               OFF_B3 = OFF_W3 + H2, NW = OFF_B3 + 1;
 
 struct Weights {
-    float w[NW];
+    float w[NW + kMassWeights];  // trunk, then the mass network (two-network head)
 };
 
 // tile of voxels per block, z fastest
@@ -81,8 +81,14 @@ __device__ __forceinline__ float layer3(const Weights& W, const float* a2) {
     return y;
 }
 
+// the voxel's own three field values (centre of the staged tile)
+__device__ __forceinline__ void centre(const float* s, int lx, int ly, int lz, float f[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] = s[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
+}
+
 __global__ void __launch_bounds__(kT) k_mlp_fwd(const Weights W, const float* __restrict__ feat, int N, float M_scale,
-                                                float* __restrict__ M) {
+                                                int head, float a, float* __restrict__ M) {
     __shared__ float s[3 * HX * HY * HZ];
     const int64_t N3 = (int64_t)N * N * N;
     const int x0 = blockIdx.z * TX, y0 = blockIdx.y * TY, z0 = blockIdx.x * TZ;
@@ -95,14 +101,23 @@ __global__ void __launch_bounds__(kT) k_mlp_fwd(const Weights W, const float* __
     layer1(W, s, lx, ly, lz, a1);
     layer2(W, a1, a2);
     const float y = layer3(W, a2);
-    M[((int64_t)gx * N + gy) * N + gz] = M_scale * softplusf(y);
+    float out;
+    if (head == 1) {
+        float f[3];
+        centre(s, lx, ly, lz, f);
+        float u0, u1, u2;
+        out = M_scale * sigmoidf(a * y) * mass_net<false>(W.w + NW, f[0], f[1], f[2], 0.f, u0, u1, u2);
+    } else {
+        out = M_scale * softplusf(y);
+    }
+    M[((int64_t)gx * N + gy) * N + gz] = out;
 }
 
 // Per voxel: recompute the forward, back-propagate gM to the 81 inputs and
 // write them to gv[81][N3] (each input row is later gathered to its voxel).
 __global__ void __launch_bounds__(kT) k_mlp_bwd(const Weights W, const float* __restrict__ feat,
-                                                const float* __restrict__ gM, int N, float M_scale,
-                                                float* __restrict__ gv) {
+                                                const float* __restrict__ gM, int N, float M_scale, int head,
+                                                float a, float* __restrict__ gv) {
     __shared__ float s[3 * HX * HY * HZ];
     const int64_t N3 = (int64_t)N * N * N;
     const int x0 = blockIdx.z * TX, y0 = blockIdx.y * TY, z0 = blockIdx.x * TZ;
@@ -116,7 +131,17 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(const Weights W, const float* __
     layer1(W, s, lx, ly, lz, a1);
     layer2(W, a1, a2);
     const float y = layer3(W, a2);
-    const float gy_ = gM[vox] * M_scale * sigmoidf(y);
+    float gy_, gc[3] = {0.f, 0.f, 0.f};
+    if (head == 1) {
+        // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
+        float f[3];
+        centre(s, lx, ly, lz, f);
+        const float p = sigmoidf(a * y), g = gM[vox] * M_scale;
+        const float m = mass_net<true>(W.w + NW, f[0], f[1], f[2], g * p, gc[0], gc[1], gc[2]);
+        gy_ = g * m * a * p * (1.f - p);
+    } else {
+        gy_ = gM[vox] * M_scale * sigmoidf(y);
+    }
     float g2[H2];
 #pragma unroll
     for (int h = 0; h < H2; ++h) g2[h] = a2[h] > 0.f ? W.w[OFF_W3 + h] * gy_ : 0.f;
@@ -133,6 +158,7 @@ __global__ void __launch_bounds__(kT) k_mlp_bwd(const Weights W, const float* __
         float acc = 0.f;
 #pragma unroll
         for (int h = 0; h < H1; ++h) acc = fmaf(W.w[h * NI + k], g1[h], acc);
+        if (k % 27 == 13) acc += gc[k / 27];  // the mass network reads the centre values
         gv[k * N3 + vox] = acc;
     }
 }
@@ -179,12 +205,13 @@ static_assert(sizeof(Weights) <= 32000, "weights must fit the kernel parameter s
 
 // nn_path 0: tensor cores, 3xTF32 (float32 accuracy); 1: tensor cores, TF32;
 // 2: float32 CUDA cores.
-int mlp_forward(pmr_ctx* c, const float* feat, float* M) {
-    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1) return mlp_tc_forward(c, feat, M, c->cfg.nn_path == 0 ? 3 : 1);
+int mlp_forward(pmr_ctx* c, const float* feat, float* M, float a) {
+    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1)
+        return mlp_tc_forward(c, feat, M, c->cfg.nn_path == 0 ? 3 : 1, a);
     static_assert(NW == 5661, "weight layout");
     Weights W;
-    std::copy(c->W_host.begin(), c->W_host.end(), W.w);
-    k_mlp_fwd<<<mlp_grid(c->N), kT, 0, c->stream>>>(W, feat, c->N, (float)c->cfg.M_scale, M);
+    std::copy(c->W_host.begin(), c->W_host.begin() + (NW + kMassWeights), W.w);
+    k_mlp_fwd<<<mlp_grid(c->N), kT, 0, c->stream>>>(W, feat, c->N, (float)c->cfg.M_scale, c->cfg.head, a, M);
     return check_launch(c, "mlp_fwd");
 }
 
@@ -193,14 +220,15 @@ int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat) {
     return check_launch(c, "stencil_T");
 }
 
-int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat) {
+int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat, float a) {
     if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1) {
-        PMR_TRY(mlp_tc_backward_gv(c, feat, gM, c->cfg.nn_path == 0 ? 3 : 1));
+        PMR_TRY(mlp_tc_backward_gv(c, feat, gM, c->cfg.nn_path == 0 ? 3 : 1, a));
         return stencil_transpose(c, c->gv, gfeat);
     }
     Weights W;
-    std::copy(c->W_host.begin(), c->W_host.end(), W.w);
-    k_mlp_bwd<<<mlp_grid(c->N), kT, 0, c->stream>>>(W, feat, gM, c->N, (float)c->cfg.M_scale, c->gv);
+    std::copy(c->W_host.begin(), c->W_host.begin() + (NW + kMassWeights), W.w);
+    k_mlp_bwd<<<mlp_grid(c->N), kT, 0, c->stream>>>(W, feat, gM, c->N, (float)c->cfg.M_scale, c->cfg.head, a,
+                                                     c->gv);
     PMR_TRY(check_launch(c, "mlp_bwd"));
     return stencil_transpose(c, c->gv, gfeat);
 }

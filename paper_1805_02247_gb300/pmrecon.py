@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(_HERE, "libpmrecon.so")
 
 PMR_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENAN", -5: "ELINESEARCH", -6: "ESTATE"}
-N_WEIGHTS = 5661
+N_WEIGHTS = 5661  # trunk network; the two-network head adds the mass network's
+N_MASS_WEIGHTS = 301
 
 
 class PMRError(RuntimeError):
@@ -31,12 +32,12 @@ class Config(ctypes.Structure):
         ("omega_m", ctypes.c_double), ("sigma8", ctypes.c_double), ("gamma_bbks", ctypes.c_double),
         ("R_feat", ctypes.c_double * 3), ("R_M", ctypes.c_double), ("sigma_N2", ctypes.c_double),
         ("mu_N", ctypes.c_double), ("f_eff", ctypes.c_double), ("M_scale", ctypes.c_double),
-        ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double), ("nn_path", ctypes.c_int),
+        ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double), ("nn_path", ctypes.c_int), ("head", ctypes.c_int),
     ]
 
 
 class Anneal(ctypes.Structure):
-    _fields_ = [("R_sm", ctypes.c_double), ("M0", ctypes.c_double)]
+    _fields_ = [("R_sm", ctypes.c_double), ("M0", ctypes.c_double), ("a_logistic", ctypes.c_double)]
 
 
 _lib = None
@@ -53,8 +54,8 @@ _SIGS = {
     "pmr_linear_field": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "pm_forward": (ctypes.c_int, [_P, _P, _P]),
     "pm_adjoint": (ctypes.c_int, [_P, _P, _P]),
-    "nn_halo_map": (ctypes.c_int, [_P, _P, _P]),
-    "nn_halo_map_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nn_halo_map": (ctypes.c_int, [_P, _P, _P, _P]),
+    "nn_halo_map_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "loss_and_grad": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "recon_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "pmr_lbfgs_reset": (ctypes.c_int, [_P]),
@@ -135,8 +136,9 @@ class Context:
         self.device = weights.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         w = weights.to(device=self.device, dtype=torch.float32).contiguous()
-        if w.numel() != N_WEIGHTS:
-            raise ValueError(f"weights must have {N_WEIGHTS} entries")
+        want = N_WEIGHTS + (N_MASS_WEIGHTS if cfg.head == 1 else 0)
+        if w.numel() != want:
+            raise ValueError(f"weights must have {want} entries")
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             rc = lib.pmr_create(ctypes.byref(cfg), _ptr(w), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
@@ -183,26 +185,32 @@ class Context:
         self._check(self._lib.pm_adjoint(self._h, _ptr(grad_delta), _ptr(g)))
         return g
 
-    def nn_halo_map(self, delta: torch.Tensor, out=None) -> torch.Tensor:
+    def nn_halo_map(self, delta: torch.Tensor, a: float = 3.0, out=None) -> torch.Tensor:
+        """Halo-mass map of the final density; a = logistic sharpness (two-network head only)."""
         m = self.mesh() if out is None else out
-        self._check(self._lib.nn_halo_map(self._h, _ptr(delta), _ptr(m)))
+        an = Anneal(0.0, 0.0, a)
+        self._check(self._lib.nn_halo_map(self._h, _ptr(delta), ctypes.byref(an), _ptr(m)))
         return m
 
-    def nn_halo_map_adjoint(self, delta: torch.Tensor, grad_mass: torch.Tensor, out=None) -> torch.Tensor:
+    def nn_halo_map_adjoint(self, delta: torch.Tensor, grad_mass: torch.Tensor, a: float = 3.0,
+                            out=None) -> torch.Tensor:
         g = self.mesh() if out is None else out
-        self._check(self._lib.nn_halo_map_adjoint(self._h, _ptr(delta), _ptr(grad_mass), _ptr(g)))
+        an = Anneal(0.0, 0.0, a)
+        self._check(self._lib.nn_halo_map_adjoint(self._h, _ptr(delta), ctypes.byref(an),
+                                                  _ptr(grad_mass), _ptr(g)))
         return g
 
-    def loss_and_grad(self, s, data, R_sm: float, M0: float, out=None, readback: bool = True):
+    def loss_and_grad(self, s, data, R_sm: float, M0: float, out=None, readback: bool = True,
+                      a: float = 3.0):
         g = self.half() if out is None else out
-        an = Anneal(R_sm, M0)
+        an = Anneal(R_sm, M0, a)
         host = (ctypes.c_double * 3)()
         self._check(self._lib.loss_and_grad(self._h, _ptr(s), _ptr(data), ctypes.byref(an),
                                             host if readback else None, _ptr(g)))
         return (tuple(host) if readback else None), g
 
-    def recon_step(self, s, data, R_sm: float, M0: float):
-        an = Anneal(R_sm, M0)
+    def recon_step(self, s, data, R_sm: float, M0: float, a: float = 3.0):
+        an = Anneal(R_sm, M0, a)
         host = (ctypes.c_double * 3)()
         conv = ctypes.c_int(0)
         self._check(self._lib.recon_step(self._h, _ptr(s), _ptr(data), ctypes.byref(an), host, ctypes.byref(conv)))
@@ -299,15 +307,16 @@ class ReconLoss(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx_, s: torch.Tensor, data: torch.Tensor, job: Context, R_sm: float, M0: float):
-        parts, g = job.loss_and_grad(s.detach().contiguous(), data.contiguous(), R_sm, M0)
+    def forward(ctx_, s: torch.Tensor, data: torch.Tensor, job: Context, R_sm: float, M0: float,
+                a: float = 3.0):
+        parts, g = job.loss_and_grad(s.detach().contiguous(), data.contiguous(), R_sm, M0, a=a)
         ctx_.save_for_backward(g)
         return torch.tensor(parts[0], dtype=torch.float64, device=s.device)
 
     @staticmethod
     def backward(ctx_, grad_out):
         (g,) = ctx_.saved_tensors
-        return g * grad_out.to(torch.float32), None, None, None, None
+        return g * grad_out.to(torch.float32), None, None, None, None, None
 
 
 class PMForward(torch.autograd.Function):

@@ -61,6 +61,33 @@ def xavier_weights(seed: int) -> np.ndarray:
     return w
 
 
+N_MASS_WEIGHTS = 20 * 3 + 20 + 10 * 20 + 10 + 10 + 1
+
+
+def mass_net_weights(seed: int, out_bias: float = 5.0, scale: float = 0.25) -> np.ndarray:
+    """Glorot-uniform weights of the 3-20-10-1 mass network times `scale`, zero hidden biases.
+
+    Layout: Wm1[20][3], bm1[20], Wm2[10][20], bm2[10], wm3[10], bm3. An untrained
+    linear output has no sign; the output bias (default 5) and the shrunken
+    weights keep the synthetic mass positive, as a trained mass network is.
+    """
+    g = rng(seed)
+    out = []
+    for fan_in, fan_out in ((3, 20), (20, 10), (10, 1)):
+        lim = scale * np.sqrt(6.0 / (fan_in + fan_out))
+        out.append(g.uniform(-lim, lim, size=(fan_out, fan_in)).ravel())
+        out.append(np.zeros(fan_out))
+    w = np.concatenate(out)
+    w[-1] = out_bias
+    assert w.size == N_MASS_WEIGHTS
+    return w.astype(np.float32)
+
+
+def two_net_weights(seed: int) -> np.ndarray:
+    """Weights of the two-network head: the trunk's 5661 then the mass network's 301."""
+    return np.concatenate([xavier_weights(seed), mass_net_weights(seed)]).astype(np.float32)
+
+
 def uniform_positions(n: int, npart: int, seed: int, lo: float = 0.0, hi: float | None = None) -> np.ndarray:
     """Particle positions in grid units, float32 SoA [3][npart], uniform in [lo, hi)."""
     hi = float(n) if hi is None else hi

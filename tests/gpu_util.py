@@ -30,7 +30,8 @@ def to_np(t: torch.Tensor) -> np.ndarray:
 def context(N=32, L=100.0, nsteps=3, seed_w=1, **kw):
     lib()
     cfg = pmrecon.default_config(N=N, L=L, nsteps=nsteps, **kw)
-    w = torch.from_numpy(synth.xavier_weights(seed_w)).cuda()
+    w = synth.two_net_weights(seed_w) if kw.get("head", 0) == 1 else synth.xavier_weights(seed_w)
+    w = torch.from_numpy(w).cuda()
     return pmrecon.Context(cfg, w), cfg
 
 

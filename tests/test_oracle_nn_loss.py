@@ -76,6 +76,72 @@ def test_mlp_backward_by_finite_differences():
         assert rdot(g, v) == pytest.approx(fd, rel=1e-6)
 
 
+def test_two_net_special_values_and_closed_form():
+    assert nn.logistic(0.0, 3.0) == 0.5 and nn.logistic(0.0, 1.0) == 0.5
+    assert nn.elu(-50.0) == pytest.approx(-1.0) and nn.elu(2.0) == 2.0
+    assert nn.elu_grad(-1e-12) == pytest.approx(1.0) and nn.elu_grad(3.0) == 1.0
+    # NNp: logit = relu(f0(x)) - 0.5; NNm: hidden 0 = elu(f1(x)), second layer
+    # passes it on, output = elu(elu(f1)) + 2  =>  closed form
+    N = 4
+    wp = np.zeros(synth.N_WEIGHTS)
+    W1, _, W2, _, w3, _ = nn.unpack(wp)
+    W1[0, 13] = 1.0
+    W2[0, 0] = 1.0
+    w3[0] = 1.0
+    wp[-1] = -0.5
+    wm = np.zeros(synth.N_MASS_WEIGHTS)
+    V1, _, V2, _, v3, _ = nn.unpack_mass(wm)
+    V1[0, 1] = 1.0
+    V2[0, 0] = 1.0
+    v3[0] = 1.0
+    wm[-1] = 2.0
+    f = np.random.default_rng(9).standard_normal((3, N, N, N))
+    a = 2.0
+    M = nn.two_net_forward(f, wp, wm, 1e12, a)
+    p = 1.0 / (1.0 + np.exp(-a * (np.maximum(f[0], 0.0) - 0.5)))
+    m = nn.elu(nn.elu(f[1])) + 2.0
+    assert np.allclose(M, 1e12 * p * m, rtol=1e-14)
+
+
+def test_two_net_backward_by_finite_differences():
+    rng = np.random.default_rng(10)
+    N = 4
+    wp = synth.xavier_weights(1).astype(np.float64)
+    wm = synth.mass_net_weights(3).astype(np.float64)
+    wm[:60] *= 12.0  # larger first-layer weights exercise both ELU branches
+    f = rng.standard_normal((3, N, N, N))
+    gM = rng.standard_normal((N, N, N))
+    g = nn.two_net_backward(gM, f, wp, wm, 2.0, 1.5)
+    fun = lambda ff: float(np.sum(gM * nn.two_net_forward(ff, wp, wm, 2.0, 1.5)))
+    for _ in range(5):
+        v = rng.standard_normal(f.shape)
+        eps = 1e-6
+        fd = (fun(f + eps * v) - fun(f - eps * v)) / (2 * eps)
+        assert rdot(g, v) == pytest.approx(fd, rel=1e-6)
+
+
+def test_two_net_loss_gradient_by_finite_differences():
+    N = 8
+    pms = pm.PMSetup(N=N, L=50.0, nsteps=2)
+    ls = loss.LossSetup(head="two_net")
+    # M0 = 1e11 (second stage of Sec. 4.3) dominates the ringing of the sub-cell
+    # R_M smoothing of the spiky logistic-head mass field at this coarse mesh
+    an = loss.Anneal(R_sm=3.0, M0=1e11, a=2.0)
+    w = np.concatenate([synth.xavier_weights(1), synth.mass_net_weights(3)])
+    data = loss.synthetic_data(synth.white_noise(N, 2), synth.scatter_noise(N, 2), w, pms, ls, a=2.0)
+    s = 0.5 * pm.linear_field(synth.white_noise(N, 0), pms)
+    parts, g = loss.loss_and_grad(s, data, w, pms, ls, an)
+    assert np.isfinite(parts["loss"])
+    f = lambda ss: loss.loss(ss, data, w, pms, ls, an)["loss"]
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        v = pm.rfft3(rng.standard_normal((N, N, N))) * np.sqrt(pm.power_half(pms) / N**3)
+        v[0, 0, 0] = 0
+        eps = 2e-7  # below the nearest CIC cell-face crossing along these directions
+        fd = (f(s + eps * v) - f(s - eps * v)) / (2 * eps)
+        assert rdot(g, v) == pytest.approx(fd, rel=2e-5)
+
+
 # ----------------------------------------------------------------------------- loss
 
 def test_prior_equals_full_grid_sum_and_its_gradient():
@@ -162,6 +228,52 @@ def test_lbfgs_minimises_a_quadratic():
         if np.linalg.norm(st.g) < 1e-7:  # Armijo on f resolves |g| to ~1e-9 in fp64
             break
     assert np.allclose(st.x, np.linalg.solve(A, b), atol=1e-7)
+
+
+def test_two_loop_with_diagonal_h0_equals_dense_bfgs_matrix():
+    rng = np.random.default_rng(4)
+    n, k = 10, 4
+    S = [rng.standard_normal(n) for _ in range(k)]
+    M = rng.standard_normal((n, n)); M = M @ M.T + n * np.eye(n)
+    Y = [M @ s for s in S]
+    g = rng.standard_normal(n)
+    D = rng.uniform(0.5, 3.0, n)
+    # initial matrix gamma D, gamma from the newest pair (Nocedal & Wright Sec. 7.2)
+    H = (S[-1] @ Y[-1]) / (Y[-1] @ (D * Y[-1])) * np.diag(D)
+    for s, y in zip(S, Y):
+        rho = 1.0 / (y @ s)
+        V = np.eye(n) - rho * np.outer(y, s)
+        H = V.T @ H @ V + rho * np.outer(s, s)
+    assert np.allclose(lbfgs.two_loop(g, S, Y, D), -H @ g, rtol=1e-12, atol=1e-12)
+
+
+def test_diagonal_h0_scaling_is_exact_on_a_scaled_diagonal_quadratic():
+    # f = 1/2 x^T A x with A = (c D)^-1: after one pair, gamma D = A^-1 exactly,
+    # so the second direction is the Newton step and lands on x = 0
+    rng = np.random.default_rng(6)
+    n = 12
+    D = rng.uniform(0.2, 5.0, n)
+    A = 1.0 / (3.7 * D)
+    fun = lambda x: (0.5 * float(x @ (A * x)), A * x)
+    st = lbfgs.LBFGSState(x=rng.standard_normal(n))
+    lbfgs.step(fun, st, H0=D, tol=0.0)
+    status, _, _ = lbfgs.step(fun, st, H0=D, tol=0.0)
+    assert status == "ok"
+    assert np.max(np.abs(st.x)) < 1e-12
+
+
+def test_prior_preconditioned_first_step_solves_the_prior():
+    # with the residual switched off the loss is the Gaussian prior; the first
+    # step -H0 g with H0 = diag(P~/w) lands exactly on its minimum s = 0
+    N = 8
+    pms = pm.PMSetup(N=N, L=100.0, nsteps=1)
+    P = pm.power_half(pms)
+    s0 = pm.linear_field(synth.white_noise(N, 5), pms)
+    fun = lambda x: (loss.prior(x, P), loss.prior_grad(x, P))
+    st = lbfgs.LBFGSState(x=s0.copy())
+    status, _, _ = lbfgs.step(fun, st, H0=loss.prior_inverse_hessian(pms))
+    assert status == "ok"
+    assert np.max(np.abs(st.x)) < 1e-9 * np.max(np.abs(s0))
 
 
 def test_two_loop_equals_dense_bfgs_matrix():
