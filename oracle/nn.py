@@ -63,6 +63,48 @@ def stencil_gather_T(gv: np.ndarray, N: int) -> np.ndarray:
     return out
 
 
+def stencil_at(fields: np.ndarray, vox: np.ndarray) -> np.ndarray:
+    """The 81 inputs of the listed voxels only: [81][n], vox = int [n][3] (x, y, z).
+    Same order and periodic wrap as stencil_gather, for meshes too large to gather whole."""
+    N = fields.shape[1]
+    rows = []
+    for c in range(3):
+        for (ox, oy, oz) in STENCIL:
+            rows.append(fields[c][(vox[:, 0] + ox) % N, (vox[:, 1] + oy) % N, (vox[:, 2] + oz) % N])
+    return np.stack(rows)
+
+
+def mlp_at(fields: np.ndarray, vox: np.ndarray, weights: np.ndarray, M_scale: float) -> np.ndarray:
+    """The softplus network of Sec. 2 evaluated at the listed voxels: M [n]."""
+    W1, b1, W2, b2, w3, b3 = unpack(weights)
+    v = stencil_at(fields, vox)
+    z2 = relu(W2 @ relu(W1 @ v + b1[:, None]) + b2[:, None])
+    return M_scale * softplus(w3 @ z2 + b3)
+
+
+def mlp_backward_at(gM: np.ndarray, vox: np.ndarray, fields: np.ndarray, weights: np.ndarray,
+                    M_scale: float) -> np.ndarray:
+    """Gradient of sum_j gM[j] M(vox_j) w.r.t. the three input fields [3][N][N][N]:
+    the network adjoint for a mass gradient that is zero off the listed voxels."""
+    N = fields.shape[1]
+    W1, b1, W2, b2, w3, b3 = unpack(weights)
+    v = stencil_at(fields, vox)
+    a1 = W1 @ v + b1[:, None]
+    a2 = W2 @ relu(a1) + b2[:, None]
+    y = w3 @ relu(a2) + b3
+    gy = np.asarray(gM, np.float64) * M_scale * expit(y)
+    ga2 = np.outer(w3, gy) * (a2 > 0)
+    ga1 = (W2.T @ ga2) * (a1 > 0)
+    gv = W1.T @ ga1
+    out = np.zeros((3, N, N, N))
+    r = 0
+    for c in range(3):
+        for (ox, oy, oz) in STENCIL:
+            np.add.at(out[c], ((vox[:, 0] + ox) % N, (vox[:, 1] + oy) % N, (vox[:, 2] + oz) % N), gv[r])
+            r += 1
+    return out
+
+
 def mlp_forward(fields: np.ndarray, weights: np.ndarray, M_scale: float):
     """Per-voxel network; returns (M [N][N][N], cache for the adjoint)."""
     N = fields.shape[1]

@@ -197,8 +197,10 @@ def sort_by_cell(keys: np.ndarray, N: int):
 
 # ----------------------------------------------------------------------------- CIC
 
-def _cic_cells(x: np.ndarray, N: int):
-    w = np.mod(np.asarray(x, np.float64), N)
+def _cic_cells(x: np.ndarray, N: int, f32_wrap: bool = False):
+    # f32_wrap: the positions are float32 values and the cell index, an integer
+    # decision, is taken from their float32 wrap (wrap_f32), as the kernels do
+    w = wrap_f32(x, N).astype(np.float64) if f32_wrap else np.mod(np.asarray(x, np.float64), N)
     i = np.floor(w)
     d = w - i
     return i.astype(np.int64) % N, d
@@ -210,9 +212,9 @@ def _offset_index_weight(i, d, o, N):
     return idx, wts
 
 
-def paint(x: np.ndarray, N: int, mass=None) -> np.ndarray:
+def paint(x: np.ndarray, N: int, mass=None, f32_wrap: bool = False) -> np.ndarray:
     """Cloud-in-cell assignment (Sec. 2: fields are CIC-convolved onto the grid)."""
-    i, d = _cic_cells(x, N)
+    i, d = _cic_cells(x, N, f32_wrap)
     m = np.ones(x.shape[1]) if mass is None else np.asarray(mass, np.float64)
     rho = np.zeros(N**3)
     for o in OFFSETS:
@@ -221,10 +223,10 @@ def paint(x: np.ndarray, N: int, mass=None) -> np.ndarray:
     return rho.reshape(N, N, N)
 
 
-def readout(field: np.ndarray, x: np.ndarray) -> np.ndarray:
+def readout(field: np.ndarray, x: np.ndarray, f32_wrap: bool = False) -> np.ndarray:
     """CIC interpolation of a mesh field at particle positions (transpose of paint in mass)."""
     N = field.shape[0]
-    i, d = _cic_cells(x, N)
+    i, d = _cic_cells(x, N, f32_wrap)
     f = field.ravel()
     out = np.zeros(x.shape[1])
     for o in OFFSETS:
@@ -233,10 +235,10 @@ def readout(field: np.ndarray, x: np.ndarray) -> np.ndarray:
     return out
 
 
-def readout_grad(field: np.ndarray, x: np.ndarray) -> np.ndarray:
+def readout_grad(field: np.ndarray, x: np.ndarray, f32_wrap: bool = False) -> np.ndarray:
     """d/dx_a of readout(field, x): derivative of the CIC weights, [3][Np]."""
     N = field.shape[0]
-    i, d = _cic_cells(x, N)
+    i, d = _cic_cells(x, N, f32_wrap)
     f = field.ravel()
     out = np.zeros((3, x.shape[1]))
     for o in OFFSETS:

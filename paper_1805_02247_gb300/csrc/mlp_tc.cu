@@ -189,10 +189,10 @@ struct TileMap {
     int64_t N3;
 };
 
-template <bool BWD>
+template <bool BWD, bool TWO_NET>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
-             TileMap tm, int ntiles, int nsplit, float M_scale, int head, float a, float* __restrict__ M_out,
+             TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ M_out,
              float* __restrict__ gv, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     const uint32_t S_A = BWD ? S_A_BWD : S_A_FWD;
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(NT, 1)
             const bool in = gx < N && gy < N && gz < N;
             const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
             const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
-            if (head == 1) {
+            if (TWO_NET) {
                 // two-network head (Sec. 2.1): M = M_scale logistic(y, a) NNm(f), f = the voxel's own values
                 float f[3];
 #pragma unroll
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NT, 1)
                 for (int j = 0; j < 8; ++j) {
                     const int k = 24 * cb + 8 * h + j;
                     float v = a[j];
-                    if (head == 1 && k < NI && k % 27 == 13) v += gcen[(k / 27) * TM + row];  // mass network's input
+                    if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(k / 27) * TM + row];  // mass network's input
                     if (in && k < NI) gv[k * N3 + vox] = v;
                 }
             }
@@ -546,10 +546,14 @@ int mlp_tc_init(pmr_ctx* c) {
     PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img, img.data(), IMG_ALL, cudaMemcpyHostToDevice), "tc weights"));
     PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_err, sizeof(int)), "tc flag"));
     PMR_TRY(check_cuda(c, cudaMemset(c->tc_err, 0, sizeof(int)), "tc flag"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_FWD),
-                       "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BWD),
-                       "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_FWD), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_FWD), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_BWD), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_BWD), "smem attr"));
     return PMR_OK;
 }
 
@@ -564,9 +568,14 @@ int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit, float a)
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
     const int grid = std::min(ntiles, c->num_sms);
-    k_mlp_tc<false><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, reinterpret_cast<const float4*>(c->tc_img), m,
-                                                        ntiles, nsplit, (float)c->cfg.M_scale, c->cfg.head, a, M,
-                                                        nullptr, c->tc_err);
+    const float4* img = reinterpret_cast<const float4*>(c->tc_img);
+    const float Ms = (float)c->cfg.M_scale;
+    if (c->cfg.head == 1)
+        k_mlp_tc<false, true><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, img, m, ntiles, nsplit, Ms, a, M,
+                                                                  nullptr, c->tc_err);
+    else
+        k_mlp_tc<false, false><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, img, m, ntiles, nsplit, Ms, a, M,
+                                                                   nullptr, c->tc_err);
     return check_launch(c, "mlp_tc_fwd");
 }
 
@@ -574,9 +583,14 @@ int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nspli
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
     const int grid = std::min(ntiles, c->num_sms);
-    k_mlp_tc<true><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, reinterpret_cast<const float4*>(c->tc_img), m, ntiles,
-                                                       nsplit, (float)c->cfg.M_scale, c->cfg.head, a, nullptr, c->gv,
-                                                       c->tc_err);
+    const float4* img = reinterpret_cast<const float4*>(c->tc_img);
+    const float Ms = (float)c->cfg.M_scale;
+    if (c->cfg.head == 1)
+        k_mlp_tc<true, true><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, nullptr,
+                                                                 c->gv, c->tc_err);
+    else
+        k_mlp_tc<true, false><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, nullptr,
+                                                                  c->gv, c->tc_err);
     return check_launch(c, "mlp_tc_bwd");
 }
 

@@ -109,6 +109,27 @@ def edge_positions(n: int) -> np.ndarray:
     return np.stack([vals, np.roll(vals, 3), np.roll(vals, 7)]).astype(np.float32).reshape(3, k)
 
 
+def lognormal_density(n: int, seed: int, sigma: float = 1.0) -> np.ndarray:
+    """A float32 overdensity mesh with the one-sided, heavy-tailed values of an
+    evolved density: delta = exp(sigma g - sigma^2/2) - 1, g a unit Gaussian
+    field given short-range correlation by averaging each cell with its six
+    neighbours (periodic) and rescaling to unit variance."""
+    g = rng(seed).standard_normal((n, n, n))
+    c = g.copy()
+    for ax in range(3):
+        c += np.roll(g, 1, axis=ax) + np.roll(g, -1, axis=ax)
+    c /= c.std()
+    return (np.exp(sigma * c - 0.5 * sigma * sigma) - 1.0).astype(np.float32)
+
+
+def sample_voxels(n: int, count: int, seed: int) -> np.ndarray:
+    """int [count][3] voxel indices: random ones plus every corner of the box, so
+    periodic neighbours across each face are among them."""
+    r = rng(seed).integers(0, n, size=(count, 3))
+    corners = np.array([[x, y, z] for x in (0, n - 1) for y in (0, n - 1) for z in (0, n - 1)])
+    return np.concatenate([corners, r]).astype(np.int64)
+
+
 def gaussian_vector(shape, seed: int) -> np.ndarray:
     """N(0,1) float32 array of any shape (adjoint seeds, L-BFGS test vectors)."""
     return rng(seed).standard_normal(shape).astype(np.float32)

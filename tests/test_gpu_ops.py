@@ -54,12 +54,12 @@ def test_paint_parity_and_mass_conservation(N, np_):
     if np_ == 0:
         assert not rho.any()
         return
-    want = opm.paint(f32(x), N)
+    want = opm.paint(f32(x), N, f32_wrap=True)
     assert rel_l2(rho, want) <= FIELD_TOL
     assert abs(rho.sum(dtype=np.float64) - np_) <= 1e-6 * np_
     m = synth.gaussian_vector(np_, seed=6)
     rho_m = to_np(ctx.paint(to_dev(x), to_dev(m)))
-    assert rel_l2(rho_m, opm.paint(f32(x), N, mass=f32(m))) <= FIELD_TOL
+    assert rel_l2(rho_m, opm.paint(f32(x), N, mass=f32(m), f32_wrap=True)) <= FIELD_TOL
     # deterministic: same bits twice
     assert np.array_equal(rho, to_np(ctx.paint(to_dev(x))))
 
@@ -70,9 +70,9 @@ def test_readout_and_grad_parity():
     x = synth.uniform_positions(N, 5000, seed=7, lo=-N, hi=2 * N)
     g = synth.gaussian_vector((N, N, N), seed=8)
     r = to_np(ctx.readout(to_dev(g), to_dev(x)))
-    assert rel_l2(r, opm.readout(f32(g), f32(x))) <= FIELD_TOL
+    assert rel_l2(r, opm.readout(f32(g), f32(x), f32_wrap=True)) <= FIELD_TOL
     rg = to_np(ctx.readout_grad(to_dev(g), to_dev(x)))
-    assert rel_l2(rg, opm.readout_grad(f32(g), f32(x))) <= FIELD_TOL
+    assert rel_l2(rg, opm.readout_grad(f32(g), f32(x), f32_wrap=True)) <= FIELD_TOL
 
 
 @pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96])

@@ -184,7 +184,13 @@ def test_recon_step_follows_oracle_lbfgs(nn_path, later_loss_tol):
 
 
 def test_annealed_reconstruction_follows_oracle():
-    # two smoothing stages of Sec. 4.2 at one M0, three L-BFGS iterations each
+    # Sec. 4.2 annealing: residual smoothing 2 -> 1 -> 0 cells, then M0 1e9 -> 1e8,
+    # one L-BFGS iteration per stage, so every stage starts afresh from the last
+    # iterate (memory reset, new loss). A longer stay in one stage is not compared
+    # point by point: after a short backtracked first step the curvature pair
+    # amplifies float32 gradient rounding (recon_step's own test bounds that).
+    # Tolerance: on this problem the oracle's own four stage losses move by at
+    # most 2e-6 when its gradients carry 1e-6 relative noise.
     from oracle import anneal as oanneal
     from paper_1805_02247_gb300 import anneal
 
@@ -192,27 +198,26 @@ def test_annealed_reconstruction_follows_oracle():
     ctx, _ = context(N=N, L=L, nsteps=nsteps)
     setup, s0 = _problem(N, L, nsteps, amp=np.sqrt(0.1))
     data = _data(N, L, nsteps)
-    stages = anneal.smoothing_schedule([6.25, 3.125], 1e9)  # 2 and 1 cells
+    stages = [anneal.Stage(6.25, 1e9), anneal.Stage(3.125, 1e9), anneal.Stage(0.0, 1e9), anneal.Stage(0.0, 1e8)]
     s_dev = to_dev(s0)
-    hist = anneal.reconstruct(ctx, s_dev, to_dev(data), stages, max_iter=3)
+    hist = anneal.reconstruct(ctx, s_dev, to_dev(data), stages, max_iter=1)
     _, ohist = oanneal.reconstruct(s0, data, synth.xavier_weights(1), setup, oloss.LossSetup(),
-                                   [(st.R_sm, st.M0) for st in stages], max_iter=3)
-    # The first accepted step follows the oracle to the loss tolerance. Later
-    # points sit on a trajectory that amplifies float32 gradient rounding: on
-    # this problem the oracle itself moves by up to 2e-3 in the loss within six
-    # iterations when its gradient carries 1e-5 relative noise, so the stage
-    # losses are held to 3e-3.
-    assert hist[0]["loss"] == pytest.approx(ohist[0][0], rel=1e-5)
-    for si in range(2):
-        got = [r["loss"] for r in hist if r["stage"] == si]
-        want = ohist[si]
-        assert len(got) == len(want)
-        assert np.all(np.diff(got) < 0)  # each stage decreases its own loss
-        assert np.allclose(got, want, rtol=3e-3)
+                                   [(st.R_sm, st.M0) for st in stages], max_iter=1)
+    assert [r["stage"] for r in hist] == [0, 1, 2, 3]
+    got = [r["loss"] for r in hist]
+    want = [h[0] for h in ohist]
+    assert got[0] == pytest.approx(want[0], rel=1e-5)
+    assert np.allclose(got, want, rtol=1e-4)
+    # a longer stage keeps decreasing its own loss
+    more = anneal.reconstruct(ctx, s_dev, to_dev(data), [anneal.Stage(0.0, 1e8)], max_iter=4)
+    assert np.all(np.diff([r["loss"] for r in more]) < 0)
 
 
 def test_two_network_annealing_over_sharpness_follows_oracle():
-    # Sec. 4.2: the logistic sharpness a is annealed between stages (here 1 -> 2)
+    # Sec. 4.2: the logistic sharpness a is annealed between stages (1 -> 2),
+    # one iteration per stage. The two-network loss is steeper: under 1e-6
+    # relative gradient noise the oracle's second-stage loss moves by 6.4e-5
+    # (7.4e-5 under 1e-5), so it is held to 5e-4; the first to the loss tolerance.
     from oracle import anneal as oanneal
     from paper_1805_02247_gb300 import anneal
 
@@ -221,12 +226,9 @@ def test_two_network_annealing_over_sharpness_follows_oracle():
     setup, s0 = _problem(N, L, nsteps, amp=np.sqrt(0.1))
     data = _data(N, L, nsteps, head="two_net")
     stages = [anneal.Stage(6.25, 1e11, 1.0), anneal.Stage(6.25, 1e11, 2.0)]
-    s_dev = to_dev(s0)
-    hist = anneal.reconstruct(ctx, s_dev, to_dev(data), stages, max_iter=2)
+    hist = anneal.reconstruct(ctx, to_dev(s0), to_dev(data), stages, max_iter=1)
     _, ohist = oanneal.reconstruct(s0, data, synth.two_net_weights(1), setup, oloss.LossSetup(head="two_net"),
-                                   [(st.R_sm, st.M0, st.a) for st in stages], max_iter=2)
-    assert hist[0]["loss"] == pytest.approx(ohist[0][0], rel=1e-5)
-    for si in range(2):
-        got = [r["loss"] for r in hist if r["stage"] == si]
-        assert len(got) == len(ohist[si])
-        assert np.allclose(got, ohist[si], rtol=3e-3)  # trajectory tolerance, as above
+                                   [(st.R_sm, st.M0, st.a) for st in stages], max_iter=1)
+    got = [r["loss"] for r in hist]
+    assert got[0] == pytest.approx(ohist[0][0], rel=1e-5)
+    assert got[1] == pytest.approx(ohist[1][0], rel=5e-4)

@@ -292,3 +292,19 @@ def test_two_loop_equals_dense_bfgs_matrix():
         V = np.eye(n) - rho * np.outer(y, s)
         H = V.T @ H @ V + rho * np.outer(s, s)
     assert np.allclose(lbfgs.two_loop(g, S, Y), -H @ g, rtol=1e-12, atol=1e-12)
+
+
+def test_sampled_network_equals_full_network_at_those_voxels():
+    # the sampled forms used at full mesh size agree with the whole-mesh forms
+    N = 8
+    f = np.stack([synth.gaussian_vector((N, N, N), seed=s) for s in (71, 72, 73)]).astype(np.float64)
+    w = synth.xavier_weights(1).astype(np.float64)
+    vox = synth.sample_voxels(N, 40, seed=74)
+    M_full, _ = nn.mlp_forward(f, w, 1e12)
+    assert np.allclose(nn.mlp_at(f, vox, w, 1e12), M_full[vox[:, 0], vox[:, 1], vox[:, 2]], rtol=1e-13)
+    # sparse mass gradient (duplicates accumulate, as in the dense adjoint)
+    gM = np.zeros((N, N, N))
+    vals = synth.gaussian_vector(vox.shape[0], seed=75).astype(np.float64)
+    np.add.at(gM, (vox[:, 0], vox[:, 1], vox[:, 2]), vals)
+    dense = nn.mlp_backward(gM, f, w, 1e12)
+    assert np.allclose(nn.mlp_backward_at(vals, vox, f, w, 1e12), dense, rtol=1e-12, atol=1e-12 * np.abs(dense).max())
