@@ -145,7 +145,7 @@ def loss_and_grad(s, data_M, weights, pms: pm.PMSetup, ls: LossSetup, an: Anneal
     L_pri = prior(s, P)
     g_M = residual_grad(cache, pms, ls, an)
     g_delta = features_T(_head_backward(g_M, f, weights, ls, an.a), pms, ls)
-    g_s = pm.final_density_T(checkpoints, x_fin, g_delta, pms) + prior_grad(s, P)
+    g_s = pm.final_density_T(checkpoints, x_fin, g_delta, pms, s) + prior_grad(s, P)
     g_s[0, 0, 0] = 0
     return {"loss": L_pri + L_res, "prior": L_pri, "residual": L_res}, g_s
 

@@ -41,6 +41,7 @@ class PMSetup:
     om: float = cosmo.OMEGA_M
     sigma8: float = cosmo.SIGMA8
     gamma: float = cosmo.GAMMA_BBKS
+    lpt_order: int = 1  # 1: Zel'dovich initial conditions; 2: second-order LPT (Sec. 3)
 
 
 # ----------------------------------------------------------------------------- Fourier mesh
@@ -152,6 +153,84 @@ def za_ics(s: np.ndarray, setup: PMSetup):
     x = lattice(setup.N) + cosmo.D(setup.a0, setup.om) * psi
     p = cosmo.Gp(setup.a0, setup.om) * psi
     return x, p
+
+
+def hessian_multiplier(N: int, i: int, j: int) -> np.ndarray:
+    """k_i k_j / k^2: takes delta_k to the Fourier modes of d_i d_j phi with
+    lap phi = delta (phi_k = -delta_k / k^2). Zero at k = 0; for i != j also
+    zero where component i or j is the Nyquist frequency (an odd factor there)."""
+    ks, nyq = wavenumbers(N)
+    k2 = k_squared(N)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        m = ks[i] * ks[j] / k2
+    m = np.where(k2 == 0, 0.0, m)
+    if i != j:
+        m = np.where(nyq[i] | nyq[j], 0.0, m)
+    return m
+
+
+HESS_PAIRS = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+
+
+def lpt2_hessian(s: np.ndarray) -> np.ndarray:
+    """[6][N][N][N]: phi_xx, phi_yy, phi_zz, phi_xy, phi_xz, phi_yz of the
+    first-order potential (lap phi = delta, the linear field at a = 1)."""
+    N = s.shape[0]
+    return np.stack([irfft3(hessian_multiplier(N, i, j) * s) for (i, j) in HESS_PAIRS])
+
+
+def lpt2_source(H: np.ndarray) -> np.ndarray:
+    """Second-order source sum_{i<j} (phi_ii phi_jj - phi_ij^2) (textbook 2LPT)."""
+    xx, yy, zz, xy, xz, yz = H
+    return xx * yy + xx * zz + yy * zz - xy**2 - xz**2 - yz**2
+
+
+def lpt2_displacement(s: np.ndarray) -> np.ndarray:
+    """psi2 = grad phi2 with lap phi2 = the second-order source, [3][N^3] at a = 1:
+    psi2_k = -i k S_k / k^2 (odd multiplier with factor -1)."""
+    N = s.shape[0]
+    Sk = rfft3(lpt2_source(lpt2_hessian(s)))
+    return np.stack([irfft3(odd_multiplier(N, j, -1.0) * Sk).ravel() for j in range(3)])
+
+
+def lpt2_growth(setup: PMSetup):
+    """(D1, D2, Gp, Gp2) at a0: D2 = -3/7 D1^2 (the usual approximation, exact in
+    Einstein-de Sitter) and Gp2 = a^3 E dD2/da = -6/7 D1 Gp."""
+    D1 = cosmo.D(setup.a0, setup.om)
+    Gp = cosmo.Gp(setup.a0, setup.om)
+    return D1, -3.0 / 7.0 * D1 * D1, Gp, -6.0 / 7.0 * D1 * Gp
+
+
+def lpt_ics(s: np.ndarray, setup: PMSetup):
+    """Initial conditions of order setup.lpt_order at a0.
+    Order 2: x = q + D1 psi1 + D2 psi2, p = Gp psi1 + Gp2 psi2."""
+    if setup.lpt_order == 1:
+        return za_ics(s, setup)
+    D1, D2, Gp, Gp2 = lpt2_growth(setup)
+    psi1 = za_displacement(s)
+    psi2 = lpt2_displacement(s)
+    return lattice(setup.N) + D1 * psi1 + D2 * psi2, Gp * psi1 + Gp2 * psi2
+
+
+def lpt_ics_T(lam_x: np.ndarray, lam_p: np.ndarray, s: np.ndarray, setup: PMSetup) -> np.ndarray:
+    """Adjoint of lpt_ics at s: gradient w.r.t. the half-array entries of s."""
+    g = za_ics_T(lam_x, lam_p, setup)
+    if setup.lpt_order == 1:
+        return g
+    N = setup.N
+    D1, D2, Gp, Gp2 = lpt2_growth(setup)
+    mu = (D2 * lam_x + Gp2 * lam_p).reshape(3, N, N, N)
+    # transpose of S -> psi2_j: irfft(conj(m_j) rfft(.)) summed over j
+    acc = np.zeros((N, N, N // 2 + 1), dtype=np.complex128)
+    for j in range(3):
+        acc += np.conj(odd_multiplier(N, j, -1.0)) * rfft3(mu[j])
+    sigma = irfft3(acc)
+    xx, yy, zz, xy, xz, yz = lpt2_hessian(s)
+    gH = [sigma * (yy + zz), sigma * (xx + zz), sigma * (xx + yy),
+          -2.0 * sigma * xy, -2.0 * sigma * xz, -2.0 * sigma * yz]
+    for (i, j), gh in zip(HESS_PAIRS, gH):
+        g += hessian_multiplier(N, i, j) * irfft3_T(gh)
+    return g
 
 
 def za_ics_T(lam_x: np.ndarray, lam_p: np.ndarray, setup: PMSetup) -> np.ndarray:
@@ -301,7 +380,7 @@ def kdk_factors(setup: PMSetup):
 def pm_forward(s: np.ndarray, setup: PMSetup):
     """s(k) -> final positions. Returns (x_final, [x_i before step i], p_final)."""
     N = setup.N
-    x, p = za_ics(s, setup)
+    x, p = lpt_ics(s, setup)
     kick, drift = kdk_factors(setup)
     checkpoints = []
     for i in range(setup.nsteps):
@@ -312,7 +391,7 @@ def pm_forward(s: np.ndarray, setup: PMSetup):
     return x, checkpoints, p
 
 
-def pm_adjoint(checkpoints, lam_x: np.ndarray, lam_p: np.ndarray, setup: PMSetup) -> np.ndarray:
+def pm_adjoint(checkpoints, lam_x: np.ndarray, lam_p: np.ndarray, setup: PMSetup, s=None) -> np.ndarray:
     """Reverse mode of pm_forward: gradients at (x_final, p_final) -> gradient w.r.t. s.
 
     Each step's force field is recomputed from the stored positions.
@@ -333,7 +412,7 @@ def pm_adjoint(checkpoints, lam_x: np.ndarray, lam_p: np.ndarray, setup: PMSetup
         G = np.stack([kick[i] * paint(x, N, mass=lam_p[j]) for j in range(3)])
         g_delta = force_T(G, om)
         lam_x += readout_grad(g_delta / rho_bar, x)
-    return za_ics_T(lam_x, lam_p, setup)
+    return lpt_ics_T(lam_x, lam_p, s, setup)
 
 
 def final_density(s: np.ndarray, setup: PMSetup) -> np.ndarray:
@@ -341,9 +420,9 @@ def final_density(s: np.ndarray, setup: PMSetup) -> np.ndarray:
     return density(x, setup.N)
 
 
-def final_density_T(checkpoints, x_final: np.ndarray, g_delta: np.ndarray, setup: PMSetup) -> np.ndarray:
+def final_density_T(checkpoints, x_final: np.ndarray, g_delta: np.ndarray, setup: PMSetup, s=None) -> np.ndarray:
     """Gradient w.r.t. s of <g_delta, delta_final(s)>."""
     N = setup.N
     rho_bar = x_final.shape[1] / N**3
     lam_x = readout_grad(g_delta / rho_bar, x_final)
-    return pm_adjoint(checkpoints, lam_x, np.zeros_like(lam_x), setup)
+    return pm_adjoint(checkpoints, lam_x, np.zeros_like(lam_x), setup, s)

@@ -189,10 +189,10 @@ def test_loss_reduces_to_prior_when_noise_is_huge():
     assert np.allclose(g, loss.prior_grad(s, P), rtol=1e-9, atol=1e-20)
 
 
-@pytest.mark.parametrize("R_sm", [0.0, 4.0])
-def test_full_gradient_by_finite_differences(R_sm):
+@pytest.mark.parametrize("R_sm,lpt_order", [(0.0, 1), (4.0, 1), (4.0, 2)])
+def test_full_gradient_by_finite_differences(R_sm, lpt_order):
     N = 8
-    pms = pm.PMSetup(N=N, L=100.0, nsteps=2)
+    pms = pm.PMSetup(N=N, L=100.0, nsteps=2, lpt_order=lpt_order)
     ls = loss.LossSetup()
     an = loss.Anneal(R_sm=R_sm, M0=1e8)
     w = synth.xavier_weights(1)

@@ -216,3 +216,105 @@ def test_pm_adjoint_by_finite_differences(N, nsteps):
         eps = 1e-6
         fd = (f(s + eps * v) - f(s - eps * v)) / (2 * eps)
         assert rdot(grad, v) == pytest.approx(fd, rel=1e-6)
+
+
+# ----------------------------------------------------------------------------- 2LPT
+
+def test_lpt2_vanishes_for_a_plane_wave():
+    # one Fourier direction: only phi_xx is nonzero, the second-order source is
+    # zero, and 2LPT reduces to Zel'dovich (exact in 1D before shell crossing)
+    N = 16
+    _, s = _plane_wave(N, 0.5)
+    assert np.max(np.abs(pm.lpt2_displacement(s))) < 1e-12 * np.max(np.abs(pm.za_displacement(s)))
+    setup2 = pm.PMSetup(N=N, L=100.0, nsteps=1, lpt_order=2)
+    x2, p2 = pm.lpt_ics(s, setup2)
+    x1, p1 = pm.za_ics(s, setup2)
+    assert np.allclose(x2, x1, rtol=0, atol=1e-12) and np.allclose(p2, p1, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("axes", [(0, 1), (0, 2), (1, 2)])
+def test_lpt2_closed_form_for_a_product_of_two_cosines(axes):
+    # phi1 = A cos(a u) cos(b v) on two axes u, v (lap phi1 = delta): the source
+    # is A^2 a^2 b^2 (cos 2au + cos 2bv) / 2, so phi2 = -(A^2/8)(b^2 cos 2au +
+    # a^2 cos 2bv) and psi2 = grad phi2 = (A^2 a b / 4)(b sin 2au, a sin 2bv)
+    N = 16
+    u, v = axes
+    a, b = 2 * np.pi * 1 / N, 2 * np.pi * 2 / N
+    A = 0.7
+    q = pm.lattice(N)
+    phi = A * np.cos(a * q[u]) * np.cos(b * q[v])
+    s = pm.rfft3((-(a * a + b * b) * phi).reshape(N, N, N))
+    want = np.zeros((3, N ** 3))
+    want[u] = A * A * a * b / 4 * b * np.sin(2 * a * q[u])
+    want[v] = A * A * a * b / 4 * a * np.sin(2 * b * q[v])
+    assert np.allclose(pm.lpt2_displacement(s), want, rtol=0, atol=1e-12)
+
+
+def test_lpt2_source_on_a_diagonal_hessian_is_the_sum_of_pair_products():
+    H = np.zeros((6, 2, 2, 2))
+    H[0], H[1], H[2] = 2.0, 3.0, 5.0
+    assert np.allclose(pm.lpt2_source(H), 2 * 3 + 2 * 5 + 3 * 5)
+    H[3] = 1.0  # phi_xy enters squared with a minus sign
+    assert np.allclose(pm.lpt2_source(H), 31 - 1)
+
+
+def test_lpt_ics_adjoint_is_exact_for_the_quadratic_map():
+    # x(s) and p(s) are quadratic in s, so central differences are exact
+    N = 8
+    setup = pm.PMSetup(N=N, L=100.0, nsteps=1, lpt_order=2)
+    s = pm.linear_field(synth.white_noise(N, 0), setup)
+    rng = np.random.default_rng(12)
+    lx, lp = rng.standard_normal((3, N ** 3)), rng.standard_normal((3, N ** 3))
+    g = pm.lpt_ics_T(lx, lp, s, setup)
+    for _ in range(3):
+        v = pm.rfft3(rng.standard_normal((N, N, N))) * np.sqrt(pm.power_half(setup) / N ** 3)
+        eps = 0.1
+        xp, pp = pm.lpt_ics(s + eps * v, setup)
+        xm, pmm = pm.lpt_ics(s - eps * v, setup)
+        fd = (np.sum(lx * (xp - xm)) + np.sum(lp * (pp - pmm))) / (2 * eps)
+        assert rdot(g, v) == pytest.approx(fd, rel=1e-10)
+
+
+def test_lpt2_pm_adjoint_by_finite_differences():
+    N, nsteps = 8, 2
+    setup = pm.PMSetup(N=N, L=100.0, nsteps=nsteps, lpt_order=2)
+    s = pm.linear_field(synth.white_noise(N, 0), setup)
+    rng = np.random.default_rng(13)
+    g_delta = rng.standard_normal((N, N, N))
+    x_fin, cps, _ = pm.pm_forward(s, setup)
+    grad = pm.final_density_T(cps, x_fin, g_delta, setup, s)
+    f = lambda ss: float(np.sum(g_delta * pm.final_density(ss, setup)))
+    for _ in range(3):
+        v = pm.rfft3(rng.standard_normal((N, N, N))) * np.sqrt(pm.power_half(setup) / N ** 3)
+        v[0, 0, 0] = 0
+        eps = 1e-6
+        fd = (f(s + eps * v) - f(s - eps * v)) / (2 * eps)
+        assert rdot(grad, v) == pytest.approx(fd, rel=1e-6)
+
+
+def _f2_kernel(k1, k2):
+    # second-order kernel of Eulerian perturbation theory (Einstein-de Sitter)
+    a, b = np.linalg.norm(k1), np.linalg.norm(k2)
+    mu = k1 @ k2 / (a * b)
+    return 5 / 7 + 0.5 * mu * (a / b + b / a) + 2 / 7 * mu * mu
+
+
+@pytest.mark.parametrize("n1,n2", [((1, 0, 0), (0, 1, 0)), ((1, 0, 0), (1, 1, 0)), ((2, 1, 0), (0, 1, 1)),
+                                   ((1, 0, 0), (0, 0, 2))])
+def test_lpt2_density_has_the_second_order_kernel(n1, n2):
+    # delta_lin = A cos(k1 q) + B cos(k2 q): the density of the displaced lattice
+    # (a direct sum over particles, no mesh) has the cos((k1 + k2) x) amplitude
+    # D1^2 F2(k1, k2) A B at second order; Zel'dovich gives a different kernel
+    # (1/2 instead of 5/7 for perpendicular modes). The second-order part is the
+    # even part in the amplitude, (d(e) + d(-e)) / (2 e^2).
+    N = 16
+    q = pm.lattice(N)
+    k1, k2 = 2 * np.pi / N * np.array(n1, float), 2 * np.pi / N * np.array(n2, float)
+    A, B, eps = 1.0, 0.8, 1e-3
+    s = pm.rfft3((A * np.cos(k1 @ q) + B * np.cos(k2 @ q)).reshape(N, N, N))
+    setup = pm.PMSetup(N=N, L=100.0, nsteps=1, a0=0.5, lpt_order=2)
+    D1 = cosmo.D(setup.a0, setup.om)
+    kk = k1 + k2
+    d = [np.mean(np.exp(-1j * (kk @ pm.lpt_ics(e * s, setup)[0]))) for e in (eps, -eps)]
+    second = (d[0] + d[1]).real / 2 / eps ** 2
+    assert second / (D1 ** 2 * A * B / 2) == pytest.approx(_f2_kernel(k1, k2), rel=1e-5)
