@@ -72,6 +72,10 @@ typedef struct pmr_config {
                            1 = the paper's two networks (Sec. 2.1), M = M_scale *
                            logistic(y, a) * NNm(f), NNm = 3-20-10-1 ELU net on the voxel's
                            three fields; its 301 weights follow the 5661 of pmr_create */
+    int lpt_order;      /* initial conditions (Sec. 3): 1 = Zel'dovich; 2 = second-order LPT,
+                           x = q + D1 psi1 + D2 psi2, D2 = -3/7 D1^2, psi2 = grad phi2 with
+                           lap phi2 = sum_{i<j} (phi_ii phi_jj - phi_ij^2) of the first-order
+                           potential (lap phi = delta). Needs 12 more float32 meshes. */
 } pmr_config;
 
 /* Per-stage annealing parameters of Sec. 4.2. */
@@ -86,7 +90,8 @@ typedef struct pmr_ctx pmr_ctx;
 
 /* Fills *cfg with the defaults: N=32, L=100, nsteps=3, a0=0.1, omega_m=0.3175,
  * sigma8=0.8, Gamma=0.21, R_feat={1,2,4}, R_M=3, sigma_N2=0.25, mu_N=0,
- * f_eff=1, M_scale=1e12, lbfgs_m=10, lbfgs_tol=1e-3. */
+ * f_eff=1, M_scale=1e12, lbfgs_m=10, lbfgs_tol=1e-3, nn_path=0, head=0,
+ * lpt_order=1. */
 void pmr_default_config(pmr_config* cfg);
 
 /* Device bytes pmr_create() will allocate for this configuration (used to
@@ -215,6 +220,18 @@ int pmr_smooth(pmr_ctx* ctx, const float* in, double R, float* out);
  * displacement disp = x - q (q = the particle's lattice point, particle index
  * (ix N + iy) N + iz) and p, both float32 [3][N^3]. */
 int pmr_za_ics(pmr_ctx* ctx, const void* s_k, float* disp, float* p);
+
+/* Initial conditions of the configured order (lpt_order; Sec. 3). Order 1 is
+ * pmr_za_ics; order 2 adds D2 psi2 to the displacement and Gp2 psi2 to p,
+ * with D2 = -3/7 D1^2 and Gp2 = a^3 E dD2/da = -6/7 D1 G_p. Same layouts. */
+int pmr_lpt_ics(pmr_ctx* ctx, const void* s_k, float* disp, float* p);
+
+/* Adjoint of pmr_lpt_ics at s_k: grad_s_k = (d disp/ds)^T lam_x + (d p/ds)^T lam_p
+ * (c64 half array, overwritten). lam_x, lam_p: float32 [3][N^3]. The
+ * second-order term is quadratic in s, so its adjoint depends on s_k.
+ * With lpt_order == 2 both calls replace state pm_adjoint needs: the next
+ * pm_adjoint returns PMR_ESTATE until pm_forward runs again. */
+int pmr_lpt_ics_adjoint(pmr_ctx* ctx, const void* s_k, const float* lam_x, const float* lam_p, void* grad_s_k);
 
 /* Growth factors the stepping uses (float64, host): D(a), G_p(a), G_f(a). */
 int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* Gf);

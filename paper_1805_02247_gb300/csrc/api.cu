@@ -74,6 +74,7 @@ const char* validate(const pmr_config* cfg) {
     if (!(cfg->lbfgs_tol >= 0)) return "lbfgs_tol must be >= 0";
     if (cfg->nn_path < 0 || cfg->nn_path > 2) return "nn_path must be 0, 1 or 2";
     if (cfg->head < 0 || cfg->head > 1) return "head must be 0 or 1";
+    if (cfg->lpt_order < 1 || cfg->lpt_order > 2) return "lpt_order must be 1 or 2";
     return nullptr;
 }
 
@@ -119,6 +120,10 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->W : nullptr), sizeof(float) * kNW);
     alloc((void**)(c ? &c->power_tab : nullptr), sizeof(float) * (3 * (N / 2) * (N / 2) + 1));
     alloc((void**)(c ? &c->inv_power_tab : nullptr), sizeof(double) * (3 * (N / 2) * (N / 2) + 1));
+    if (cfg.lpt_order == 2) {
+        alloc((void**)(c ? &c->lpt_H : nullptr), sizeof(float) * 6 * N3);
+        alloc((void**)(c ? &c->lpt_G : nullptr), sizeof(float) * 6 * N3);
+    }
 }
 
 size_t lbfgs_bytes(const pmr_config& cfg) {
@@ -214,6 +219,7 @@ void pmr_default_config(pmr_config* cfg) {
     cfg->lbfgs_tol = 1e-3;
     cfg->nn_path = 0;
     cfg->head = 0;
+    cfg->lpt_order = 1;
 }
 
 size_t pmr_workspace_bytes(const pmr_config* cfg) {
@@ -248,6 +254,8 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
     const double om = cfg->omega_m;
     c->D0 = growth_D(cfg->a0, om);
     c->Gp0 = growth_Gp(cfg->a0, om);
+    c->D2_0 = -3.0 / 7.0 * c->D0 * c->D0;    // second-order growth, D2 = -3/7 D1^2
+    c->Gp2_0 = -6.0 / 7.0 * c->D0 * c->Gp0;  // a^3 E dD2/da
     const int n = cfg->nsteps;
     for (int i = 0; i < n; ++i) {
         const double ai = cfg->a0 + (1.0 - cfg->a0) * i / n, aj = cfg->a0 + (1.0 - cfg->a0) * (i + 1) / n;
@@ -540,6 +548,20 @@ int pmr_za_ics(pmr_ctx* c, const void* s_k, float* disp, float* mom) {
     PMR_TRY(check_ctx(c));
     if (!s_k || !disp || !mom) return fail(c, PMR_EINVAL, "NULL argument");
     return za_ics(c, (const float2*)s_k, disp, mom);
+}
+
+int pmr_lpt_ics(pmr_ctx* c, const void* s_k, float* disp, float* mom) {
+    PMR_TRY(check_ctx(c));
+    if (!s_k || !disp || !mom) return fail(c, PMR_EINVAL, "NULL argument");
+    if (c->cfg.lpt_order == 2) c->have_forward = false;  // replaces the Hessian pm_adjoint needs
+    return lpt_ics(c, (const float2*)s_k, disp, mom);
+}
+
+int pmr_lpt_ics_adjoint(pmr_ctx* c, const void* s_k, const float* lam_x, const float* lam_p, void* grad_s_k) {
+    PMR_TRY(check_ctx(c));
+    if (!s_k || !lam_x || !lam_p || !grad_s_k) return fail(c, PMR_EINVAL, "NULL argument");
+    if (c->cfg.lpt_order == 2) c->have_forward = false;
+    return lpt_adjoint(c, (const float2*)s_k, lam_x, lam_p, (float2*)grad_s_k, false);
 }
 
 int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* Gf) {

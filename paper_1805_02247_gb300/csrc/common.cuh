@@ -95,13 +95,14 @@ Radix make_radix(int n);
 bool radix_ok(int n);
 
 // Fourier-space multiplier applied inside the fused x-pass.
-enum MulType : int { MUL_ONE = 0, MUL_GAUSS = 1, MUL_ODD = 2, MUL_POWER = 3 };
+enum MulType : int { MUL_ONE = 0, MUL_GAUSS = 1, MUL_ODD = 2, MUL_POWER = 3, MUL_HESS = 4 };
 struct Mul {
     int type;     // MulType
     int j;        // component for MUL_ODD (0=x, 1=y, 2=z)
     float scale;  // overall factor
     float R2;     // Gaussian: R^2 in grid units
     int weighted; // multiply by the half-array weight w(kz) (2 interior, 1 on kz=0, N/2)
+    int i2;       // second component for MUL_HESS (k_j k_i2 / k^2)
 };
 
 struct FFTPlan {
@@ -145,6 +146,9 @@ struct pmr_ctx {
 
     // growth and stepping (host, float64)
     double D0 = 0, Gp0 = 0;
+    double D2_0 = 0, Gp2_0 = 0;  // second-order LPT growth at a0 (lpt_order == 2)
+    float* lpt_H = nullptr;      // [6][N^3] phi_xx, phi_yy, phi_zz, phi_xy, phi_xz, phi_yz of the last ICs
+    float* lpt_G = nullptr;      // [6][N^3] their adjoint
     std::vector<double> kick, drift;
 
     pmr::FFTPlan plan;
@@ -250,6 +254,8 @@ int conv_Nto1(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float
 int k_to_real(pmr_ctx* c, const float2* in, float* const* out, const Mul* mul, int nout);
 // nin real ins -> k-space out = sum_i mul_i * rfft(in_i)
 int real_to_k(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float2* out);
+// out += sum_i mul_i rfft(in_i)
+int real_to_k_add(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float2* out);
 
 // PM kernels (pm.cu) ------------------------------------------------------------
 // positions are either explicit absolute positions (lattice == false) or
@@ -266,6 +272,8 @@ int kick_drift(pmr_ctx* c, const float* F, const float* disp_in, float* disp_out
 int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
                     float drift);
 int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad);
+int lpt_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom);
+int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* lam_p, float2* grad, bool have_H);
 int pm_forward_impl(pmr_ctx* c, const float2* s_k);
 int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state
 int density_from(pmr_ctx* c, const float* disp, float* delta);

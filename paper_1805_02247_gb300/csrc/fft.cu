@@ -297,6 +297,7 @@ struct XFused {
     int nin, nout;
     int fwd;  // forward transform along x before the multiply
     int inv;  // inverse transform along x after it
+    int acc;  // add the result to out instead of storing it
     Mul mul[3];
     const float* ptab;  // sqrt power table for MUL_POWER
 };
@@ -312,6 +313,14 @@ __device__ __forceinline__ float2 apply_mul(const Mul& m, float2 v, int nx, int 
     const float kx = twopi_n * nx, ky = twopi_n * ny, kzf = twopi_n * kz;
     const float k2 = kx * kx + ky * ky + kzf * kzf;
     if (m.type == MUL_GAUSS) return cscale(v, f * expf(-0.5f * k2 * m.R2));
+    if (m.type == MUL_HESS) {
+        // k_j k_i2 / k^2, zero at k = 0; for j != i2 also zero where either
+        // component is the Nyquist frequency (an odd factor there)
+        const int na = (m.j == 0) ? nx : (m.j == 1) ? ny : kz;
+        const int nb = (m.i2 == 0) ? nx : (m.i2 == 1) ? ny : kz;
+        if (n2 == 0 || (m.j != m.i2 && (2 * abs(na) == N || 2 * abs(nb) == N))) return make_float2(0.f, 0.f);
+        return cscale(v, f * (twopi_n * na) * (twopi_n * nb) / k2);
+    }
     // MUL_ODD: i k_j / k^2, zero at k = 0 and on the Nyquist plane of component j
     const int nj = (m.j == 0) ? nx : (m.j == 1) ? ny : kz;
     if (n2 == 0 || 2 * abs(nj) == N) return make_float2(0.f, 0.f);
@@ -357,7 +366,10 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
             if (p.inv) R = smem_fft<true, true>(A, B, s_tw, rd, kCols, kCols, 1);
             for (int t = threadIdx.x; t < T; t += blockDim.x) {
                 int m = t / kCols, c = t % kCols;
-                if (c < cw) p.out[o][base + m * g.es + c] = R[t];
+                if (c < cw) {
+                    float2* d = p.out[o] + base + m * g.es + c;
+                    *d = p.acc ? cadd(*d, R[t]) : R[t];
+                }
             }
             __syncthreads();
         }
@@ -379,7 +391,10 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
         if (p.inv) R = smem_fft<true, true>(K, A, s_tw, rd, kCols, kCols, 1);
         for (int t = threadIdx.x; t < T; t += blockDim.x) {
             int m = t / kCols, c = t % kCols;
-            if (c < cw) p.out[0][base + m * g.es + c] = R[t];
+            if (c < cw) {
+                float2* d = p.out[0] + base + m * g.es + c;
+                *d = p.acc ? cadd(*d, R[t]) : R[t];
+            }
         }
     }
 }
@@ -536,6 +551,19 @@ int real_to_k(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float
     const float2* ins[3] = {ks[0], ks[1], ks[2]};
     float2* outs[1] = {out};
     return launch_x_fused(c, make_x(ins, nin, outs, 1, mul, nin, true, false, c));
+}
+
+int real_to_k_add(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float2* out) {
+    float2* ks[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
+    for (int i = 0; i < nin; ++i) {
+        PMR_TRY(launch_z_r2c(c, in[i], ks[i]));
+        PMR_TRY(launch_col(c, ks[i], ks[i], geom_y(c), false));
+    }
+    const float2* ins[3] = {ks[0], ks[1], ks[2]};
+    float2* outs[1] = {out};
+    XFused p = make_x(ins, nin, outs, 1, mul, nin, true, false, c);
+    p.acc = 1;
+    return launch_x_fused(c, p);
 }
 
 }  // namespace pmr

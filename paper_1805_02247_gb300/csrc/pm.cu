@@ -494,6 +494,43 @@ __global__ void k_za_adj_combine(const float* __restrict__ lx, const float* __re
     if (i < n) out[i] = D0 * lx[i] + Gp0 * lp[i];
 }
 
+// ----------------------------------------------------------------------------- second-order LPT
+
+// S = phi_xx phi_yy + phi_xx phi_zz + phi_yy phi_zz - phi_xy^2 - phi_xz^2 - phi_yz^2
+__global__ void k_lpt2_source(const float* __restrict__ H, int64_t n, float* __restrict__ S) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float xx = H[i], yy = H[n + i], zz = H[2 * n + i];
+    const float xy = H[3 * n + i], xz = H[4 * n + i], yz = H[5 * n + i];
+    S[i] = xx * yy + xx * zz + yy * zz - xy * xy - xz * xz - yz * yz;
+}
+
+// disp holds psi1 on entry: disp = D1 psi1 + D2 psi2, mom = Gp psi1 + Gp2 psi2
+__global__ void k_lpt2_finish(float* __restrict__ disp, const float* __restrict__ psi2, float* __restrict__ mom,
+                              int64_t n, float D1, float D2, float Gp, float Gp2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a = disp[i], b = psi2[i];
+    disp[i] = D1 * a + D2 * b;
+    mom[i] = Gp * a + Gp2 * b;
+}
+
+// adjoint of the source: dS/dphi_ii = sum of the other two diagonal entries,
+// dS/dphi_ij = -2 phi_ij (i < j); G = sigma * dS/dH
+__global__ void k_lpt2_hess_grad(const float* __restrict__ sigma, const float* __restrict__ H, int64_t n,
+                                 float* __restrict__ G) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float sg = sigma[i];
+    const float xx = H[i], yy = H[n + i], zz = H[2 * n + i];
+    G[i] = sg * (yy + zz);
+    G[n + i] = sg * (xx + zz);
+    G[2 * n + i] = sg * (xx + yy);
+    G[3 * n + i] = -2.f * sg * H[3 * n + i];
+    G[4 * n + i] = -2.f * sg * H[4 * n + i];
+    G[5 * n + i] = -2.f * sg * H[5 * n + i];
+}
+
 }  // namespace
 
 // ============================================================================= host wrappers
@@ -593,6 +630,78 @@ int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
     return check_launch(c, "za_finish");
 }
 
+namespace {
+// phi_ij of the first-order potential (lap phi = delta = irfft(s)) into lpt_H
+int lpt2_hessian(pmr_ctx* c, const float2* s_k) {
+    static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int h = 0; h < 2; ++h) {
+        Mul mul[3];
+        float* outs[3];
+        for (int t = 0; t < 3; ++t) {
+            const int* pr = pairs[3 * h + t];
+            mul[t] = Mul{MUL_HESS, pr[0], 1.0f, 0.f, 0, pr[1]};
+            outs[t] = c->lpt_H + (int64_t)(3 * h + t) * c->N3;
+        }
+        PMR_TRY(k_to_real(c, s_k, outs, mul, 3));
+    }
+    return PMR_OK;
+}
+}  // namespace
+
+// Sec. 3 initial conditions of order cfg.lpt_order; the Hessian of the
+// first-order potential stays in lpt_H for the adjoint.
+int lpt_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
+    if (c->cfg.lpt_order != 2) return za_ics(c, s_k, disp, mom);
+    const int64_t N3 = c->N3;
+    Mul mul[3];
+    for (int j = 0; j < 3; ++j) mul[j] = Mul{MUL_ODD, j, 1.0f, 0.f, 0};
+    float* psi1[3] = {disp, disp + N3, disp + 2 * N3};
+    PMR_TRY(k_to_real(c, s_k, psi1, mul, 3));
+    PMR_TRY(lpt2_hessian(c, s_k));
+    k_lpt2_source<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->lpt_H, N3, c->delta);
+    PMR_TRY(check_launch(c, "lpt2_source"));
+    // psi2 = grad phi2, lap phi2 = S: psi2_k = -i k S_k / k^2
+    for (int j = 0; j < 3; ++j) mul[j] = Mul{MUL_ODD, j, -1.0f, 0.f, 0};
+    float* psi2[3] = {c->F, c->F + N3, c->F + 2 * N3};
+    PMR_TRY(conv_1toN(c, c->delta, psi2, mul, 3));
+    k_lpt2_finish<<<nblocks(3 * N3, kT), kT, 0, c->stream>>>(disp, c->F, mom, 3 * N3, (float)c->D0, (float)c->D2_0,
+                                                              (float)c->Gp0, (float)c->Gp2_0);
+    return check_launch(c, "lpt2_finish");
+}
+
+// Adjoint of lpt_ics at s_k (grad overwritten). have_H: lpt_H already holds
+// the Hessian of s_k (it does after lpt_ics on the same s_k).
+int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* lam_p, float2* grad, bool have_H) {
+    PMR_TRY(za_adjoint(c, lam_x, lam_p, grad));
+    if (c->cfg.lpt_order != 2) return PMR_OK;
+    const int64_t N3 = c->N3;
+    if (!have_H) PMR_TRY(lpt2_hessian(c, s_k));
+    // mu = D2 lam_x + Gp2 lam_p; sigma = sum_j irfft(conj(-i k_j / k^2) rfft(mu_j))
+    k_za_adj_combine<<<nblocks(3 * N3, kT), kT, 0, c->stream>>>(lam_x, lam_p, c->F, 3 * N3, (float)c->D2_0,
+                                                                 (float)c->Gp2_0);
+    PMR_TRY(check_launch(c, "lpt2_adj_combine"));
+    Mul mul[3];
+    for (int j = 0; j < 3; ++j) mul[j] = Mul{MUL_ODD, j, 1.0f, 0.f, 0};
+    const float* mu[3] = {c->F, c->F + N3, c->F + 2 * N3};
+    PMR_TRY(conv_Nto1(c, mu, mul, 3, c->delta));
+    k_lpt2_hess_grad<<<nblocks(N3, kT), kT, 0, c->stream>>>(c->delta, c->lpt_H, N3, c->lpt_G);
+    PMR_TRY(check_launch(c, "lpt2_hess_grad"));
+    // grad += sum_ij (k_i k_j / k^2) (w / N^3) rfft(G_ij)
+    static const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    const float inv_n3 = (float)(1.0 / (double)N3);
+    for (int h = 0; h < 2; ++h) {
+        Mul hm[3];
+        const float* gin[3];
+        for (int t = 0; t < 3; ++t) {
+            const int* pr = pairs[3 * h + t];
+            hm[t] = Mul{MUL_HESS, pr[0], inv_n3, 0.f, 1, pr[1]};
+            gin[t] = c->lpt_G + (int64_t)(3 * h + t) * N3;
+        }
+        PMR_TRY(real_to_k_add(c, gin, hm, 3, grad));
+    }
+    return PMR_OK;
+}
+
 int kick_drift(pmr_ctx* c, const float* F, const float* din, float* dout, float* mom, float kick, float drift) {
     k_kick_drift<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
     return check_launch(c, "kick_drift");
@@ -619,7 +728,7 @@ int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad)
 
 int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
     const int64_t N3 = c->N3;
-    PMR_TRY(za_ics(c, s_k, c->disp, c->mom));
+    PMR_TRY(lpt_ics(c, s_k, c->disp, c->mom));
     const float om15 = (float)(1.5 * c->cfg.omega_m);
     Mul fm[3];
     for (int j = 0; j < 3; ++j) fm[j] = Mul{MUL_ODD, j, om15, 0.f, 0};
@@ -657,7 +766,7 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
         PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
         PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
     }
-    return za_adjoint(c, c->lam_x, c->lam_p, grad);
+    return lpt_adjoint(c, nullptr, c->lam_x, c->lam_p, grad, true);  // Hessian kept by pm_forward
 }
 
 }  // namespace pmr

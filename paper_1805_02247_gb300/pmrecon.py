@@ -33,6 +33,7 @@ class Config(ctypes.Structure):
         ("R_feat", ctypes.c_double * 3), ("R_M", ctypes.c_double), ("sigma_N2", ctypes.c_double),
         ("mu_N", ctypes.c_double), ("f_eff", ctypes.c_double), ("M_scale", ctypes.c_double),
         ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double), ("nn_path", ctypes.c_int), ("head", ctypes.c_int),
+        ("lpt_order", ctypes.c_int),
     ]
 
 
@@ -69,6 +70,8 @@ _SIGS = {
     "pmr_force": (ctypes.c_int, [_P, _P, _P]),
     "pmr_smooth": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "pmr_za_ics": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pmr_lpt_ics": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pmr_lpt_ics_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pmr_growth": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "pmr_lbfgs_direction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _I64, _P]),
     "pmr_power_spectra": (ctypes.c_int, [_P, _P, _P, _P]),
@@ -292,6 +295,18 @@ class Context:
         mom = torch.empty_like(disp)
         self._check(self._lib.pmr_za_ics(self._h, _ptr(s), _ptr(disp), _ptr(mom)))
         return disp, mom
+
+    def lpt_ics(self, s: torch.Tensor):
+        """Initial conditions of the configured order: (displacement, momentum), [3][N^3] each."""
+        disp = torch.empty(3, self.N**3, device=self.device, dtype=torch.float32)
+        mom = torch.empty_like(disp)
+        self._check(self._lib.pmr_lpt_ics(self._h, _ptr(s), _ptr(disp), _ptr(mom)))
+        return disp, mom
+
+    def lpt_ics_adjoint(self, s: torch.Tensor, lam_x: torch.Tensor, lam_p: torch.Tensor) -> torch.Tensor:
+        g = self.half()
+        self._check(self._lib.pmr_lpt_ics_adjoint(self._h, _ptr(s), _ptr(lam_x), _ptr(lam_p), _ptr(g)))
+        return g
 
     def lbfgs_direction(self, g: torch.Tensor, S: torch.Tensor, Y: torch.Tensor) -> torch.Tensor:
         d = torch.empty_like(g)

@@ -96,6 +96,18 @@ def test_linear_field_and_za_full(job):
     assert rel_l2(to_np(mom), p_want) <= FIELD_TOL
 
 
+def test_lpt2_ics_full():
+    # second-order LPT initial conditions at the full mesh (their own context)
+    ctx, _ = context(N=N, L=L, nsteps=1, lpt_order=2)
+    setup = opm.PMSetup(N=N, L=L, nsteps=1, lpt_order=2)
+    s = f32(opm.linear_field(f32(synth.white_noise(N, 0)), setup))
+    disp, mom = ctx.lpt_ics(to_dev(s))
+    x_want, p_want = opm.lpt_ics(s, setup)
+    assert rel_l2(to_np(disp), x_want - opm.lattice(N)) <= FIELD_TOL
+    assert rel_l2(to_np(mom), p_want) <= FIELD_TOL
+    ctx.close()
+
+
 def _tile_block():
     # one corner of the mesh: whole network tiles (2 x 4 x 16 voxels) and the
     # periodic neighbours across three faces

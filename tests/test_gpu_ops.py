@@ -152,3 +152,28 @@ def test_power_spectra_parity(N, L):
     # deterministic: identical bits on a second call
     again = [t.numpy() for t in ctx.power_spectra(to_dev(a), to_dev(b))]
     assert all(np.array_equal(x, y) for x, y in zip(got, again))
+
+
+@pytest.mark.parametrize("N,L", [(32, 100.0), (24, 400.0)])
+def test_lpt2_ics_and_adjoint_parity(N, L):
+    # second-order LPT initial conditions (Sec. 3) and their adjoint
+    ctx, _ = context(N=N, L=L, lpt_order=2)
+    setup = opm.PMSetup(N=N, L=L, nsteps=3, lpt_order=2)
+    s = f32(opm.linear_field(f32(synth.white_noise(N, 0)), setup))
+    disp, mom = ctx.lpt_ics(to_dev(s))
+    x_want, p_want = opm.lpt_ics(s, setup)
+    assert rel_l2(to_np(disp), x_want - opm.lattice(N)) <= FIELD_TOL
+    assert rel_l2(to_np(mom), p_want) <= FIELD_TOL
+    lx = f32(synth.gaussian_vector((3, N ** 3), seed=31))
+    lp = f32(synth.gaussian_vector((3, N ** 3), seed=32))
+    g = to_np(ctx.lpt_ics_adjoint(to_dev(s), to_dev(lx), to_dev(lp)))
+    assert rel_l2(g, opm.lpt_ics_T(lx, lp, s, setup)) <= GRAD_TOL
+
+
+def test_lpt_order_one_is_zeldovich():
+    N = 16
+    ctx, _ = context(N=N, L=100.0, lpt_order=1)
+    s = f32(opm.linear_field(f32(synth.white_noise(N, 0)), opm.PMSetup(N=N, L=100.0, nsteps=1)))
+    d1, p1 = ctx.lpt_ics(to_dev(s))
+    d0, p0 = ctx.za_ics(to_dev(s))
+    assert torch.equal(d1, d0) and torch.equal(p1, p0)

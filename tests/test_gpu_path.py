@@ -45,6 +45,24 @@ def test_pm_adjoint_parity(N, L, nsteps):
     assert rel_l2(got, want) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("N,L,nsteps", [(16, 100.0, 2), (24, 400.0, 5)])
+def test_pm_forward_and_adjoint_parity_with_2lpt(N, L, nsteps):
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, lpt_order=2)
+    setup = opm.PMSetup(N=N, L=L, nsteps=nsteps, lpt_order=2)
+    _, s = _problem(N, L, nsteps)
+    delta = to_np(ctx.pm_forward(to_dev(s)))
+    x_fin, cps, _ = opm.pm_forward(s, setup)
+    assert rel_l2(delta, opm.density(x_fin, N)) <= FIELD_TOL
+    g = synth.gaussian_vector((N, N, N), seed=22)
+    got = to_np(ctx.pm_adjoint(to_dev(g)))
+    assert rel_l2(got, opm.final_density_T(cps, x_fin, f32(g), setup, s)) <= GRAD_TOL
+    # computing initial conditions on their own replaces the state the adjoint needs
+    from paper_1805_02247_gb300.pmrecon import PMRError
+    ctx.lpt_ics(to_dev(s))
+    with pytest.raises(PMRError, match="ESTATE"):
+        ctx.pm_adjoint(to_dev(g))
+
+
 def test_pm_adjoint_needs_forward():
     from paper_1805_02247_gb300.pmrecon import PMRError
     ctx, _ = context(N=8)
@@ -135,6 +153,19 @@ def test_loss_and_grad_parity(N, L, nsteps, R_sm, M0):
     assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
     assert parts[1] == pytest.approx(want["prior"], rel=FIELD_TOL)
     assert parts[2] == pytest.approx(want["residual"], rel=FIELD_TOL)
+    assert rel_l2(to_np(g), gwant) <= GRAD_TOL
+
+
+def test_loss_and_grad_parity_with_2lpt():
+    N, L, nsteps, R_sm, M0 = 16, 50.0, 2, 4.0, 1e8
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, lpt_order=2)
+    setup = opm.PMSetup(N=N, L=L, nsteps=nsteps, lpt_order=2)
+    _, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
+    want, gwant = oloss.loss_and_grad(s, data, synth.xavier_weights(1), setup, oloss.LossSetup(),
+                                      oloss.Anneal(R_sm=R_sm, M0=M0))
+    assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
     assert rel_l2(to_np(g), gwant) <= GRAD_TOL
 
 
