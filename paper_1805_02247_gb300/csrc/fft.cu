@@ -399,6 +399,291 @@ __global__ void __launch_bounds__(kThreads) k_x_fused(XFused p, ColGeom g, Radix
     }
 }
 
+// ----------------------------------------------------------------------------- register column FFTs
+//
+// Column passes for N = N1 N2 with both factors small: a block takes 16
+// adjacent columns (one 128-byte line per row) and each 1D transform runs as
+// two rounds of small DFTs held in registers, with one transpose through
+// shared memory in between (the four-step decomposition):
+//   forward order:  x[N2 n1 + n2]  --DFT_N1 over n1, x W^(n2 k1), DFT_N2 over n2-->  X[k1 + N1 k2]
+//   inverse order:  X[k1 + N1 k2]  --DFT_N2 over k2, x W^(n2 k1), DFT_N1 over k1-->  x[n2 + N2 n1]
+// Either order computes a DFT of either sign. A thread owns one column and a
+// set of n2 (rows N2 n1 + n2) or of k1 (rows k1 + N1 k2), so every global
+// access of a warp is two full 128-byte rows and no index needs a division.
+
+constexpr int kRC = 16;  // columns per tile
+
+// R-point DFT in registers, R = 2^a 3^b: X[k + s q] = sum_j W_R^(jk) S_j[k] W_r^(jq),
+// S_j the s-point DFT of x[r m + j]. W_R^u = tw[u * TWS] (tw = W_N table).
+template <int R, bool INV, int TWS>
+__device__ __forceinline__ void dft_reg(float2* v, const float2* tw) {
+    if constexpr (R == 2 || R == 3 || R == 4) {
+        dft<R, INV>(v);
+    } else if constexpr (R > 4) {
+        constexpr int r = (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 3;
+        constexpr int s = R / r;
+        float2 sub[r][s];
+#pragma unroll
+        for (int j = 0; j < r; ++j)
+#pragma unroll
+            for (int m = 0; m < s; ++m) sub[j][m] = v[r * m + j];
+#pragma unroll
+        for (int j = 0; j < r; ++j) dft_reg<s, INV, TWS * r>(sub[j], tw);
+#pragma unroll
+        for (int k = 0; k < s; ++k) {
+            float2 t[r];
+#pragma unroll
+            for (int j = 0; j < r; ++j) {
+                if (j == 0 || k == 0) {
+                    t[j] = sub[j][k];
+                } else {
+                    float2 w = tw[j * k * TWS];
+                    if (INV) w.y = -w.y;
+                    t[j] = cmul(sub[j][k], w);
+                }
+            }
+            dft<r, INV>(t);
+#pragma unroll
+            for (int q = 0; q < r; ++q) v[k + s * q] = t[q];
+        }
+    }
+}
+
+template <int N1_, int N2_>
+struct Reg {
+    static constexpr int N1 = N1_, N2 = N2_, N = N1 * N2;
+    static constexpr int G = N1 < N2 ? N1 : N2;  // threads per column
+    static constexpr int T = kRC * G;            // block size
+    static constexpr int A1 = N2 / G;            // n2 values per thread
+    static constexpr int A2 = N1 / G;            // k1 values per thread
+    static_assert(N1 % G == 0 && N2 % G == 0, "factors must divide");
+    static constexpr int E = N / G;              // complex values per thread
+    // twiddles + transpose buffer (plain pass); + kept k-space tile (fused pass)
+    static constexpr size_t smem_col() { return sizeof(float2) * (size_t)(N + N * kRC); }
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(N + 2 * N * kRC); }
+};
+
+// S[k1][n2][c]
+template <class RG>
+__device__ __forceinline__ int sidx(int k1, int n2, int c) {
+    return (k1 * RG::N2 + n2) * kRC + c;
+}
+
+// x[N2 n1 + n2] (thread owns n2 = g + G a) -> X[k1 + N1 k2] (thread owns k1 = g + G a)
+template <class RG, bool INV>
+__device__ __forceinline__ void four_step_fwd(float2 (&v1)[RG::A1][RG::N1], float2 (&v2)[RG::A2][RG::N2], float2* S,
+                                              const float2* tw, int c, int g) {
+    constexpr int N1 = RG::N1, N2 = RG::N2, G = RG::G;
+#pragma unroll
+    for (int a = 0; a < RG::A1; ++a) {
+        const int n2 = g + G * a;
+        dft_reg<N1, INV, N2>(v1[a], tw);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 v = v1[a][k1];
+            if (k1 > 0) {
+                float2 w = tw[n2 * k1];
+                if (INV) w.y = -w.y;
+                v = cmul(v, w);
+            }
+            S[sidx<RG>(k1, n2, c)] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RG::A2; ++a) {
+        const int k1 = g + G * a;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v2[a][n2] = S[sidx<RG>(k1, n2, c)];
+        dft_reg<N2, INV, N1>(v2[a], tw);
+    }
+    __syncthreads();  // S free again
+}
+
+// X[k1 + N1 k2] (thread owns k1) -> x[n2 + N2 n1] (thread owns n2)
+template <class RG, bool INV>
+__device__ __forceinline__ void four_step_inv(float2 (&v2)[RG::A2][RG::N2], float2 (&v1)[RG::A1][RG::N1], float2* S,
+                                              const float2* tw, int c, int g) {
+    constexpr int N1 = RG::N1, N2 = RG::N2, G = RG::G;
+#pragma unroll
+    for (int a = 0; a < RG::A2; ++a) {
+        const int k1 = g + G * a;
+        dft_reg<N2, INV, N1>(v2[a], tw);
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            float2 v = v2[a][n2];
+            if (n2 > 0 && k1 > 0) {
+                float2 w = tw[n2 * k1];
+                if (INV) w.y = -w.y;
+                v = cmul(v, w);
+            }
+            S[sidx<RG>(k1, n2, c)] = v;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RG::A1; ++a) {
+        const int n2 = g + G * a;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v1[a][k1] = S[sidx<RG>(k1, n2, c)];
+        dft_reg<N1, INV, N2>(v1[a], tw);
+    }
+    __syncthreads();
+}
+
+// rows N2 n1 + n2 of the thread's n2 set
+template <class RG>
+__device__ __forceinline__ void load_n2(float2 (&v1)[RG::A1][RG::N1], const float2* in, int64_t base, int64_t es,
+                                        bool ok, int g) {
+#pragma unroll
+    for (int a = 0; a < RG::A1; ++a)
+#pragma unroll
+        for (int n1 = 0; n1 < RG::N1; ++n1)
+            v1[a][n1] = ok ? in[base + (int64_t)(RG::N2 * n1 + g + RG::G * a) * es] : make_float2(0.f, 0.f);
+}
+
+// rows k1 + N1 k2 of the thread's k1 set
+template <class RG>
+__device__ __forceinline__ void load_k1(float2 (&v2)[RG::A2][RG::N2], const float2* in, int64_t base, int64_t es,
+                                        bool ok, int g) {
+#pragma unroll
+    for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+        for (int k2 = 0; k2 < RG::N2; ++k2)
+            v2[a][k2] = ok ? in[base + (int64_t)(g + RG::G * a + RG::N1 * k2) * es] : make_float2(0.f, 0.f);
+}
+
+__device__ __forceinline__ void put(float2* d, float2 v, bool acc) { *d = acc ? cadd(*d, v) : v; }
+
+// Plain y- or x-pass (no multiplier); in-place safe (the tile is read before any write).
+template <class RG, bool INV>
+__global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out, ColGeom geo,
+                                                     const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    float2* s_tw = sm;
+    float2* S = s_tw + RG::N;
+    load_twiddles(s_tw, tw, RG::N);
+    const int c = threadIdx.x % kRC, g = threadIdx.x / kRC;
+    const int c0 = blockIdx.x * kRC;
+    const bool ok = c0 + c < geo.ncols;
+    const int64_t base = (int64_t)blockIdx.y * geo.os + c0 + c;
+    float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
+    load_n2<RG>(v1, in, base, geo.es, ok, g);
+    __syncthreads();  // twiddles
+    four_step_fwd<RG, INV>(v1, v2, S, s_tw, c, g);
+    if (ok)
+#pragma unroll
+        for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+            for (int k2 = 0; k2 < RG::N2; ++k2)
+                out[base + (int64_t)(g + RG::G * a + RG::N1 * k2) * geo.es] = v2[a][k2];
+}
+
+// x-pass with multipliers, same contract as k_x_fused. MODE 0: one input,
+// one output; 1: one input, several outputs; 2: several inputs, one output.
+template <class RG, int MODE>
+__global__ void __launch_bounds__(RG::T, 65536 / (RG::T * 128)) k_x_reg(XFused p, ColGeom geo,
+                                                                      const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int N = RG::N;
+    float2* s_tw = sm;
+    float2* S = s_tw + N;
+    load_twiddles(s_tw, tw, N);
+    const int c = threadIdx.x % kRC, g = threadIdx.x / kRC;
+    const int c0 = blockIdx.x * kRC;
+    const bool ok = c0 + c < geo.ncols;
+    const int kz = c0 + c;
+    const int oy = blockIdx.y;
+    const int ny = (2 * oy <= N) ? oy : oy - N;
+    const int64_t base = (int64_t)oy * geo.os + c0 + c;
+    __syncthreads();  // twiddles
+
+    float2* Kb = S + N * kRC;  // kept k-space tile: value e of thread t at Kb[e * T + t]
+    float2 v1[RG::A1][RG::N1];
+    auto to_k = [&](const float2* src, float2 (&dst)[RG::A2][RG::N2]) {
+        if (p.fwd) {
+            load_n2<RG>(v1, src, base, geo.es, ok, g);
+            four_step_fwd<RG, false>(v1, dst, S, s_tw, c, g);
+        } else {
+            load_k1<RG>(dst, src, base, geo.es, ok, g);
+        }
+    };
+    auto mul_into = [&](const Mul& m, const float2 (&src)[RG::A2][RG::N2], float2 (&dst)[RG::A2][RG::N2], bool add) {
+#pragma unroll
+        for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+            for (int k2 = 0; k2 < RG::N2; ++k2) {
+                const int mx = g + RG::G * a + RG::N1 * k2;
+                const int nx = (2 * mx <= N) ? mx : mx - N;
+                // padding columns (kz > N/2) stay zero and never index the power table
+                const float2 v = ok ? apply_mul(m, src[a][k2], nx, ny, kz, N, p.ptab) : make_float2(0.f, 0.f);
+                dst[a][k2] = add ? cadd(dst[a][k2], v) : v;
+            }
+    };
+    auto emit = [&](float2 (&R)[RG::A2][RG::N2], float2* dst) {
+        if (p.inv) {
+            four_step_inv<RG, true>(R, v1, S, s_tw, c, g);
+            if (ok)
+#pragma unroll
+                for (int a = 0; a < RG::A1; ++a)
+#pragma unroll
+                    for (int n1 = 0; n1 < RG::N1; ++n1)
+                        put(dst + base + (int64_t)(g + RG::G * a + RG::N2 * n1) * geo.es, v1[a][n1], p.acc);
+        } else if (ok) {
+#pragma unroll
+            for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                for (int k2 = 0; k2 < RG::N2; ++k2)
+                    put(dst + base + (int64_t)(g + RG::G * a + RG::N1 * k2) * geo.es, R[a][k2], p.acc);
+        }
+    };
+
+    float2 X[RG::A2][RG::N2];
+    if constexpr (MODE == 0) {
+        to_k(p.in[0], X);
+        mul_into(p.mul[0], X, X, false);
+        emit(X, p.out[0]);
+    } else if constexpr (MODE == 1) {
+        to_k(p.in[0], X);
+        {
+#pragma unroll
+            for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                for (int k2 = 0; k2 < RG::N2; ++k2) Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x] = X[a][k2];
+#pragma unroll 1
+            for (int o = 0; o < p.nout; ++o) {
+#pragma unroll
+                for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                    for (int k2 = 0; k2 < RG::N2; ++k2) X[a][k2] = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
+                mul_into(p.mul[o], X, X, false);
+                emit(X, p.out[o]);
+            }
+        }
+    } else {
+        float2 acc[RG::A2][RG::N2];
+#pragma unroll 1
+        for (int i = 0; i < p.nin; ++i) {
+            to_k(p.in[i], X);
+            mul_into(p.mul[i], X, acc, i > 0);
+        }
+        emit(acc, p.out[0]);
+    }
+}
+
+// Tile shapes of the register path: N -> (N1, N2); other N use the shared-memory Stockham kernels.
+template <class F>
+bool with_reg(int N, F f) {
+    switch (N) {
+        case 64: f(Reg<8, 8>{}); return true;
+        case 128: f(Reg<16, 8>{}); return true;
+        case 192: f(Reg<8, 24>{}); return true;
+        case 256: f(Reg<16, 16>{}); return true;
+        case 512: f(Reg<16, 32>{}); return true;
+        default: return false;
+    }
+}
+
 size_t smem_z(int N, bool c2r) {
     int M = N / 2, ld = M + 1;
     return sizeof(float2) * (size_t)(M + N + (c2r ? 3 : 2) * kRows * ld);
@@ -424,15 +709,32 @@ int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
 }
 
 int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
-    dim3 grid(nblocks(g.ncols, kCols), c->N);
-    if (inv) k_col<true><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
-    else k_col<false><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
+    bool done = with_reg(c->N, [&](auto rg) {
+        using RG = decltype(rg);
+        dim3 grid(nblocks(g.ncols, kRC), c->N);
+        if (inv) k_col_reg<RG, true><<<grid, RG::T, RG::smem_col(), c->stream>>>(in, out, g, c->plan.twN);
+        else k_col_reg<RG, false><<<grid, RG::T, RG::smem_col(), c->stream>>>(in, out, g, c->plan.twN);
+    });
+    if (!done) {
+        dim3 grid(nblocks(g.ncols, kCols), c->N);
+        if (inv) k_col<true><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
+        else k_col<false><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
+    }
     return check_launch(c, "col_pass");
 }
 
 int launch_x_fused(pmr_ctx* c, const XFused& p) {
-    dim3 grid(nblocks(c->P, kCols), c->N);
-    k_x_fused<<<grid, kThreads, smem_col(c->N, 3), c->stream>>>(p, geom_x(c), c->plan.rN, c->plan.twN);
+    bool done = with_reg(c->N, [&](auto rg) {
+        using RG = decltype(rg);
+        dim3 grid(nblocks(c->P, kRC), c->N);
+        if (p.nin > 1) k_x_reg<RG, 2><<<grid, RG::T, RG::smem(), c->stream>>>(p, geom_x(c), c->plan.twN);
+        else if (p.nout > 1) k_x_reg<RG, 1><<<grid, RG::T, RG::smem(), c->stream>>>(p, geom_x(c), c->plan.twN);
+        else k_x_reg<RG, 0><<<grid, RG::T, RG::smem(), c->stream>>>(p, geom_x(c), c->plan.twN);
+    });
+    if (!done) {
+        dim3 grid(nblocks(c->P, kCols), c->N);
+        k_x_fused<<<grid, kThreads, smem_col(c->N, 3), c->stream>>>(p, geom_x(c), c->plan.rN, c->plan.twN);
+    }
     // distinct names per variant: their algorithmic bytes differ
     static const char* names[2][2][4] = {
         {{"x_mul_1", "x_mul_1", "x_mul_2", "x_mul_3"}, {"x_inv_1", "x_inv_1", "x_inv_2", "x_inv_3"}},
@@ -483,6 +785,18 @@ int fft_init(pmr_ctx* c) {
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, false)), "smem attr"));
+    int rc = PMR_OK;
+    with_reg(N, [&](auto rg) {
+        using RG = decltype(rg);
+        const int sz = (int)RG::smem();
+        for (cudaError_t e : {cudaFuncSetAttribute(k_col_reg<RG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
+                              cudaFuncSetAttribute(k_col_reg<RG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
+                              cudaFuncSetAttribute(k_x_reg<RG, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
+                              cudaFuncSetAttribute(k_x_reg<RG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
+                              cudaFuncSetAttribute(k_x_reg<RG, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)})
+            if (rc == PMR_OK) rc = check_cuda(c, e, "smem attr");
+    });
+    PMR_TRY(rc);
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, true)), "smem attr"));
     return PMR_OK;
 }

@@ -75,8 +75,9 @@ def test_readout_and_grad_parity():
     assert rel_l2(rg, opm.readout_grad(f32(g), f32(x), f32_wrap=True)) <= FIELD_TOL
 
 
-@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96])
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96, 128, 192])
 def test_rfft_irfft_parity(N):
+    # 64, 128, 192 (and 256, 512) take the register four-step column passes
     ctx, _ = context(N=N)
     f = synth.gaussian_vector((N, N, N), seed=N)
     k = to_np(ctx.rfft(to_dev(f)))
@@ -88,8 +89,8 @@ def test_rfft_irfft_parity(N):
     assert rel_l2(got, opm.irfft3(f32(u))) <= FIELD_TOL
 
 
-def test_force_and_smooth_parity():
-    N = 32
+@pytest.mark.parametrize("N", [32, 64, 128])
+def test_force_and_smooth_parity(N):
     ctx, cfg = context(N=N, L=100.0)
     d = synth.gaussian_vector((N, N, N), seed=11)
     F = to_np(ctx.force(to_dev(d)))
