@@ -449,10 +449,12 @@ __device__ __forceinline__ void dft_reg(float2* v, const float2* tw) {
     }
 }
 
+constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
 template <int N1_, int N2_>
 struct Reg {
     static constexpr int N1 = N1_, N2 = N2_, N = N1 * N2;
-    static constexpr int G = N1 < N2 ? N1 : N2;  // threads per column
+    static constexpr int G = cgcd(N1, N2);       // threads per column
     static constexpr int T = kRC * G;            // block size
     static constexpr int A1 = N2 / G;            // n2 values per thread
     static constexpr int A2 = N1 / G;            // k1 values per thread
@@ -684,6 +686,200 @@ bool with_reg(int N, F f) {
     }
 }
 
+// ----------------------------------------------------------------------------- register z passes
+//
+// Rows of N reals are M = N/2 complex points z_m = x_2m + i x_2m+1. A block
+// stages R rows in shared memory with coalesced loads, runs the M-point
+// transform of each row as the four-step order above (G threads per row,
+// one transpose), and applies the real-to-complex split (or its inverse) from
+// shared memory, so global reads and writes are whole rows.
+
+template <class RG>
+struct ZReg {
+    static constexpr int M = RG::N, G = RG::G;
+    static constexpr int R = (128 / G) < 8 ? 8 : 128 / G;  // rows per block
+    static constexpr int T = R * G;
+    static constexpr int LDA = M + 8;                       // row pitch of the staging buffer
+    static constexpr int LDS = RG::N1 * (RG::N2 + 1);       // row pitch of the transpose buffer
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(M + 2 * M + R * (LDA + 1) + R * LDS); }
+};
+
+// four-step M-point transform of row r (natural order in A -> natural order in A)
+template <class RG, bool INV>
+__device__ __forceinline__ void row_fft(float2* A, float2* S, const float2* tw, int g) {
+    constexpr int N1 = RG::N1, N2 = RG::N2, G = RG::G;
+    float2 v1[RG::A1][N1];
+#pragma unroll
+    for (int a = 0; a < RG::A1; ++a) {
+        const int n2 = g + G * a;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v1[a][n1] = A[N2 * n1 + n2];
+        dft_reg<N1, INV, N2>(v1[a], tw);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 v = v1[a][k1];
+            if (k1 > 0) {
+                float2 w = tw[n2 * k1];
+                if (INV) w.y = -w.y;
+                v = cmul(v, w);
+            }
+            S[k1 * (N2 + 1) + n2] = v;
+        }
+    }
+    __syncthreads();
+    float2 v2[RG::A2][N2];
+#pragma unroll
+    for (int a = 0; a < RG::A2; ++a) {
+        const int k1 = g + G * a;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) v2[a][n2] = S[k1 * (N2 + 1) + n2];
+        dft_reg<N2, INV, N1>(v2[a], tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) A[k1 + N1 * k2] = v2[a][k2];
+    }
+    __syncthreads();
+}
+
+template <class RG>
+__global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restrict__ in, float2* __restrict__ out,
+                                                             int64_t nrows, const float2* __restrict__ twM,
+                                                             const float2* __restrict__ twN) {
+    using Z = ZReg<RG>;
+    constexpr int M = Z::M, N = 2 * M, P = M + 1;
+    extern __shared__ float2 sm[];
+    float2* s_twM = sm;
+    float2* s_twN = s_twM + M;
+    float2* A = s_twN + N;                    // [R][LDA + 1]
+    float2* S = A + Z::R * (Z::LDA + 1);      // [R][LDS]
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * Z::R;
+    const int rows = (int)min((int64_t)Z::R, nrows - row0);
+    for (int t = tid; t < M; t += Z::T) s_twM[t] = twM[t];
+    for (int t = tid; t < N; t += Z::T) s_twN[t] = twN[t];
+    const float2* src = reinterpret_cast<const float2*>(in + row0 * N);
+    {
+        // every load of the thread in flight before the first shared-memory store
+        constexpr int LD = (Z::R * M + Z::T - 1) / Z::T;
+        float2 v[LD];
+#pragma unroll
+        for (int q = 0; q < LD; ++q) {
+            const int t = tid + q * Z::T, r = t / M;
+            v[q] = (t < Z::R * M && r < rows) ? src[t] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < LD; ++q) {
+            const int t = tid + q * Z::T, r = t / M, m = t - r * M;
+            if (t < Z::R * M) A[r * (Z::LDA + 1) + m] = v[q];
+        }
+    }
+    __syncthreads();
+    const int r = tid / Z::G, g = tid - r * Z::G;
+    row_fft<RG, false>(A + r * (Z::LDA + 1), S + r * Z::LDS, s_twM, g);
+    // X_k = E_k + exp(-2 pi i k / N) O_k from Z_k and conj(Z_(M-k))
+    for (int t = tid; t < Z::R * P; t += Z::T) {
+        const int rr = t / P, k = t - rr * P;
+        if (rr >= rows) continue;
+        const float2* Zr = A + rr * (Z::LDA + 1);
+        float2 zk = Zr[k == M ? 0 : k];
+        float2 zc = Zr[k == 0 ? 0 : M - k];
+        zc.y = -zc.y;
+        float2 e = cscale(cadd(zk, zc), 0.5f);
+        float2 dd = csub(zk, zc);
+        float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
+        out[(row0 + rr) * P + k] = cadd(e, cmul(s_twN[k], o));
+    }
+}
+
+template <class RG>
+__global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restrict__ in, float* __restrict__ out,
+                                                             int64_t nrows, float scale, const float2* __restrict__ twM,
+                                                             const float2* __restrict__ twN) {
+    using Z = ZReg<RG>;
+    constexpr int M = Z::M, N = 2 * M, P = M + 1;
+    extern __shared__ float2 sm[];
+    float2* s_twM = sm;
+    float2* s_twN = s_twM + M;
+    float2* A = s_twN + N;                    // [R][LDA + 1]: the P inputs, then z
+    float2* S = A + Z::R * (Z::LDA + 1);      // [R][LDS]
+    const int tid = threadIdx.x;
+    const int64_t row0 = (int64_t)blockIdx.x * Z::R;
+    const int rows = (int)min((int64_t)Z::R, nrows - row0);
+    for (int t = tid; t < M; t += Z::T) s_twM[t] = twM[t];
+    for (int t = tid; t < N; t += Z::T) s_twN[t] = twN[t];
+    const float2* src = in + row0 * P;
+    {
+        constexpr int LD = (Z::R * P + Z::T - 1) / Z::T;
+        float2 v[LD];
+#pragma unroll
+        for (int q = 0; q < LD; ++q) {
+            const int t = tid + q * Z::T, r = t / P;
+            v[q] = (t < Z::R * P && r < rows) ? src[t] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < LD; ++q) {
+            const int t = tid + q * Z::T, r = t / P, k = t - r * P;
+            if (t < Z::R * P) A[r * (Z::LDA + 1) + k] = v[q];
+        }
+    }
+    __syncthreads();
+    // z_k = E_k + i O_k with E, O from X_k and conj(X_(M-k)); the pairs (k, M-k)
+    // are updated by one thread so the row can be rewritten in place
+    for (int t = tid; t < Z::R * (M / 2 + 1); t += Z::T) {
+        const int rr = t / (M / 2 + 1), k = t - rr * (M / 2 + 1);
+        float2* Xr = A + rr * (Z::LDA + 1);
+        const int kc = M - k;
+        float2 xk = Xr[k], xc = Xr[kc];
+        if (k == 0) {  // X_0 and X_M: imaginary parts carry nothing for a real signal
+            xk.y = 0.f;
+            xc.y = 0.f;
+        }
+        float2 zk, zc;
+        {
+            float2 c = xc;
+            c.y = -c.y;
+            float2 e = cscale(cadd(xk, c), 0.5f);
+            float2 w = s_twN[k];
+            w.y = -w.y;  // exp(+2 pi i k / N)
+            float2 o = cmul(cscale(csub(xk, c), 0.5f), w);
+            zk = make_float2(e.x - o.y, e.y + o.x);  // e + i o
+        }
+        if (kc != k && kc < M) {
+            float2 c = xk;
+            c.y = -c.y;
+            float2 e = cscale(cadd(xc, c), 0.5f);
+            float2 w = s_twN[kc];
+            w.y = -w.y;
+            float2 o = cmul(cscale(csub(xc, c), 0.5f), w);
+            zc = make_float2(e.x - o.y, e.y + o.x);
+            Xr[kc] = zc;
+        }
+        Xr[k] = zk;
+    }
+    __syncthreads();
+    const int r = tid / Z::G, g = tid - r * Z::G;
+    row_fft<RG, true>(A + r * (Z::LDA + 1), S + r * Z::LDS, s_twM, g);
+    float2* dst = reinterpret_cast<float2*>(out + row0 * N);
+    const float sc = scale * 2.0f / (float)N;
+    for (int t = tid; t < Z::R * M; t += Z::T) {
+        const int rr = t / M, m = t - rr * M;
+        if (rr < rows) dst[(int64_t)rr * M + m] = cscale(A[rr * (Z::LDA + 1) + m], sc);
+    }
+}
+
+// Row transform shapes: N -> M = N/2 = N1 N2.
+template <class F>
+bool with_zreg(int N, F f) {
+    switch (N) {
+        case 64: f(Reg<8, 4>{}); return true;
+        case 128: f(Reg<8, 8>{}); return true;
+        case 192: f(Reg<8, 12>{}); return true;
+        case 256: f(Reg<16, 8>{}); return true;
+        case 384: f(Reg<8, 24>{}); return true;
+        case 512: f(Reg<16, 16>{}); return true;
+        default: return false;
+    }
+}
+
 size_t smem_z(int N, bool c2r) {
     int M = N / 2, ld = M + 1;
     return sizeof(float2) * (size_t)(M + N + (c2r ? 3 : 2) * kRows * ld);
@@ -695,16 +891,28 @@ ColGeom geom_x(const pmr_ctx* c) { return ColGeom{c->N, c->P, (int64_t)c->N * c-
 
 int launch_z_r2c(pmr_ctx* c, const float* in, float2* out) {
     int64_t nrows = (int64_t)c->N * c->N;
-    k_z_r2c<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, false), c->stream>>>(in, out, nrows, c->N, c->plan.rM,
-                                                                                c->plan.twM, c->plan.twN);
+    bool done = with_zreg(c->N, [&](auto rg) {
+        using Z = ZReg<decltype(rg)>;
+        k_z_r2c_reg<decltype(rg)><<<nblocks(nrows, Z::R), Z::T, Z::smem(), c->stream>>>(in, out, nrows, c->plan.twM,
+                                                                                       c->plan.twN);
+    });
+    if (!done)
+        k_z_r2c<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, false), c->stream>>>(in, out, nrows, c->N, c->plan.rM,
+                                                                                    c->plan.twM, c->plan.twN);
     return check_launch(c, "z_r2c");
 }
 
 int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
     int64_t nrows = (int64_t)c->N * c->N;
     float scale = (float)(1.0 / ((double)c->N * c->N));
-    k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
-                                                                               c->plan.rM, c->plan.twM, c->plan.twN);
+    bool done = with_zreg(c->N, [&](auto rg) {
+        using Z = ZReg<decltype(rg)>;
+        k_z_c2r_reg<decltype(rg)><<<nblocks(nrows, Z::R), Z::T, Z::smem(), c->stream>>>(in, out, nrows, scale,
+                                                                                       c->plan.twM, c->plan.twN);
+    });
+    if (!done)
+        k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
+                                                                                   c->plan.rM, c->plan.twM, c->plan.twN);
     return check_launch(c, "z_c2r");
 }
 
@@ -786,6 +994,13 @@ int fft_init(pmr_ctx* c) {
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, false)), "smem attr"));
     int rc = PMR_OK;
+    with_zreg(N, [&](auto rg) {
+        using Z = ZReg<decltype(rg)>;
+        const int sz = (int)Z::smem();
+        for (cudaError_t e : {cudaFuncSetAttribute(k_z_r2c_reg<decltype(rg)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
+                              cudaFuncSetAttribute(k_z_c2r_reg<decltype(rg)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)})
+            if (rc == PMR_OK) rc = check_cuda(c, e, "smem attr");
+    });
     with_reg(N, [&](auto rg) {
         using RG = decltype(rg);
         const int sz = (int)RG::smem();
