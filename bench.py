@@ -263,13 +263,15 @@ def _time_evals(ctx, s, data, steps, M0=None):
 
 def extras(dev, steps):
     """The same workload through the other configured paths (one context at a
-    time): the paper's two-network head, second-order LPT ICs, the plain-TF32
-    network, the L-BFGS iteration of recon_step, and the two-point statistics."""
+    time): the paper's two-network head, second-order LPT ICs, the plain-TF32,
+    bf16 and CUDA-core networks, the L-BFGS iteration of recon_step, and the
+    two-point statistics."""
     import torch
 
     out = {}
     for key, kw, M0 in (("two_network_head", {"head": 1}, 1e11), ("lpt2_ics", {"lpt_order": 2}, None),
-                        ("nn_tf32", {"nn_path": 1}, None), ("nn_fp32_cuda_cores", {"nn_path": 2}, None)):
+                        ("nn_tf32", {"nn_path": 1}, None), ("nn_bf16", {"nn_path": 3}, None),
+                        ("nn_fp32_cuda_cores", {"nn_path": 2}, None)):
         ctx, s, data, s_true = _setup_job(dev, **kw)
         ms = _time_evals(ctx, s, data, steps, M0)
         out[key] = {"value": 1e3 / ms, "unit": UNIT, "ms_per_eval": ms, "config": kw}

@@ -67,7 +67,8 @@ typedef struct pmr_config {
     double lbfgs_tol;   /* relative loss decrease that counts as converged (Sec. 4.3: 1e-3) */
     int nn_path;        /* network arithmetic: 0 = tensor cores (tcgen05), each operand split
                            into two TF32 parts, float32 accuracy (default); 1 = tensor cores,
-                           plain TF32 (faster, ~1e-3 relative); 2 = float32 CUDA cores */
+                           plain TF32 (~1e-3 relative); 2 = float32 CUDA cores; 3 = tensor
+                           cores with bfloat16 operands and float32 accumulation (~3e-3) */
     int head;           /* 0 = one network with a softplus output, M = M_scale ln(1 + e^y);
                            1 = the paper's two networks (Sec. 2.1), M = M_scale *
                            logistic(y, a) * NNm(f), NNm = 3-20-10-1 ELU net on the voxel's

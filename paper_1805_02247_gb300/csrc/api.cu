@@ -72,7 +72,7 @@ const char* validate(const pmr_config* cfg) {
     if (!std::isfinite(cfg->mu_N) || !std::isfinite(cfg->f_eff)) return "mu_N and f_eff must be finite";
     if (cfg->lbfgs_m < 1 || cfg->lbfgs_m > 64) return "lbfgs_m must be 1..64";
     if (!(cfg->lbfgs_tol >= 0)) return "lbfgs_tol must be >= 0";
-    if (cfg->nn_path < 0 || cfg->nn_path > 2) return "nn_path must be 0, 1 or 2";
+    if (cfg->nn_path < 0 || cfg->nn_path > 3) return "nn_path must be 0, 1, 2 or 3";
     if (cfg->head < 0 || cfg->head > 1) return "head must be 0 or 1";
     if (cfg->lpt_order < 1 || cfg->lpt_order > 2) return "lpt_order must be 1 or 2";
     return nullptr;

@@ -162,6 +162,7 @@ struct pmr_ctx {
     uint32_t* shell_off = nullptr;
     double* shell_out = nullptr;
     float* tc_img = nullptr;    // tensor-core operand images of the weights (TF32 head + tail)
+    float* tc_img_bf = nullptr; // the same as bfloat16
     int* tc_err = nullptr;      // set by a tensor-core kernel whose barrier wait timed out
     int num_sms = 0;
 

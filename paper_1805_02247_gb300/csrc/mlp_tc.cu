@@ -32,7 +32,7 @@ constexpr int OFF_B1 = H1 * NI, OFF_W2 = OFF_B1 + H1, OFF_B2 = OFF_W2 + H2 * H1,
               OFF_B3 = OFF_W3 + H2;
 
 constexpr int TM = 128;           // voxels per tile = MMA M = TMEM lanes
-constexpr int K1 = 88, N1 = 64;   // layer 1 (81 -> 50, padded)
+constexpr int N1 = 64;            // layer 1 (81 -> 50, padded; K1 per precision below)
 constexpr int K2 = 64, N2 = 32;   // layer 2 (50 -> 30, padded)
 constexpr int K3 = 32, NB3 = 64;  // backward layer 2: g_a2 -> g_a1 (B = W2)
 constexpr int K4 = 64, NB4 = 96;  // backward layer 1: g_a1 -> g_v  (B = W1)
@@ -45,38 +45,50 @@ constexpr int HALO = 3 * HX * HY * HZ;
 // TMEM columns
 constexpr uint32_t COL_D1 = 0, COL_D2 = 64, COL_D3 = 96, COL_D4 = 160;
 
-// Byte offset of element (r, k) in an R-row, K-major, no-swizzle operand image:
-// k-steps of 8 (32 bytes of TF32) are sub-images of R*32 bytes; inside one,
-// core matrix (row group r/8, K chunk (k/4)%2) sits at 256*(r/8) + 128*chunk.
-// So the K-direction core-matrix stride (LBO) is 128 B and the 8-row-group
-// stride (SBO) is 256 B. Read either way round, every access of one k-step
-// stays inside its R*32-byte sub-image.
-__host__ __device__ constexpr uint32_t img_off(int R, int r, int k) {
-    return (uint32_t)((k >> 3) * (R * 32) + (r >> 3) * 256 + ((k >> 2) & 1) * 128 + (r & 7) * 16 + (k & 3) * 4);
-}
-constexpr uint32_t img_bytes(int R, int K) { return (uint32_t)(R * K * 4); }
-
-// shared-memory map (bytes); weight images first, in the order of the global image
-constexpr uint32_t SZ_B1 = img_bytes(N1, K1), SZ_B2 = img_bytes(N2, K2), SZ_B3 = img_bytes(NB3, K3),
-                   SZ_B4 = img_bytes(NB4, K4);
-constexpr uint32_t S_B1 = 0;                  // hi, lo
-constexpr uint32_t S_B2 = S_B1 + 2 * SZ_B1;   // hi, lo
-constexpr uint32_t S_VEC = S_B2 + 2 * SZ_B2;  // b1[64], b2[32], w3[32], b3[4], mass network[301]
-constexpr uint32_t VEC_MASS = 160;             // float offset of the mass-network weights
-constexpr uint32_t SZ_VEC = 1920;              // 4 * (160 + 301) rounded up to 128 B
-constexpr uint32_t S_B3 = S_VEC + SZ_VEC;     // backward only
-constexpr uint32_t S_B4 = S_B3 + 2 * SZ_B3;
-constexpr uint32_t IMG_FWD = S_B3;            // bytes of the image the forward copies
-constexpr uint32_t IMG_ALL = S_B4 + 2 * SZ_B4;
-constexpr uint32_t SZ_A = img_bytes(TM, K1);  // largest A operand (hi or lo)
-constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
+constexpr uint32_t VEC_MASS = 160;  // float offset of the mass-network weights in the vector block
+constexpr uint32_t SZ_VEC = 1920;    // b1[64], b2[32], w3[32], b3[4], mass network[301]: 4 * 461 rounded to 128 B
 constexpr int HALO_PER = (HALO + NT - 1) / NT;  // halo values each thread loads
-// halo, partials, g_y, centre-value gradients, stencil offsets, barrier + TMEM slot
-constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * 3 * TM + 4 * K1 + 64;
-constexpr uint32_t SMEM_FWD = S_A_FWD + 2 * SZ_A + SZ_TAIL;
-constexpr uint32_t SMEM_BWD = S_A_BWD + 2 * SZ_A + SZ_TAIL;
-static_assert(SMEM_BWD <= 232448, "shared memory budget");
-static_assert((S_B2 | S_VEC | S_B3 | S_B4 | S_A_FWD | S_A_BWD | SZ_A) % 128 == 0, "128-byte aligned regions");
+
+// Operand precision. BF = false: float32 split into TF32 head and tail parts
+// (kind::tf32, K = 8 per instruction); BF = true: one bfloat16 part
+// (kind::f16 with bf16 inputs and float32 accumulation, K = 16). Either way a
+// k-step is 32 bytes of a row, so the layout below is the same in bytes.
+//
+// Byte offset of element (r, k) in an R-row, K-major, no-swizzle operand image:
+// k-steps are sub-images of R*32 bytes; inside one, core matrix (row group r/8,
+// 16-byte K chunk) sits at 256*(r/8) + 128*chunk. So the K-direction
+// core-matrix stride (LBO) is 128 B and the 8-row-group stride (SBO) 256 B.
+// Every access of one k-step stays inside its R*32-byte sub-image.
+template <bool BF>
+struct Lay {
+    static constexpr int ES = BF ? 2 : 4;    // bytes per element
+    static constexpr int KS = 32 / ES;       // K per instruction
+    static constexpr int EC = 16 / ES;       // elements per 16-byte core-matrix row
+    static constexpr int NP = BF ? 1 : 2;    // parts per operand (head, tail)
+    static constexpr int K1 = BF ? 96 : 88;  // layer-1 K (81 inputs) padded to whole k-steps
+    __host__ __device__ static constexpr uint32_t off(int R, int r, int k) {
+        return (uint32_t)((k / KS) * (R * 32) + (r >> 3) * 256 + ((k / EC) & 1) * 128 + (r & 7) * 16 + (k % EC) * ES);
+    }
+    static constexpr uint32_t bytes(int R, int K) { return (uint32_t)(R * K * ES); }
+    // shared-memory map (bytes); weight images first, in the order of the global image
+    static constexpr uint32_t SZ_B1 = bytes(N1, K1), SZ_B2 = bytes(N2, K2), SZ_B3 = bytes(NB3, K3),
+                              SZ_B4 = bytes(NB4, K4);
+    static constexpr uint32_t S_B1 = 0;
+    static constexpr uint32_t S_B2 = S_B1 + NP * SZ_B1;
+    static constexpr uint32_t S_VEC = S_B2 + NP * SZ_B2;
+    static constexpr uint32_t S_B3 = S_VEC + SZ_VEC;  // backward only
+    static constexpr uint32_t S_B4 = S_B3 + NP * SZ_B3;
+    static constexpr uint32_t IMG_FWD = S_B3;         // bytes of the image the forward copies
+    static constexpr uint32_t IMG_ALL = S_B4 + NP * SZ_B4;
+    static constexpr uint32_t SZ_A = bytes(TM, K1);   // largest A operand (one part)
+    static constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
+    // halo, partials, g_y, centre-value gradients, stencil offsets, barrier + TMEM slot
+    static constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * 3 * TM + 4 * K1 + 64;
+    static constexpr uint32_t SMEM_FWD = S_A_FWD + NP * SZ_A + SZ_TAIL;
+    static constexpr uint32_t SMEM_BWD = S_A_BWD + NP * SZ_A + SZ_TAIL;
+    static_assert(SMEM_BWD <= 232448, "shared memory budget");
+    static_assert((S_B2 | S_VEC | S_B3 | S_B4 | S_A_FWD | S_A_BWD | SZ_A) % 128 == 0, "128-byte aligned regions");
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -96,6 +108,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 // Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f16 with bf16 A and B, D f32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -163,6 +187,26 @@ __device__ __forceinline__ void put4(unsigned char* Ahi, unsigned char* Alo, uin
     *reinterpret_cast<float4*>(Alo + off) = make_float4(a - ha, b - hb, c - hc, d - hd);
 }
 
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// Store 8 consecutive K values of row r starting at k0 (k0 % 8 == 0) in the operand image(s).
+template <bool BF>
+__device__ __forceinline__ void put8(unsigned char* Ahi, unsigned char* Alo, int r, int k0, const float* v) {
+    using L = Lay<BF>;
+    if constexpr (BF) {
+        *reinterpret_cast<uint4*>(Ahi + L::off(TM, r, k0)) =
+            make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                       pack_bf16x2(v[6], v[7]));
+    } else {
+        put4(Ahi, Alo, L::off(TM, r, k0), v[0], v[1], v[2], v[3]);
+        put4(Ahi, Alo, L::off(TM, r, k0 + 4), v[4], v[5], v[6], v[7]);
+    }
+}
+
 __device__ __forceinline__ int wrapi(int v, int N) { return v < 0 ? v + N : (v >= N ? v - N : v); }
 
 __device__ __forceinline__ float softplusf(float y) { return y > 0.f ? y + log1pf(expf(-y)) : log1pf(expf(y)); }
@@ -170,15 +214,21 @@ __device__ __forceinline__ float sigmoidf(float y) {
     return y >= 0.f ? 1.f / (1.f + expf(-y)) : expf(y) / (1.f + expf(y));
 }
 
-// issue the MMAs of one layer: D (+)= A x B^T over ksteps, hi*hi (+ hi*lo + lo*hi)
+// issue the MMAs of one layer: D (+)= A x B^T over K; TF32: hi*hi (+ hi*lo + lo*hi), BF16: one product
+template <bool BF>
 __device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            int ksteps, int Rb, uint32_t idesc, int nsplit) {
+                                            int K, int Rb, int nsplit) {
+    const int ksteps = K / Lay<BF>::KS;
     for (int ks = 0; ks < ksteps; ++ks) {
         const uint32_t ao = (uint32_t)ks * (TM * 32), bo = (uint32_t)ks * (Rb * 32);
-        mma_tf32(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc, ks > 0 ? 1u : 0u);
-        if (nsplit > 1) {
-            mma_tf32(d, sdesc(a_hi + ao), sdesc(b_lo + bo), idesc, 1u);
-            mma_tf32(d, sdesc(a_lo + ao), sdesc(b_hi + bo), idesc, 1u);
+        if constexpr (BF) {
+            mma_bf16(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_bf16(TM, Rb), ks > 0 ? 1u : 0u);
+        } else {
+            mma_tf32(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), ks > 0 ? 1u : 0u);
+            if (nsplit > 1) {
+                mma_tf32(d, sdesc(a_hi + ao), sdesc(b_lo + bo), idesc_tf32(TM, Rb), 1u);
+                mma_tf32(d, sdesc(a_lo + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), 1u);
+            }
         }
     }
 }
@@ -189,23 +239,25 @@ struct TileMap {
     int64_t N3;
 };
 
-template <bool BWD, bool TWO_NET>
+template <bool BWD, bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
              TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ M_out,
              float* __restrict__ gv, int* __restrict__ err) {
+    using L = Lay<BF>;
+    constexpr int K1 = L::K1;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const uint32_t S_A = BWD ? S_A_BWD : S_A_FWD;
+    const uint32_t S_A = BWD ? L::S_A_BWD : L::S_A_FWD;
     unsigned char* Ahi = sm + S_A;
-    unsigned char* Alo = Ahi + SZ_A;
-    float* halo = reinterpret_cast<float*>(Alo + SZ_A);
+    unsigned char* Alo = Ahi + (L::NP - 1) * L::SZ_A;  // == Ahi with one part
+    float* halo = reinterpret_cast<float*>(Ahi + L::NP * L::SZ_A);
     float* part = halo + HALO;   // [4][TM]
     float* gys = part + 4 * TM;  // [TM]
     float* gcen = gys + TM;      // [3][TM]: gradient w.r.t. the voxel's own three values (mass network)
     int* koff = reinterpret_cast<int*>(gcen + 3 * TM);  // [K1]: halo offset of stencil input k (-1: padding)
     uint64_t* bar = reinterpret_cast<uint64_t*>(koff + K1);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-    const float* vec = reinterpret_cast<const float*>(sm + S_VEC);
+    const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
     const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -217,7 +269,7 @@ __global__ void __launch_bounds__(NT, 1)
 
     // weight images -> shared memory (once per block)
     {
-        const uint32_t n16 = (BWD ? IMG_ALL : IMG_FWD) / 16;
+        const uint32_t n16 = (BWD ? L::IMG_ALL : L::IMG_FWD) / 16;
         float4* dst = reinterpret_cast<float4*>(sm);
         for (uint32_t i = tid; i < n16; i += NT) dst[i] = img[i];
     }
@@ -298,8 +350,7 @@ __global__ void __launch_bounds__(NT, 1)
                     const int ko = koff[ks * 8 + j];
                     v[j] = ko >= 0 ? halo[ko + base] : 0.f;
                 }
-                put4(Ahi, Alo, img_off(TM, r, ks * 8), v[0], v[1], v[2], v[3]);
-                put4(Ahi, Alo, img_off(TM, r, ks * 8 + 4), v[4], v[5], v[6], v[7]);
+                put8<BF>(Ahi, Alo, r, ks * 8, v);
             }
         }
         fence_async_smem();
@@ -309,8 +360,8 @@ __global__ void __launch_bounds__(NT, 1)
         // (c) layer 1
         if (tid == 0) {
             tc_fence_after();
-            issue_layer(tmem + COL_D1, sA_hi, sA_lo, smem_u32(sm + S_B1), smem_u32(sm + S_B1 + SZ_B1), K1 / 8, N1,
-                        idesc_tf32(TM, N1), nsplit);
+            issue_layer<BF>(tmem + COL_D1, sA_hi, sA_lo, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1),
+                            K1, N1, nsplit);
             mma_commit(bar);
         }
         ok = __syncthreads_and(mbar_wait(bar, phase));
@@ -330,9 +381,8 @@ __global__ void __launch_bounds__(NT, 1)
                 mask1 |= (pre > 0.f ? 1u : 0u) << j;
                 z[j] = fmaxf(pre, 0.f);
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                put4(Ahi, Alo, img_off(TM, row, 16 * cb + 4 * q), z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+            put8<BF>(Ahi, Alo, row, 16 * cb, z);
+            put8<BF>(Ahi, Alo, row, 16 * cb + 8, z + 8);
         }
         fence_async_smem();
         tc_fence_before();
@@ -341,8 +391,8 @@ __global__ void __launch_bounds__(NT, 1)
         // (e) layer 2
         if (tid == 0) {
             tc_fence_after();
-            issue_layer(tmem + COL_D2, sA_hi, sA_lo, smem_u32(sm + S_B2), smem_u32(sm + S_B2 + SZ_B2), K2 / 8, N2,
-                        idesc_tf32(TM, N2), nsplit);
+            issue_layer<BF>(tmem + COL_D2, sA_hi, sA_lo, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2),
+                            K2, N2, nsplit);
             mma_commit(bar);
         }
         ok = __syncthreads_and(mbar_wait(bar, phase));
@@ -409,16 +459,15 @@ __global__ void __launch_bounds__(NT, 1)
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) v[j] = ((mask2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
-            put4(Ahi, Alo, img_off(TM, row, 8 * cb), v[0], v[1], v[2], v[3]);
-            put4(Ahi, Alo, img_off(TM, row, 8 * cb + 4), v[4], v[5], v[6], v[7]);
+            put8<BF>(Ahi, Alo, row, 8 * cb, v);
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_layer(tmem + COL_D3, sA_hi, sA_lo, smem_u32(sm + S_B3), smem_u32(sm + S_B3 + SZ_B3), K3 / 8, NB3,
-                        idesc_tf32(TM, NB3), nsplit);
+            issue_layer<BF>(tmem + COL_D3, sA_hi, sA_lo, smem_u32(sm + L::S_B3), smem_u32(sm + L::S_B3 + L::SZ_B3),
+                            K3, NB3, nsplit);
             mma_commit(bar);
         }
         ok = __syncthreads_and(mbar_wait(bar, phase));
@@ -432,17 +481,16 @@ __global__ void __launch_bounds__(NT, 1)
             tmem_ld16(lane_base + COL_D3 + 16 * cb, a);
 #pragma unroll
             for (int j = 0; j < 16; ++j) a[j] = ((mask1 >> j) & 1u) ? a[j] : 0.f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                put4(Ahi, Alo, img_off(TM, row, 16 * cb + 4 * q), a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+            put8<BF>(Ahi, Alo, row, 16 * cb, a);
+            put8<BF>(Ahi, Alo, row, 16 * cb + 8, a + 8);
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            issue_layer(tmem + COL_D4, sA_hi, sA_lo, smem_u32(sm + S_B4), smem_u32(sm + S_B4 + SZ_B4), K4 / 8, NB4,
-                        idesc_tf32(TM, NB4), nsplit);
+            issue_layer<BF>(tmem + COL_D4, sA_hi, sA_lo, smem_u32(sm + L::S_B4), smem_u32(sm + L::S_B4 + L::SZ_B4),
+                            K4, NB4, nsplit);
             mma_commit(bar);
         }
         ok = __syncthreads_and(mbar_wait(bar, phase));
@@ -498,14 +546,31 @@ float tf32_round(float x) {
     return r;
 }
 
-void put_operand(std::vector<float>& img, uint32_t base, int R, int K, float (*get)(const float*, int, int),
+// host: float -> bfloat16 bits, round to nearest, ties to even (finite values)
+uint16_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+// B operand (R rows, K columns) into the image: TF32 head and tail parts, or one bf16 part
+template <bool BF>
+void put_operand(std::vector<unsigned char>& img, uint32_t base, int R, int K, float (*get)(const float*, int, int),
                  const float* W) {
+    using L = Lay<BF>;
     for (int r = 0; r < R; ++r)
         for (int k = 0; k < K; ++k) {
             const float v = get(W, r, k);
-            const float hi = tf32_round(v);
-            img[(base + img_off(R, r, k)) / 4] = hi;
-            img[(base + img_bytes(R, K) + img_off(R, r, k)) / 4] = v - hi;
+            const uint32_t o = base + L::off(R, r, k);
+            if constexpr (BF) {
+                const uint16_t h = bf16_bits(v);
+                std::memcpy(&img[o], &h, 2);
+            } else {
+                const float hi = tf32_round(v), lo = v - hi;
+                std::memcpy(&img[o], &hi, 4);
+                std::memcpy(&img[o + L::bytes(R, K)], &lo, 4);
+            }
         }
 }
 
@@ -526,72 +591,90 @@ TileMap tile_map(const pmr_ctx* c, int* ntiles) {
     return m;
 }
 
-}  // namespace
-
-// Weight images for the tensor-core kernels, built once per context.
-int mlp_tc_init(pmr_ctx* c) {
-    std::vector<float> img(IMG_ALL / 4, 0.f);
-    const float* W = c->W_host.data();
-    put_operand(img, S_B1, N1, K1, get_B1, W);
-    put_operand(img, S_B2, N2, K2, get_B2, W);
-    put_operand(img, S_B3, NB3, K3, get_B3, W);
-    put_operand(img, S_B4, NB4, K4, get_B4, W);
-    float* vec = img.data() + S_VEC / 4;
+template <bool BF>
+std::vector<unsigned char> build_image(const float* W) {
+    using L = Lay<BF>;
+    std::vector<unsigned char> img(L::IMG_ALL, 0);
+    put_operand<BF>(img, L::S_B1, N1, L::K1, get_B1, W);
+    put_operand<BF>(img, L::S_B2, N2, K2, get_B2, W);
+    put_operand<BF>(img, L::S_B3, NB3, K3, get_B3, W);
+    put_operand<BF>(img, L::S_B4, NB4, K4, get_B4, W);
+    float vec[SZ_VEC / 4] = {};
     for (int h = 0; h < H1; ++h) vec[h] = W[OFF_B1 + h];
     for (int h = 0; h < H2; ++h) vec[64 + h] = W[OFF_B2 + h];
     for (int h = 0; h < H2; ++h) vec[96 + h] = W[OFF_W3 + h];
     vec[128] = W[OFF_B3];
     for (int i = 0; i < kMassWeights; ++i) vec[VEC_MASS + i] = W[OFF_B3 + 1 + i];  // zeros unless head == 1
-    PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_img, IMG_ALL), "tc weights"));
-    PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img, img.data(), IMG_ALL, cudaMemcpyHostToDevice), "tc weights"));
+    std::memcpy(&img[L::S_VEC], vec, SZ_VEC);
+    return img;
+}
+
+template <bool BF>
+int set_smem_attrs(pmr_ctx* c) {
+    using L = Lay<BF>;
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)L::SMEM_FWD), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)L::SMEM_FWD), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)L::SMEM_BWD), "smem attr"));
+    return check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)L::SMEM_BWD), "smem attr");
+}
+
+template <bool BWD, bool BF>
+int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nsplit, float a) {
+    using L = Lay<BF>;
+    int ntiles = 0;
+    TileMap m = tile_map(c, &ntiles);
+    const int grid = std::min(ntiles, c->num_sms);
+    const float4* img = reinterpret_cast<const float4*>(BF ? c->tc_img_bf : c->tc_img);
+    const float Ms = (float)c->cfg.M_scale;
+    const uint32_t smem = BWD ? L::SMEM_BWD : L::SMEM_FWD;
+    float* gv = BWD ? c->gv : nullptr;
+    if (c->cfg.head == 1)
+        k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv,
+                                                               c->tc_err);
+    else
+        k_mlp_tc<BWD, false, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv,
+                                                                c->tc_err);
+    return check_launch(c, BWD ? "mlp_tc_bwd" : "mlp_tc_fwd");
+}
+
+}  // namespace
+
+// Weight images for the tensor-core kernels (TF32 parts and bf16), built once per context.
+int mlp_tc_init(pmr_ctx* c) {
+    const float* W = c->W_host.data();
+    const std::vector<unsigned char> it = build_image<false>(W), ib = build_image<true>(W);
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_img, it.size()), "tc weights"));
+    PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img, it.data(), it.size(), cudaMemcpyHostToDevice), "tc weights"));
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_img_bf, ib.size()), "tc weights"));
+    PMR_TRY(check_cuda(c, cudaMemcpy(c->tc_img_bf, ib.data(), ib.size(), cudaMemcpyHostToDevice), "tc weights"));
     PMR_TRY(check_cuda(c, cudaMalloc(&c->tc_err, sizeof(int)), "tc flag"));
     PMR_TRY(check_cuda(c, cudaMemset(c->tc_err, 0, sizeof(int)), "tc flag"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)SMEM_FWD), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)SMEM_FWD), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)SMEM_BWD), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)SMEM_BWD), "smem attr"));
-    return PMR_OK;
+    PMR_TRY(set_smem_attrs<false>(c));
+    return set_smem_attrs<true>(c);
 }
 
 void mlp_tc_free(pmr_ctx* c) {
     cudaFree(c->tc_img);
+    cudaFree(c->tc_img_bf);
+    c->tc_img_bf = nullptr;
     cudaFree(c->tc_err);
     c->tc_img = nullptr;
     c->tc_err = nullptr;
 }
 
+// nsplit: 3 = TF32 head/tail products (float32 accuracy), 1 = plain TF32, 0 = bf16 operands
 int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit, float a) {
-    int ntiles = 0;
-    TileMap m = tile_map(c, &ntiles);
-    const int grid = std::min(ntiles, c->num_sms);
-    const float4* img = reinterpret_cast<const float4*>(c->tc_img);
-    const float Ms = (float)c->cfg.M_scale;
-    if (c->cfg.head == 1)
-        k_mlp_tc<false, true><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, img, m, ntiles, nsplit, Ms, a, M,
-                                                                  nullptr, c->tc_err);
-    else
-        k_mlp_tc<false, false><<<grid, NT, SMEM_FWD, c->stream>>>(feat, nullptr, img, m, ntiles, nsplit, Ms, a, M,
-                                                                   nullptr, c->tc_err);
-    return check_launch(c, "mlp_tc_fwd");
+    return nsplit == 0 ? launch_tc<false, true>(c, feat, nullptr, M, 0, a)
+                       : launch_tc<false, false>(c, feat, nullptr, M, nsplit, a);
 }
 
 int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit, float a) {
-    int ntiles = 0;
-    TileMap m = tile_map(c, &ntiles);
-    const int grid = std::min(ntiles, c->num_sms);
-    const float4* img = reinterpret_cast<const float4*>(c->tc_img);
-    const float Ms = (float)c->cfg.M_scale;
-    if (c->cfg.head == 1)
-        k_mlp_tc<true, true><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, nullptr,
-                                                                 c->gv, c->tc_err);
-    else
-        k_mlp_tc<true, false><<<grid, NT, SMEM_BWD, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, nullptr,
-                                                                  c->gv, c->tc_err);
-    return check_launch(c, "mlp_tc_bwd");
+    return nsplit == 0 ? launch_tc<true, true>(c, feat, gM, nullptr, 0, a)
+                       : launch_tc<true, false>(c, feat, gM, nullptr, nsplit, a);
 }
 
 }  // namespace pmr

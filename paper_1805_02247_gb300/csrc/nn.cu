@@ -203,11 +203,13 @@ int nn_features(pmr_ctx* c, const float* delta) {
 
 static_assert(sizeof(Weights) <= 32000, "weights must fit the kernel parameter space");
 
+// tensor-core operand mode of nn_path: 0 -> TF32 head/tail (3 products), 1 -> TF32, 3 -> bf16
+int tc_split(const pmr_ctx* c) { return c->cfg.nn_path == 0 ? 3 : (c->cfg.nn_path == 1 ? 1 : 0); }
+
 // nn_path 0: tensor cores, 3xTF32 (float32 accuracy); 1: tensor cores, TF32;
 // 2: float32 CUDA cores.
 int mlp_forward(pmr_ctx* c, const float* feat, float* M, float a) {
-    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1)
-        return mlp_tc_forward(c, feat, M, c->cfg.nn_path == 0 ? 3 : 1, a);
+    if (c->cfg.nn_path != 2) return mlp_tc_forward(c, feat, M, tc_split(c), a);
     static_assert(NW == 5661, "weight layout");
     Weights W;
     std::copy(c->W_host.begin(), c->W_host.begin() + (NW + kMassWeights), W.w);
@@ -221,8 +223,8 @@ int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat) {
 }
 
 int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat, float a) {
-    if (c->cfg.nn_path == 0 || c->cfg.nn_path == 1) {
-        PMR_TRY(mlp_tc_backward_gv(c, feat, gM, c->cfg.nn_path == 0 ? 3 : 1, a));
+    if (c->cfg.nn_path != 2) {
+        PMR_TRY(mlp_tc_backward_gv(c, feat, gM, tc_split(c), a));
         return stencil_transpose(c, c->gv, gfeat);
     }
     Weights W;

@@ -84,11 +84,15 @@ def test_nn_halo_map_and_adjoint_parity():
     assert rel_l2(gd, oloss.nn_halo_map_T(gM, delta, w, setup, ls)) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("nn_path,ftol,gtol", [(0, FIELD_TOL, GRAD_TOL), (2, FIELD_TOL, GRAD_TOL), (1, 1e-2, 5e-2)])
+@pytest.mark.parametrize("nn_path,ftol,gtol", [(0, FIELD_TOL, GRAD_TOL), (2, FIELD_TOL, GRAD_TOL), (1, 1e-2, 5e-2),
+                                               (3, 2e-2, 1e-1)])
 @pytest.mark.parametrize("N,L", [(32, 100.0), (24, 60.0)])
 def test_network_paths_against_oracle(nn_path, ftol, gtol, N, L):
     # 0: tcgen05 tensor cores with two-part TF32 operands (float32 accuracy),
-    # 2: float32 CUDA cores, 1: plain TF32 tensor cores (looser, reported path).
+    # 2: float32 CUDA cores, 1: plain TF32 tensor cores, 3: bfloat16 tensor
+    # cores with float32 accumulation (8-bit mantissas, ~2^-9 per operand; the
+    # backward also sees ReLU masks flip on near-zero units, observed 5.6% on the
+    # input gradient at 32^3): percent-level bounds, the bench reports the errors.
     # N = 24 leaves partial voxel tiles (tiles are 2 x 4 x 16).
     ctx, _ = context(N=N, L=L, nn_path=nn_path)
     setup = opm.PMSetup(N=N, L=L, nsteps=3)
@@ -167,6 +171,19 @@ def test_loss_and_grad_parity_with_2lpt():
                                       oloss.Anneal(R_sm=R_sm, M0=M0))
     assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
     assert rel_l2(to_np(g), gwant) <= GRAD_TOL
+
+
+def test_bf16_network_loss_and_gradient_against_oracle():
+    # the bf16 tensor-core path inside the whole loss and gradient
+    N, L, nsteps, R_sm, M0 = 16, 50.0, 2, 4.0, 1e8
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, nn_path=3)
+    setup, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
+    want, gwant = oloss.loss_and_grad(s, data, synth.xavier_weights(1), setup, oloss.LossSetup(),
+                                      oloss.Anneal(R_sm=R_sm, M0=M0))
+    assert parts[0] == pytest.approx(want["loss"], rel=1e-2)
+    assert rel_l2(to_np(g), gwant) <= 1e-1
 
 
 def test_loss_nan_is_reported():
