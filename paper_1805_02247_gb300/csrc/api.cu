@@ -111,7 +111,8 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->gm : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->gm2 : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->gfeat : nullptr), sizeof(float) * 3 * N3);
-    alloc((void**)(c ? &c->gv : nullptr), sizeof(float) * 81 * N3);
+    if (cfg.nn_path == 2) alloc((void**)(c ? &c->gv : nullptr), sizeof(float) * 81 * N3);
+    else alloc((void**)(c ? &c->gbox : nullptr), sizeof(float) * (size_t)mlp_tc_box_floats((int)N));
     alloc((void**)(c ? &c->cA : nullptr), sizeof(float2) * NH);
     alloc((void**)(c ? &c->cB : nullptr), sizeof(float2) * NH);
     alloc((void**)(c ? &c->c3 : nullptr), sizeof(float2) * 3 * NH);

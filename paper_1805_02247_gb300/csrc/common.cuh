@@ -198,7 +198,8 @@ struct pmr_ctx {
     float* gm = nullptr;    // N3 scratch mesh
     float* gm2 = nullptr;   // N3 scratch mesh
     float* gfeat = nullptr; // 3 * N3
-    float* gv = nullptr;    // 81 * N3 network input-gradient scratch
+    float* gv = nullptr;    // 81 * N3 network input-gradient scratch (CUDA-core network)
+    float* gbox = nullptr;  // per-tile box sums of the input gradient (tensor-core network)
     float2* cA = nullptr;   // complex work arrays, NH each
     float2* cB = nullptr;
     float2* c3 = nullptr;   // 3 * NH
@@ -299,7 +300,9 @@ void twopt_free(pmr_ctx* c);
 int mlp_tc_init(pmr_ctx* c);
 void mlp_tc_free(pmr_ctx* c);
 int mlp_tc_forward(pmr_ctx* c, const float* feat, float* M, int nsplit, float a);
-int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit, float a);  // -> c->gv
+int mlp_tc_backward_gv(pmr_ctx* c, const float* feat, const float* gM, int nsplit, float a);  // -> c->gbox
+int mlp_tc_box_floats(int N);               // size of c->gbox
+int stencil_tiles(pmr_ctx* c, float* gfeat);  // c->gbox -> input gradient of the three fields
 
 // loss (loss.cu) ----------------------------------------------------------------
 int residual_forward(pmr_ctx* c, const float* data, const pmr_anneal* an, double* L_res_dev);

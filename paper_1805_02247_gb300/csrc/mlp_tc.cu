@@ -15,7 +15,10 @@
 // Backward per tile (after the forward): g_a2 = w3 g_y [a2 > 0]
 //                     A3 = g_a2[128 x 32] x W2 -> D3 = g_a1 (pre-mask) [128 x 64]
 //                     A4 = g_a1 [a1 > 0] [128 x 64] x W1 -> D4 = g_v[128 x 96]
-// g_v (81 columns) goes to the [81][N^3] scratch that the stencil transpose sums.
+// The backward stages g_v (81 columns) in shared memory and sums it per target
+// cell of the tile's box (the tile grown by one cell, 3 fields x 4 x 6 x 18), so
+// a tile writes 1296 floats instead of 81 x 128; k_stencil_tiles adds the
+// overlapping boxes of up to 8 tiles per cell in a fixed order.
 //
 // Every mbarrier wait is bounded; on timeout the block records an error flag,
 // waits (bounded) for its MMAs, frees its TMEM and returns.
@@ -82,10 +85,12 @@ struct Lay {
     static constexpr uint32_t IMG_ALL = S_B4 + NP * SZ_B4;
     static constexpr uint32_t SZ_A = bytes(TM, K1);   // largest A operand (one part)
     static constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
+    static constexpr uint32_t SZ_GVS = 4 * NI * TM;   // backward: g_v staged as [81][128] floats over the A region
+    static constexpr uint32_t SZ_AREG = NP * SZ_A > SZ_GVS ? NP * SZ_A : SZ_GVS;
     // halo, partials, g_y, centre-value gradients, stencil offsets, barrier + TMEM slot
     static constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * 3 * TM + 4 * K1 + 64;
-    static constexpr uint32_t SMEM_FWD = S_A_FWD + NP * SZ_A + SZ_TAIL;
-    static constexpr uint32_t SMEM_BWD = S_A_BWD + NP * SZ_A + SZ_TAIL;
+    static constexpr uint32_t SMEM_FWD = S_A_FWD + SZ_AREG + SZ_TAIL;
+    static constexpr uint32_t SMEM_BWD = S_A_BWD + SZ_AREG + SZ_TAIL;
     static_assert(SMEM_BWD <= 232448, "shared memory budget");
     static_assert((S_B2 | S_VEC | S_B3 | S_B4 | S_A_FWD | S_A_BWD | SZ_A) % 128 == 0, "128-byte aligned regions");
 };
@@ -243,14 +248,15 @@ template <bool BWD, bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
              TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ M_out,
-             float* __restrict__ gv, int* __restrict__ err) {
+             float* __restrict__ gbox, int* __restrict__ err) {
     using L = Lay<BF>;
     constexpr int K1 = L::K1;
     extern __shared__ __align__(1024) unsigned char sm[];
     const uint32_t S_A = BWD ? L::S_A_BWD : L::S_A_FWD;
     unsigned char* Ahi = sm + S_A;
     unsigned char* Alo = Ahi + (L::NP - 1) * L::SZ_A;  // == Ahi with one part
-    float* halo = reinterpret_cast<float*>(Ahi + L::NP * L::SZ_A);
+    float* halo = reinterpret_cast<float*>(Ahi + L::SZ_AREG);
+    float* gvs = reinterpret_cast<float*>(Ahi);  // backward: g_v [81][TM], after the last MMA
     float* part = halo + HALO;   // [4][TM]
     float* gys = part + 4 * TM;  // [TM]
     float* gcen = gys + TM;      // [3][TM]: gradient w.r.t. the voxel's own three values (mass network)
@@ -308,10 +314,15 @@ __global__ void __launch_bounds__(NT, 1)
         z0 = tz * TZ;
     };
     float hv[HALO_PER];
+    float gm_next = 0.f;  // backward: this thread's g_M of the next tile (rows tid < TM)
     auto load_halo = [&](int tile) {
         if (tile >= ntiles) return;
         int x0, y0, z0;
         tile_origin(tile, x0, y0, z0);
+        if (BWD && tid < TM) {
+            const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
+            gm_next = (gx < N && gy < N && gz < N) ? gM[((int64_t)gx * N + gy) * N + gz] : 0.f;
+        }
 #pragma unroll
         for (int q = 0; q < HALO_PER; ++q) {
             const int t = tid + q * NT;
@@ -336,6 +347,7 @@ __global__ void __launch_bounds__(NT, 1)
             const int t = tid + q * NT;
             if (t < HALO) halo[t] = hv[q];
         }
+        const float gm_cur = gm_next;
         __syncthreads();
         load_halo(tile + gridDim.x);
 
@@ -432,7 +444,7 @@ __global__ void __launch_bounds__(NT, 1)
                     float u0, u1, u2;
                     if (in) M_out[vox] = M_scale * p * mass_net<false>(vec + VEC_MASS, f[0], f[1], f[2], 0.f, u0, u1, u2);
                 } else {
-                    const float g = in ? gM[vox] * M_scale : 0.f;
+                    const float g = in ? gm_cur * M_scale : 0.f;
                     float g0, g1, g2;
                     const float m = mass_net<true>(vec + VEC_MASS, f[0], f[1], f[2], g * p, g0, g1, g2);
                     gys[r] = g * m * a * p * (1.f - p);
@@ -443,7 +455,7 @@ __global__ void __launch_bounds__(NT, 1)
             } else if (!BWD) {
                 if (in) M_out[vox] = M_scale * softplusf(y);
             } else {
-                gys[r] = in ? gM[vox] * M_scale * sigmoidf(y) : 0.f;
+                gys[r] = in ? gm_cur * M_scale * sigmoidf(y) : 0.f;
             }
         }
         if (!BWD) {
@@ -498,12 +510,10 @@ __global__ void __launch_bounds__(NT, 1)
         if (!ok) break;
         tc_fence_after();
 
-        // (i) g_v: 24 columns per thread -> gv[k][voxel], k < 81
+        // (i) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
         {
             const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
-            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-            const bool in = gx < N && gy < N && gz < N;
-            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
+            const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
 #pragma unroll
             for (int h = 0; h < 3; ++h) {
                 float a[8];
@@ -513,11 +523,37 @@ __global__ void __launch_bounds__(NT, 1)
                     const int k = 24 * cb + 8 * h + j;
                     float v = a[j];
                     if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(k / 27) * TM + row];  // mass network's input
-                    if (in && k < NI) gv[k * N3 + vox] = v;
+                    if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
                 }
             }
         }
         tc_fence_before();
+        __syncthreads();
+        // (j) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
+        //     tile voxel at box cell - 1 - o, offsets o in a fixed order
+        for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
+            const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
+            const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
+            float acc = 0.f;
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int lx = hx - 1 - ox;
+                if (lx < 0 || lx >= TX) continue;
+#pragma unroll
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int ly = hy - 1 - oy;
+                    if (ly < 0 || ly >= TY) continue;
+#pragma unroll
+                    for (int oz = -1; oz <= 1; ++oz) {
+                        const int lz = hz - 1 - oz;
+                        if (lz < 0 || lz >= TZ) continue;
+                        const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                        acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
+                    }
+                }
+            }
+            gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
+        }
         __syncthreads();
     }
 
@@ -591,6 +627,51 @@ TileMap tile_map(const pmr_ctx* c, int* ntiles) {
     return m;
 }
 
+// Candidate (tile, box index) pairs of cell x along one axis: the tiles of the
+// real cells x+1, x, x-1 (periodic), each holding x at box index (p mod TS) + 1 + d;
+// duplicates (the same tile and index reached twice) are dropped.
+template <int TS>
+__device__ __forceinline__ int axis_boxes(int x, int N, int* t_out, int* b_out) {
+    int n = 0;
+#pragma unroll
+    for (int d = 1; d >= -1; --d) {
+        int p = x - d;
+        p = p < 0 ? p + N : (p >= N ? p - N : p);
+        const int t = p / TS, b = p - t * TS + 1 + d;
+        bool dup = false;
+        for (int i = 0; i < n; ++i) dup |= (t_out[i] == t && b_out[i] == b);
+        if (!dup) {
+            t_out[n] = t;
+            b_out[n] = b;
+            ++n;
+        }
+    }
+    return n;
+}
+
+// g_field[c](cell) = sum over the tiles whose box holds the cell, in a fixed order.
+__global__ void __launch_bounds__(256) k_stencil_tiles(const float* __restrict__ gbox, int N, int nty, int ntz,
+                                                       float* __restrict__ gfeat) {
+    const int64_t N3 = (int64_t)N * N * N;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N3) return;
+    const int x = (int)(v / ((int64_t)N * N)), y = (int)((v / N) % N), z = (int)(v % N);
+    int tx[3], bx[3], ty[3], by[3], tz[3], bz[3];
+    const int nx = axis_boxes<TX>(x, N, tx, bx), ny = axis_boxes<TY>(y, N, ty, by), nz = axis_boxes<TZ>(z, N, tz, bz);
+    constexpr int BOX = HX * HY * HZ;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < ny; ++j)
+            for (int k = 0; k < nz; ++k) {
+                const int64_t tile = ((int64_t)tx[i] * nty + ty[j]) * ntz + tz[k];
+                const float* b = gbox + tile * (3 * BOX) + (bx[i] * HY + by[j]) * HZ + bz[k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] += b[c * BOX];
+            }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gfeat[c * N3 + v] = acc[c];
+}
+
 template <bool BF>
 std::vector<unsigned char> build_image(const float* W) {
     using L = Lay<BF>;
@@ -631,7 +712,7 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     const float4* img = reinterpret_cast<const float4*>(BF ? c->tc_img_bf : c->tc_img);
     const float Ms = (float)c->cfg.M_scale;
     const uint32_t smem = BWD ? L::SMEM_BWD : L::SMEM_FWD;
-    float* gv = BWD ? c->gv : nullptr;
+    float* gv = BWD ? c->gbox : nullptr;
     if (c->cfg.head == 1)
         k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv,
                                                                c->tc_err);
@@ -664,6 +745,17 @@ void mlp_tc_free(pmr_ctx* c) {
     cudaFree(c->tc_err);
     c->tc_img = nullptr;
     c->tc_err = nullptr;
+}
+
+int mlp_tc_box_floats(int N) {
+    return ((N + TX - 1) / TX) * ((N + TY - 1) / TY) * ((N + TZ - 1) / TZ) * 3 * HX * HY * HZ;
+}
+
+// input gradient of the three fields from the per-tile box sums of mlp_tc_backward_gv
+int stencil_tiles(pmr_ctx* c, float* gfeat) {
+    k_stencil_tiles<<<nblocks(c->N3, 256), 256, 0, c->stream>>>(c->gbox, c->N, (c->N + TY - 1) / TY,
+                                                                (c->N + TZ - 1) / TZ, gfeat);
+    return check_launch(c, "stencil_tiles");
 }
 
 // nsplit: 3 = TF32 head/tail products (float32 accuracy), 1 = plain TF32, 0 = bf16 operands

@@ -225,7 +225,7 @@ int stencil_transpose(pmr_ctx* c, const float* gv, float* gfeat) {
 int mlp_backward(pmr_ctx* c, const float* feat, const float* gM, float* gfeat, float a) {
     if (c->cfg.nn_path != 2) {
         PMR_TRY(mlp_tc_backward_gv(c, feat, gM, tc_split(c), a));
-        return stencil_transpose(c, c->gv, gfeat);
+        return stencil_tiles(c, gfeat);
     }
     Weights W;
     std::copy(c->W_host.begin(), c->W_host.begin() + (NW + kMassWeights), W.w);
