@@ -111,6 +111,17 @@ size_t pmr_workspace_bytes(const pmr_config* cfg);
 int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream, pmr_ctx** out);
 int pmr_destroy(pmr_ctx* ctx);
 int pmr_set_stream(pmr_ctx* ctx, void* stream);
+
+/* Serving aid (no counterpart in the paper): with enable != 0, the launches of
+ * one loss_and_grad evaluation (the ~480 kernels of the ICs, PM steps, network,
+ * loss and adjoint) are captured once into a CUDA graph and replayed as one
+ * graph launch for every later evaluation with the same s_k, data, anneal
+ * parameters and gradient buffer (recon_step's line-search trials, repeated
+ * loss_and_grad calls); any change re-captures. Results are identical to the
+ * direct launches. Capture is thread-local, so other threads may keep using
+ * CUDA meanwhile. Needs a context on a non-default stream (PMR_EINVAL
+ * otherwise); enable = 0 drops the graph. */
+int pmr_use_graphs(pmr_ctx* ctx, int enable);
 const char* pmr_last_error(const pmr_ctx* ctx);
 
 /* ---------------------------------------------------------------- the path */

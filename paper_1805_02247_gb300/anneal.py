@@ -46,12 +46,13 @@ def smoothing_schedule(radii_mpc, M0: float) -> list[Stage]:
     return [Stage(float(r), M0) for r in radii_mpc]
 
 
-def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=None):
+def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=None, min_iter: int = 1):
     """Runs the stages on s (complex64 half array, updated in place).
 
     Returns a list of per-iteration records {stage, iter, loss, prior, residual,
-    converged, seconds}. A stage ends when recon_step reports convergence or
-    after max_iter iterations; a line-search failure ends the stage.
+    converged, seconds}. A stage ends when recon_step reports convergence (from
+    its min_iter-th iteration on) or after max_iter iterations; a line-search
+    failure ends the stage.
     """
     history = []
     for si, st in enumerate(stages):
@@ -69,6 +70,6 @@ def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=Non
             history.append(rec)
             if callback:
                 callback(rec)
-            if conv:
+            if conv and it + 1 >= min_iter:
                 break
     return history

@@ -271,6 +271,7 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
         if (rc == PMR_OK) rc = check_cuda(c, cudaMalloc(p, b), "workspace");
     });
     if (rc == PMR_OK) rc = fft_init(c);
+    if (rc == PMR_OK) rc = pm_init(c);
     if (rc == PMR_OK) rc = lbfgs_alloc(c);
     if (rc == PMR_OK) {
         // linear power P~ = P(k) N^6 / L^3 on integer |n|^2, k = 2 pi |n| / L
@@ -315,6 +316,7 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
 int pmr_destroy(pmr_ctx* c) {
     if (!c) return PMR_OK;
     cudaStreamSynchronize(c->stream);
+    if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     free_all(c);
     delete c;
@@ -323,6 +325,10 @@ int pmr_destroy(pmr_ctx* c) {
 
 int pmr_set_stream(pmr_ctx* c, void* stream) {
     PMR_TRY(check_ctx(c));
+    if (c->graphs && !stream) return fail(c, PMR_EINVAL, "CUDA graphs need a non-default stream");
+    if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
+    c->g_exec = nullptr;
+    c->g_s = nullptr;
     c->stream = (cudaStream_t)stream;
     return PMR_OK;
 }
@@ -368,12 +374,68 @@ int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const pmr_anneal* an, co
     return features_T(c, c->gfeat, grad_delta);
 }
 
+namespace {
+void drop_graph(pmr_ctx* c) {
+    if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
+    c->g_exec = nullptr;
+    c->g_s = nullptr;
+}
+
+bool same_anneal(const pmr_anneal& a, const pmr_anneal& b) {
+    return a.R_sm == b.R_sm && a.M0 == b.M0 && a.a_logistic == b.a_logistic;
+}
+}  // namespace
+
+// One evaluation; with graphs on, the launches of loss_and_grad_impl for these
+// (s, data, an, grad) are captured once and replayed as one graph launch.
+static int evaluate(pmr_ctx* c, const float2* s, const float* data, const pmr_anneal* an, double* host,
+                    float2* grad) {
+    if (!c->graphs) return loss_and_grad_impl(c, s, data, an, host, grad);
+    if (!c->g_exec || c->g_s != s || c->g_data != data || c->g_grad != grad || !same_anneal(c->g_an, *an)) {
+        drop_graph(c);
+        const bool timing = c->timing;
+        const int64_t l0 = c->launches;
+        c->timing = false;
+        PMR_TRY(check_cuda(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
+        const int rc = loss_and_grad_impl(c, s, data, an, nullptr, grad);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->timing = timing;
+        c->g_launches = c->launches - l0;
+        c->launches = l0;
+        if (rc != PMR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        PMR_TRY(check_cuda(c, e, "end capture"));
+        const cudaError_t ei = cudaGraphInstantiate(&c->g_exec, g, 0);
+        cudaGraphDestroy(g);
+        PMR_TRY(check_cuda(c, ei, "graph instantiate"));
+        c->g_s = s;
+        c->g_data = data;
+        c->g_grad = grad;
+        c->g_an = *an;
+    }
+    PMR_TRY(check_cuda(c, cudaGraphLaunch(c->g_exec, c->stream), "graph launch"));
+    c->launches += c->g_launches;
+    if (host) return finish_loss(c, host);
+    return PMR_OK;
+}
+
+int pmr_use_graphs(pmr_ctx* c, int enable) {
+    PMR_TRY(check_ctx(c));
+    if (enable && !c->stream) return fail(c, PMR_EINVAL, "CUDA graphs need a context created on a non-default stream");
+    if (!enable) drop_graph(c);
+    c->graphs = enable != 0;
+    return PMR_OK;
+}
+
 int loss_and_grad(pmr_ctx* c, const void* s_k, const float* data_mass, const pmr_anneal* an, double* loss_out,
                   void* grad_s_k) {
     PMR_TRY(check_ctx(c));
     if (!s_k || !data_mass || !an || !grad_s_k) return fail(c, PMR_EINVAL, "NULL argument");
     if (!(an->R_sm >= 0) || !std::isfinite(an->M0)) return fail(c, PMR_EINVAL, "anneal: R_sm >= 0, finite M0");
-    return loss_and_grad_impl(c, (const float2*)s_k, data_mass, an, loss_out, (float2*)grad_s_k);
+    return evaluate(c, (const float2*)s_k, data_mass, an, loss_out, (float2*)grad_s_k);
 }
 
 int pmr_lbfgs_reset(pmr_ctx* c) {
@@ -394,7 +456,7 @@ int recon_step(pmr_ctx* c, void* s_k_v, const float* data, const pmr_anneal* an,
     if (!L.have_f || an->R_sm != L.an.R_sm || an->M0 != L.an.M0 || an->a_logistic != L.an.a_logistic) {
         L.k = 0;
         L.head = 0;
-        PMR_TRY(loss_and_grad_impl(c, s_k, data, an, host, L.gk));
+        PMR_TRY(evaluate(c, s_k, data, an, host, L.gk));
         PMR_TRY(c64_to_f64(c, s_k, L.x, c->NH));
         PMR_TRY(c64_to_f64(c, L.gk, L.g, c->NH));
         L.f = host[0];
@@ -429,7 +491,7 @@ int recon_step(pmr_ctx* c, void* s_k_v, const float* data, const pmr_anneal* an,
     for (int it = 0; it < 20; ++it) {
         PMR_TRY(axpy64(c, L.xt, L.d, nullptr, t, n, L.x));
         PMR_TRY(f64_to_c64(c, L.xt, s_k, c->NH));
-        int rc = loss_and_grad_impl(c, s_k, data, an, host, L.gk);
+        int rc = evaluate(c, s_k, data, an, host, L.gk);
         if (rc != PMR_OK && rc != PMR_ENAN) return rc;
         if (rc == PMR_OK && host[0] <= L.f + c1 * t * gd) {
             fnew = host[0];

@@ -215,6 +215,14 @@ struct pmr_ctx {
     // timing on, an event is recorded after each launch on the context stream
     int64_t launches = 0;
     bool timing = false;
+    // optional CUDA graph of one loss_and_grad evaluation (pmr_use_graphs)
+    bool graphs = false;
+    cudaGraphExec_t g_exec = nullptr;
+    const float2* g_s = nullptr;
+    const float* g_data = nullptr;
+    float2* g_grad = nullptr;
+    pmr_anneal g_an{};
+    int64_t g_launches = 0;  // kernel launches inside the graph
     std::vector<cudaEvent_t> ev_pool;
     std::vector<const char*> ev_names;
     size_t ev_used = 0;
@@ -275,6 +283,7 @@ int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x,
                     float drift);
 int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad);
 int lpt_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom);
+int pm_init(pmr_ctx* c);
 int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* lam_p, float2* grad, bool have_H);
 int pm_forward_impl(pmr_ctx* c, const float2* s_k);
 int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state

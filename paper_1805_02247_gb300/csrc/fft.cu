@@ -10,6 +10,8 @@
 // mixed-radix (4, 3, 2) Stockham autosort in shared memory with float64-built
 // twiddle tables.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -968,6 +970,22 @@ XFused make_x(const float2* const* in, int nin, float2* const* out, int nout, co
 
 }  // namespace
 
+namespace {
+// A kernel's dynamic shared-memory limit is process-wide while contexts of
+// different mesh sizes may run at once: the limit only ever grows.
+int raise_smem_limit(pmr_ctx* c, const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> set;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[fn];
+    if (bytes <= cur) return PMR_OK;
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes),
+                       "smem attr"));
+    cur = bytes;
+    return PMR_OK;
+}
+}  // namespace
+
 int fft_init(pmr_ctx* c) {
     const int N = c->N, M = N / 2;
     c->plan.N = N;
@@ -988,31 +1006,24 @@ int fft_init(pmr_ctx* c) {
     PMR_TRY(check_cuda(c, cudaMalloc(&c->plan.twM, sizeof(float2) * M), "twiddles"));
     PMR_TRY(check_cuda(c, cudaMemcpy(c->plan.twN, tN.data(), sizeof(float2) * N, cudaMemcpyHostToDevice), "twiddles"));
     PMR_TRY(check_cuda(c, cudaMemcpy(c->plan.twM, tM.data(), sizeof(float2) * M, cudaMemcpyHostToDevice), "twiddles"));
-    size_t big = smem_col(N, 3);
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_x_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_col<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col(N, 2)), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_r2c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, false)), "smem attr"));
+    PMR_TRY(raise_smem_limit(c, (const void*)k_x_fused, smem_col(N, 3)));
+    PMR_TRY(raise_smem_limit(c, (const void*)k_col<true>, smem_col(N, 2)));
+    PMR_TRY(raise_smem_limit(c, (const void*)k_col<false>, smem_col(N, 2)));
+    PMR_TRY(raise_smem_limit(c, (const void*)k_z_r2c, smem_z(N, false)));
+    PMR_TRY(raise_smem_limit(c, (const void*)k_z_c2r, smem_z(N, true)));
     int rc = PMR_OK;
     with_zreg(N, [&](auto rg) {
         using Z = ZReg<decltype(rg)>;
-        const int sz = (int)Z::smem();
-        for (cudaError_t e : {cudaFuncSetAttribute(k_z_r2c_reg<decltype(rg)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
-                              cudaFuncSetAttribute(k_z_c2r_reg<decltype(rg)>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)})
-            if (rc == PMR_OK) rc = check_cuda(c, e, "smem attr");
+        for (const void* fn : {(const void*)k_z_r2c_reg<decltype(rg)>, (const void*)k_z_c2r_reg<decltype(rg)>})
+            if (rc == PMR_OK) rc = raise_smem_limit(c, fn, Z::smem());
     });
     with_reg(N, [&](auto rg) {
         using RG = decltype(rg);
-        const int sz = (int)RG::smem();
-        for (cudaError_t e : {cudaFuncSetAttribute(k_col_reg<RG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
-                              cudaFuncSetAttribute(k_col_reg<RG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
-                              cudaFuncSetAttribute(k_x_reg<RG, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
-                              cudaFuncSetAttribute(k_x_reg<RG, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz),
-                              cudaFuncSetAttribute(k_x_reg<RG, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)})
-            if (rc == PMR_OK) rc = check_cuda(c, e, "smem attr");
+        for (const void* fn : {(const void*)k_col_reg<RG, true>, (const void*)k_col_reg<RG, false>,
+                               (const void*)k_x_reg<RG, 0>, (const void*)k_x_reg<RG, 1>, (const void*)k_x_reg<RG, 2>})
+            if (rc == PMR_OK) rc = raise_smem_limit(c, fn, RG::smem());
     });
     PMR_TRY(rc);
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_z_c2r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z(N, true)), "smem attr"));
     return PMR_OK;
 }
 

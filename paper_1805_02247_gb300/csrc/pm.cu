@@ -581,13 +581,16 @@ int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uin
     } else {
         using T = PaintTile<3>;
         const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-        PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)T::smem),
-                           "smem attr"));
         k_paint_tile<3><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, mass, scale, offset,
                                                           rho[0], rho[1], rho[2]);
     }
     return check_launch(c, nmass <= 1 ? "paint" : "paint3");
+}
+
+int pm_init(pmr_ctx* c) {
+    return check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)PaintTile<3>::smem),
+                      "smem attr");
 }
 
 int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,

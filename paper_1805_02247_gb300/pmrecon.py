@@ -71,6 +71,7 @@ _SIGS = {
     "pmr_smooth": (ctypes.c_int, [_P, _P, ctypes.c_double, _P]),
     "pmr_za_ics": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmr_lpt_ics": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pmr_use_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmr_lpt_ics_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "pmr_growth": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "pmr_lbfgs_direction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _I64, _P]),
@@ -242,6 +243,10 @@ class Context:
             name, n, ms = line.split()
             out[name] = (int(n), float(ms))
         return out
+
+    def use_graphs(self, enable: bool = True):
+        """Replay each loss evaluation as one captured CUDA graph (needs a non-default stream)."""
+        self._check(self._lib.pmr_use_graphs(self._h, 1 if enable else 0))
 
     def lbfgs_reset(self):
         self._check(self._lib.pmr_lbfgs_reset(self._h))
