@@ -85,6 +85,24 @@ def algorithmic(name: str, N: int):
     return table.get(name)
 
 
+# DRAM bytes (read + write) per launch from one-pass ncu counters of the current
+# kernels on this workload (profiles/dram_traffic_256cubed.md; the network
+# backward from the 192^3 capture of profiles/mlp_tc_bwd_192cubed.md scaled by
+# the voxel ratio (256/192)^3). Valid for N = 256 only.
+TRAFFIC_256 = {
+    "mlp_tc_bwd": (114.4e6 + 233.7e6) * (256 / 192) ** 3,
+    "paint": 338.2e6 + 56.1e6,
+    "paint3": 541.5e6 + 184.4e6,
+    "col_pass": 67.7e6 + 8.9e6,
+    "z_c2r": 67.7e6 + 18.0e6,
+    "z_r2c": 67.1e6 + 18.2e6,
+}
+
+
+def measured_traffic(name: str, N: int):
+    return TRAFFIC_256.get(name) if N == 256 else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -226,7 +244,7 @@ def replica_throughput(seconds: float, steps: int, world: int, device):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def _setup_job(dev, **cfg_kw):
+def _setup_job(dev, stream=None, **cfg_kw):
     """A context on the benchmark workload plus its synthetic inputs (untimed)."""
     import torch
 
@@ -235,7 +253,7 @@ def _setup_job(dev, **cfg_kw):
     N = WORK["N"]
     cfg = pmrecon.default_config(N=N, L=WORK["L"], nsteps=WORK["nsteps"], a0=WORK["a0"], **cfg_kw)
     wn = synth.two_net_weights(1) if cfg.head == 1 else synth.xavier_weights(1)
-    ctx = pmrecon.Context(cfg, torch.from_numpy(wn).to(dev))
+    ctx = pmrecon.Context(cfg, torch.from_numpy(wn).to(dev), stream=stream)
     # truth from seed 2, start at 10% power from seed 0
     s_true = ctx.linear_field(torch.from_numpy(synth.white_noise(N, 2)).to(dev), 1.0)
     m_true = ctx.nn_halo_map(ctx.pm_forward(s_true))
@@ -327,10 +345,18 @@ def run_ours(args):
         dist.barrier()
     build.build()  # no-op once fresh
     N = WORK["N"]
-    ctx, s, data, s_true = _setup_job(dev)
+    # the context runs on its own stream so that each evaluation can be replayed
+    # as one captured CUDA graph (pmr_use_graphs); the events below are recorded
+    # on that stream
+    job_stream = torch.cuda.Stream(dev)
+    stream_ctx = torch.cuda.stream(job_stream)
+    stream_ctx.__enter__()
+    ctx, s, data, s_true = _setup_job(dev, stream=job_stream)
     g = ctx.half()
     del s_true
     torch.cuda.synchronize()
+    if not args.no_graphs:
+        ctx.use_graphs(True)
 
     def step():
         ctx.loss_and_grad(s, data, WORK["R_sm"], WORK["M0"], out=g, readback=True)
@@ -360,13 +386,17 @@ def run_ours(args):
     value, ms_max = replica_throughput(ms / 1e3, args.steps, world, dev)
     ms_max *= 1e3
 
-    # ---- per-kernel durations (CUDA events after every launch on the context stream)
+    # ---- per-kernel durations (CUDA events after every launch on the context stream;
+    #      direct launches, since a replayed graph has no per-kernel events)
     ksteps = max(1, min(args.steps, 3))
+    ctx.use_graphs(False)
     ctx.timing(True)
     for _ in range(ksteps):
         step()
     rep = ctx.timing_report()
     ctx.timing(False)
+    if not args.no_graphs:
+        ctx.use_graphs(True)
     total = sum(v[1] for k, v in rep.items() if k != "begin")
     kernels = sorted(((k, n, t_) for k, (n, t_) in rep.items() if k != "begin"), key=lambda r: -r[2])
     peaks, peak_src = measured_peaks()
@@ -379,7 +409,7 @@ def run_ours(args):
         kind, amount = alg
         avg_s = t_ / n / 1e3
         common = {"kernel": name, "share": t_ / total, "avg_launch_ms": avg_s * 1e3, "algorithmic_per_launch": amount,
-                  "traffic": None}
+                  "traffic": measured_traffic(name, N)}
         if kind == "bytes":
             ach = amount / avg_s / 1e9
             return {**common, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -427,6 +457,7 @@ def run_ours(args):
 
     ctx.close()
     del s, data, g
+    stream_ctx.__exit__(None, None, None)
     torch.cuda.empty_cache()
     extra = {}
     if rank == 0 and world == 1 and not args.no_extras:
@@ -439,6 +470,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(), "N": N, "L": WORK["L"], "nsteps": WORK["nsteps"],
                        "parallelism": "replicas" if world > 1 else "single",
+                       "launch": "direct" if args.no_graphs else "one CUDA graph per evaluation",
                        "l2": "inputs larger than L2 (about 10 GB touched per evaluation)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches) * args.steps,
@@ -466,6 +498,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip the other-path measurements")
+    ap.add_argument("--no-graphs", action="store_true", help="launch every kernel directly instead of one graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--N", type=int, default=WORK["N"], help="mesh side (profiling of small cases only)")
     ap.add_argument("--nsteps", type=int, default=WORK["nsteps"], help="PM steps (profiling of small cases only)")

@@ -280,3 +280,33 @@ def test_two_network_annealing_over_sharpness_follows_oracle():
     got = [r["loss"] for r in hist]
     assert got[0] == pytest.approx(ohist[0][0], rel=1e-5)
     assert got[1] == pytest.approx(ohist[1][0], rel=5e-4)
+
+
+def test_graph_replay_matches_direct_launches():
+    # pmr_use_graphs: the captured evaluation gives the same bits as direct launches,
+    # and a change of the anneal parameters re-captures
+    from paper_1805_02247_gb300 import pmrecon
+    N, L, nsteps = 16, 50.0, 2
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        cfg = pmrecon.default_config(N=N, L=L, nsteps=nsteps)
+        ctx = pmrecon.Context(cfg, torch.from_numpy(synth.xavier_weights(1)).cuda(), stream=stream)
+        _, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+        s_dev, d_dev = to_dev(s), to_dev(_data(N, L, nsteps))
+        direct = [ctx.loss_and_grad(s_dev, d_dev, R, 1e8) for R in (4.0, 2.0)]
+        direct = [(p, g.clone()) for p, g in direct]
+        ctx.use_graphs(True)
+        for _ in range(2):  # capture, then replay
+            for (p0, g0), R in zip(direct, (4.0, 2.0)):
+                p1, g1 = ctx.loss_and_grad(s_dev, d_dev, R, 1e8)
+                assert p1 == p0
+                assert torch.equal(g1, g0)
+        stream.synchronize()
+        ctx.close()
+
+
+def test_graphs_need_a_stream():
+    from paper_1805_02247_gb300.pmrecon import PMRError
+    ctx, _ = context(N=8)  # default (legacy) stream
+    with pytest.raises(PMRError, match="EINVAL"):
+        ctx.use_graphs(True)
