@@ -59,8 +59,9 @@ def algorithmic(name: str, N: int):
         "x_conv_1": ("bytes", 16 * NH), "x_conv_3": ("bytes", 32 * NH), "x_conv_in3": ("bytes", 32 * NH),
         "x_fwd_1": ("bytes", 16 * NH), "x_fwd_in3": ("bytes", 32 * NH),
         "x_inv_3": ("bytes", 32 * NH), "x_inv_1": ("bytes", 16 * NH),
-        "paint": ("bytes", (12 + 4 + 4 + 4) * N3),     # positions, perm, offsets -> density
-        "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),
+        "paint": ("bytes", (12 + 4 + 4) * N3),         # sorted offsets, bin starts -> density
+        "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),  # sorted offsets, perm, starts, 3 masses -> 3 meshes
+        "sorted_frac": ("bytes", (4 + 12 + 12) * N3),  # perm, positions -> sorted offsets
         "kick_drift": ("bytes", (12 + 12 + 24 + 12) * N3),  # F, disp in, mom r/w, disp out
         "adj_direct": ("bytes", (12 + 12 + 24 + 24) * N3),  # F, disp, lam_x r/w, lam_p r/w
         "readout_grad": ("bytes", (4 + 12 + 24) * N3),
@@ -91,8 +92,6 @@ def algorithmic(name: str, N: int):
 # the voxel ratio (256/192)^3). Valid for N = 256 only.
 TRAFFIC_256 = {
     "mlp_tc_bwd": (114.4e6 + 233.7e6) * (256 / 192) ** 3,
-    "paint": 338.2e6 + 56.1e6,
-    "paint3": 541.5e6 + 184.4e6,
     "col_pass": 67.7e6 + 8.9e6,
     "z_c2r": 67.7e6 + 18.0e6,
     "z_r2c": 67.1e6 + 18.2e6,

@@ -194,7 +194,7 @@ int pmr_paint(pmr_ctx* ctx, const float* x, int64_t np, const float* mass, float
  * cudaMalloc; code that runs while a CUDA graph is being captured, framework
  * plug-ins whose host owns every device allocation, and loops that must not
  * let cudaMalloc/cudaFree synchronise the device cannot make that call. This
- * variant allocates nothing: its sorting scratch (about 6.3 MB) is one fixed
+ * variant allocates nothing: its sorting scratch (about 9.4 MB) is one fixed
  * array in device memory that every GPU loading the library holds until the
  * process exits. Limits: N^3 <= 262144 (N <= 64) and np <= 262144; larger
  * sizes return PMR_EINVAL. The first call on a device looks up the array's

@@ -101,6 +101,8 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->sort_tmp : nullptr), sizeof(uint32_t) * N3);
     alloc((void**)(c ? &c->perm_all : nullptr), sizeof(uint32_t) * N3 * (cfg.nsteps + 1));
     alloc((void**)(c ? &c->start_all : nullptr), sizeof(uint32_t) * (N3 + 1) * (cfg.nsteps + 1));
+    alloc((void**)(c ? &c->sfrac : nullptr), sizeof(float) * 3 * N3);
+    alloc((void**)(c ? &c->sfrac_all : nullptr), sizeof(float) * 3 * N3 * (cfg.nsteps + 1));
     alloc((void**)(c ? &c->delta : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->F : nullptr), sizeof(float) * 3 * N3);
     alloc((void**)(c ? &c->feat : nullptr), sizeof(float) * 3 * N3);

@@ -185,6 +185,8 @@ struct pmr_ctx {
     // per-step sort of the path's positions, kept from the forward sweep for the
     // adjoint: slot s holds perm [N3] and cell offsets [N3 + 1] of x_s, s = 0..nsteps
     uint32_t* perm_all = nullptr;
+    float* sfrac = nullptr;      // [3][N^3] fractional offsets in the order of perm (paint)
+    float* sfrac_all = nullptr;  // [nsteps+1][3][N^3] the same for every step's sort (reused by the adjoint)
     uint32_t* start_all = nullptr;
 
     // meshes
@@ -288,10 +290,12 @@ int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* 
 int pm_forward_impl(pmr_ctx* c, const float2* s_k);
 int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state
 int density_from(pmr_ctx* c, const float* disp, float* delta);
+// sfrac (nullable): also write the particles' fractional offsets in sorted order, [3][np]
 int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out, uint32_t* perm,
-                   uint32_t* start);
+                   uint32_t* start, float* sfrac);
+// sfrac (nullable): the offsets written by the sort that produced perm/start
 int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uint32_t* perm, const uint32_t* start,
-               const float* mass, int nmass, float scale, float offset, float* const* rho);
+               const float* sfrac, const float* mass, int nmass, float scale, float offset, float* const* rho);
 // density of step s's positions; sort == true sorts them into slot s first,
 // otherwise slot s must already hold their sort (from the forward sweep)
 int density_slot(pmr_ctx* c, int s, const float* disp, float* delta, bool sort);

@@ -29,7 +29,8 @@ constexpr size_t kCounts = up(4 * kMaxCells);
 constexpr size_t kLong = up(4 * kMaxCells);
 constexpr size_t kPart = up(4 * ((kMaxCells + 1023) / 1024));
 constexpr size_t kLongCount = up(16);
-constexpr size_t kScratchBytes = kKeys + kPerm + kTmp + kStart + kCounts + kLong + kPart + kLongCount;
+constexpr size_t kFrac = up(4 * 3 * kMaxParticles);  // sorted fractional offsets, as pmr_paint uses them
+constexpr size_t kScratchBytes = kKeys + kPerm + kTmp + kStart + kCounts + kLong + kPart + kLongCount + kFrac;
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_paint_scratch[kScratchBytes];
@@ -82,7 +83,8 @@ extern "C" int pmr_paint_noalloc(int N, const float* x, int64_t np, const float*
     c.counts = reinterpret_cast<uint32_t*>(p); p += kCounts;
     c.long_list = reinterpret_cast<uint32_t*>(p); p += kLong;
     c.scan_part = reinterpret_cast<uint32_t*>(p); p += kPart;
-    c.long_count = reinterpret_cast<uint32_t*>(p);
+    c.long_count = reinterpret_cast<uint32_t*>(p); p += kLongCount;
+    c.sfrac = reinterpret_cast<float*>(p);
 
     // cell_sort clears the histogram and the long-segment counter itself;
     // every other region is fully written before it is read.

@@ -201,6 +201,18 @@ __global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t np, const u
     perm[start[k] + r] = (uint32_t)i;
 }
 
+// Fractional CIC offsets of the particles in sorted order, for the paints:
+// sfrac[a][j] of particle perm[j] (the same float32 values cell_of gives).
+__global__ void k_sorted_frac(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN,
+                              const uint32_t* __restrict__ perm, float* __restrict__ sfrac) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const Cell cl = cell_of(pos, np, perm[j], lattice, N, fN);
+    sfrac[j] = cl.d[0];
+    sfrac[np + j] = cl.d[1];
+    sfrac[2 * np + j] = cl.d[2];
+}
+
 // Restore ascending particle index inside each cell segment (atomics above
 // leave it arbitrary): short segments by one thread, long ones queued.
 constexpr int kShort = 16;
@@ -331,10 +343,15 @@ struct PaintTile {
     static constexpr size_t smem = sizeof(float) * NM * 8 * NB;
 };
 
-template <int NM>
+// FRAC: the fractional offsets of the sorted particles come precomputed
+// (sfrac[a][j], a = axis, j = sorted index), so a bin's loop reads three
+// coalesced floats per particle instead of recomputing its cell from the
+// position; otherwise each particle's offsets are derived from pos here.
+template <int NM, bool FRAC>
 __global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ pos, int64_t np, bool lattice, int N,
                                                     FastDiv fN, const uint32_t* __restrict__ start,
-                                                    const uint32_t* __restrict__ perm, const float* __restrict__ mass,
+                                                    const uint32_t* __restrict__ perm,
+                                                    const float* __restrict__ sfrac, const float* __restrict__ mass,
                                                     float scale, float offset, float* r0, float* r1, float* r2) {
     constexpr int PTX = PaintTile<NM>::X, PTY = PaintTile<NM>::Y, PTZ = PaintTile<NM>::Z;
     constexpr int PBY = PaintTile<NM>::BY, PBZ = PaintTile<NM>::BZ, PNB = PaintTile<NM>::NB;
@@ -354,8 +371,17 @@ __global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ po
             for (int o = 0; o < 8; ++o) acc[m][o] = 0.f;
         const uint32_t s = start[b], e = start[b + 1];
         for (uint32_t j = s; j < e; ++j) {
-            const int64_t i = perm[j];
-            const Cell cl = cell_of(pos, np, i, lattice, N, fN);
+            Cell cl;
+            int64_t i = 0;
+            if (FRAC) {
+                cl.d[0] = sfrac[j];
+                cl.d[1] = sfrac[np + j];
+                cl.d[2] = sfrac[2 * np + j];
+                if (mass) i = perm[j];
+            } else {
+                i = perm[j];
+                cl = cell_of(pos, np, i, lattice, N, fN);
+            }
             float mv[NM];
 #pragma unroll
             for (int m = 0; m < NM; ++m) mv[m] = mass ? mass[m * np + i] : 1.f;
@@ -536,7 +562,7 @@ __global__ void k_lpt2_hess_grad(const float* __restrict__ sigma, const float* _
 // ============================================================================= host wrappers
 
 int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out, uint32_t* perm,
-                   uint32_t* start) {
+                   uint32_t* start, float* sfrac) {
     const int N = c->N;
     const int64_t N3 = c->N3;
     uint32_t* keys = keys_out ? keys_out : c->keys;
@@ -562,40 +588,54 @@ int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint3
     k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(start, perm, N3, c->long_list, c->long_count);
     PMR_TRY(check_launch(c, "fix_short"));
     k_fix_long<<<304, kT, 0, c->stream>>>(start, perm, c->long_list, c->long_count, c->sort_tmp);
-    return check_launch(c, "fix_long");
+    PMR_TRY(check_launch(c, "fix_long"));
+    if (!sfrac || np == 0) return PMR_OK;
+    k_sorted_frac<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, FastDiv((uint32_t)N), perm, sfrac);
+    return check_launch(c, "sorted_frac");
 }
 
 int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out) {
-    return cell_sort_into(c, pos, np, lattice, keys_out, c->perm, c->cell_start);
+    return cell_sort_into(c, pos, np, lattice, keys_out, c->perm, c->cell_start, c->sfrac);
 }
 
 int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uint32_t* perm, const uint32_t* start,
-               const float* mass, int nmass, float scale, float offset, float* const* rho) {
+               const float* sfrac, const float* mass, int nmass, float scale, float offset, float* const* rho) {
     const int N = c->N;
     const FastDiv fN((uint32_t)N);
     if (nmass <= 1) {
         using T = PaintTile<1>;
         const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-        k_paint_tile<1><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, mass, scale, offset,
-                                                          rho[0], nullptr, nullptr);
+        if (sfrac)
+            k_paint_tile<1, true><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, sfrac, mass,
+                                                                    scale, offset, rho[0], nullptr, nullptr);
+        else
+            k_paint_tile<1, false><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, nullptr,
+                                                                     mass, scale, offset, rho[0], nullptr, nullptr);
     } else {
         using T = PaintTile<3>;
         const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-        k_paint_tile<3><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, mass, scale, offset,
-                                                          rho[0], rho[1], rho[2]);
+        if (sfrac)
+            k_paint_tile<3, true><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, sfrac, mass,
+                                                                    scale, offset, rho[0], rho[1], rho[2]);
+        else
+            k_paint_tile<3, false><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, nullptr,
+                                                                     mass, scale, offset, rho[0], rho[1], rho[2]);
     }
     return check_launch(c, nmass <= 1 ? "paint" : "paint3");
 }
 
 int pm_init(pmr_ctx* c) {
-    return check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)PaintTile<3>::smem),
+                       "smem attr"));
+    return check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)PaintTile<3>::smem),
                       "smem attr");
 }
 
 int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,
           float offset, float* const* rho) {
-    return paint_with(c, pos, np, lattice, c->perm, c->cell_start, mass, nmass, scale, offset, rho);
+    return paint_with(c, pos, np, lattice, c->perm, c->cell_start, c->sfrac, mass, nmass, scale, offset, rho);
 }
 
 int readout(pmr_ctx* c, const float* field, const float* pos, int64_t np, bool lattice, float* out) {
@@ -619,9 +659,10 @@ int density_from(pmr_ctx* c, const float* disp, float* delta) {
 int density_slot(pmr_ctx* c, int s, const float* disp, float* delta, bool sort) {
     uint32_t* perm = c->perm_all + (int64_t)s * c->N3;
     uint32_t* start = c->start_all + (int64_t)s * (c->N3 + 1);
-    if (sort) PMR_TRY(cell_sort_into(c, disp, c->N3, true, nullptr, perm, start));
+    float* sfrac = c->sfrac_all + (int64_t)s * 3 * c->N3;
+    if (sort) PMR_TRY(cell_sort_into(c, disp, c->N3, true, nullptr, perm, start, sfrac));
     float* outs[1] = {delta};
-    return paint_with(c, disp, c->N3, true, perm, start, nullptr, 1, 1.0f, -1.0f, outs);
+    return paint_with(c, disp, c->N3, true, perm, start, sfrac, nullptr, 1, 1.0f, -1.0f, outs);
 }
 
 int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom) {
@@ -764,7 +805,7 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
         PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
         PMR_TRY(adj_kick_direct(c, c->F, d, c->lam_x, c->lam_p, (float)c->kick[s], (float)c->drift[s]));
         PMR_TRY(paint_with(c, d, N3, true, c->perm_all + (int64_t)s * N3, c->start_all + (int64_t)s * (N3 + 1),
-                           c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
+                           c->sfrac_all + (int64_t)s * 3 * N3, c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
         const float* gins[3] = {Gj[0], Gj[1], Gj[2]};
         PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
         PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
