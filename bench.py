@@ -87,11 +87,9 @@ def algorithmic(name: str, N: int):
 
 
 # DRAM bytes (read + write) per launch from one-pass ncu counters of the current
-# kernels on this workload (profiles/dram_traffic_256cubed.md; the network
-# backward from the 192^3 capture of profiles/mlp_tc_bwd_192cubed.md scaled by
-# the voxel ratio (256/192)^3). Valid for N = 256 only.
+# kernels on this workload (profiles/dram_traffic_256cubed.md); kernels changed
+# since their counters were taken have no entry. Valid for N = 256 only.
 TRAFFIC_256 = {
-    "mlp_tc_bwd": (114.4e6 + 233.7e6) * (256 / 192) ** 3,
     "col_pass": 67.7e6 + 8.9e6,
     "z_c2r": 67.7e6 + 18.0e6,
     "z_r2c": 67.1e6 + 18.2e6,

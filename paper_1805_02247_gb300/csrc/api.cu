@@ -114,7 +114,12 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->gm2 : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->gfeat : nullptr), sizeof(float) * 3 * N3);
     if (cfg.nn_path == 2) alloc((void**)(c ? &c->gv : nullptr), sizeof(float) * 81 * N3);
-    else alloc((void**)(c ? &c->gbox : nullptr), sizeof(float) * (size_t)mlp_tc_box_floats((int)N));
+    else {
+        alloc((void**)(c ? &c->gbox : nullptr), sizeof(float) * (size_t)mlp_tc_box_floats((int)N));
+        alloc((void**)(c ? &c->nn_y : nullptr), sizeof(float) * N3);
+        alloc((void**)(c ? &c->nn_m1 : nullptr), sizeof(uint16_t) * 4 * N3);
+        alloc((void**)(c ? &c->nn_m2 : nullptr), sizeof(uint8_t) * 4 * N3);
+    }
     alloc((void**)(c ? &c->cA : nullptr), sizeof(float2) * NH);
     alloc((void**)(c ? &c->cB : nullptr), sizeof(float2) * NH);
     alloc((void**)(c ? &c->c3 : nullptr), sizeof(float2) * 3 * NH);
@@ -372,6 +377,8 @@ int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const pmr_anneal* an, co
     PMR_TRY(check_ctx(c));
     if (!delta || !grad_mass || !grad_delta) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(nn_features(c, delta));
+    // the tensor-core backward starts from the forward's saved activations
+    if (c->cfg.nn_path != 2) PMR_TRY(mlp_forward(c, c->feat, c->M, logistic_a(an)));
     PMR_TRY(mlp_backward(c, c->feat, grad_mass, c->gfeat, logistic_a(an)));
     return features_T(c, c->gfeat, grad_delta);
 }

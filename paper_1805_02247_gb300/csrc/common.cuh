@@ -202,6 +202,9 @@ struct pmr_ctx {
     float* gfeat = nullptr; // 3 * N3
     float* gv = nullptr;    // 81 * N3 network input-gradient scratch (CUDA-core network)
     float* gbox = nullptr;  // per-tile box sums of the input gradient (tensor-core network)
+    float* nn_y = nullptr;      // tensor-core network forward, saved per voxel for its backward: y [N3],
+    uint16_t* nn_m1 = nullptr;  // layer-1 ReLU mask [4][N3] (16 columns each),
+    uint8_t* nn_m2 = nullptr;   // layer-2 ReLU mask [4][N3] (8 columns each)
     float2* cA = nullptr;   // complex work arrays, NH each
     float2* cB = nullptr;
     float2* c3 = nullptr;   // 3 * NH

@@ -15,6 +15,9 @@
 // Backward per tile (after the forward): g_a2 = w3 g_y [a2 > 0]
 //                     A3 = g_a2[128 x 32] x W2 -> D3 = g_a1 (pre-mask) [128 x 64]
 //                     A4 = g_a1 [a1 > 0] [128 x 64] x W1 -> D4 = g_v[128 x 96]
+// The forward saves, per voxel, y and the ReLU masks of both hidden layers
+// (16 bytes); the backward starts from them at layer 3 instead of recomputing
+// layers 1-2 (halo, operand build, two MMA layers and their epilogues).
 // The backward stages g_v (81 columns) in shared memory and sums it per target
 // cell of the tile's box (the tile grown by one cell, 3 fields x 4 x 6 x 18), so
 // a tile writes 1296 floats instead of 81 x 128; k_stencil_tiles adds the
@@ -244,11 +247,19 @@ struct TileMap {
     int64_t N3;
 };
 
+// Saved activations of the forward: y[N3], layer-1 mask m1[4][N3] (16 bits per
+// column block), layer-2 mask m2[4][N3] (8 bits per column block).
+struct Saved {
+    float* y;
+    uint16_t* m1;
+    uint8_t* m2;
+};
+
 template <bool BWD, bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NT, 1)
     k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
              TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ M_out,
-             float* __restrict__ gbox, int* __restrict__ err) {
+             float* __restrict__ gbox, Saved sv, int* __restrict__ err) {
     using L = Lay<BF>;
     constexpr int K1 = L::K1;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -314,14 +325,31 @@ __global__ void __launch_bounds__(NT, 1)
         z0 = tz * TZ;
     };
     float hv[HALO_PER];
-    float gm_next = 0.f;  // backward: this thread's g_M of the next tile (rows tid < TM)
+    // backward, loaded one tile ahead: g_M, y and the centre values of rows tid < TM;
+    // the saved masks of this thread's row and column block
+    float gm_next = 0.f, y_next = 0.f, f_next[3] = {0.f, 0.f, 0.f};
+    uint32_t m1_next = 0, m2_next = 0;
     auto load_halo = [&](int tile) {
         if (tile >= ntiles) return;
         int x0, y0, z0;
         tile_origin(tile, x0, y0, z0);
-        if (BWD && tid < TM) {
-            const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
-            gm_next = (gx < N && gy < N && gz < N) ? gM[((int64_t)gx * N + gy) * N + gz] : 0.f;
+        if (BWD) {
+            if (tid < TM) {
+                const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
+                const bool in = gx < N && gy < N && gz < N;
+                const int64_t v = ((int64_t)gx * N + gy) * N + gz;
+                gm_next = in ? gM[v] : 0.f;
+                y_next = in ? sv.y[v] : 0.f;
+                if (TWO_NET)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) f_next[c] = in ? feat[c * N3 + v] : 0.f;
+            }
+            const int gx = x0 + (row >> 6), gy = y0 + ((row >> 4) & 3), gz = z0 + (row & 15);
+            const bool in = gx < N && gy < N && gz < N;
+            const int64_t v = ((int64_t)gx * N + gy) * N + gz;
+            m1_next = in ? sv.m1[cb * N3 + v] : 0u;
+            m2_next = in ? sv.m2[cb * N3 + v] : 0u;
+            return;  // the backward needs no halo
         }
 #pragma unroll
         for (int q = 0; q < HALO_PER; ++q) {
@@ -339,7 +367,13 @@ __global__ void __launch_bounds__(NT, 1)
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         int x0, y0, z0;
         tile_origin(tile, x0, y0, z0);
+        // this thread's TMEM row as a voxel
+        const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
+        const bool row_in = row_gx < N && row_gy < N && row_gz < N;
+        const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
+        uint32_t mask1 = 0, mask2 = 0;
 
+        if constexpr (!BWD) {
         // (a) this tile's halo (loaded during the previous tile) -> shared memory,
         //     then start loading the next tile's
 #pragma unroll
@@ -347,7 +381,6 @@ __global__ void __launch_bounds__(NT, 1)
             const int t = tid + q * NT;
             if (t < HALO) halo[t] = hv[q];
         }
-        const float gm_cur = gm_next;
         __syncthreads();
         load_halo(tile + gridDim.x);
 
@@ -393,6 +426,7 @@ __global__ void __launch_bounds__(NT, 1)
                 mask1 |= (pre > 0.f ? 1u : 0u) << j;
                 z[j] = fmaxf(pre, 0.f);
             }
+            if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
             put8<BF>(Ahi, Alo, row, 16 * cb, z);
             put8<BF>(Ahi, Alo, row, 16 * cb + 8, z + 8);
         }
@@ -425,6 +459,7 @@ __global__ void __launch_bounds__(NT, 1)
                 s = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), s);
             }
             part[cb * TM + row] = s;
+            if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
         }
         __syncthreads();
         if (tid < TM) {
@@ -434,36 +469,49 @@ __global__ void __launch_bounds__(NT, 1)
             const bool in = gx < N && gy < N && gz < N;
             const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
             const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
+            if (sv.y && in) sv.y[vox] = y;
             if (TWO_NET) {
                 // two-network head (Sec. 2.1): M = M_scale logistic(y, a) NNm(f), f = the voxel's own values
                 float f[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
                 const float p = sigmoidf(a * y);
-                if (!BWD) {
-                    float u0, u1, u2;
-                    if (in) M_out[vox] = M_scale * p * mass_net<false>(vec + VEC_MASS, f[0], f[1], f[2], 0.f, u0, u1, u2);
-                } else {
-                    const float g = in ? gm_cur * M_scale : 0.f;
+                float u0, u1, u2;
+                if (in) M_out[vox] = M_scale * p * mass_net<false>(vec + VEC_MASS, f[0], f[1], f[2], 0.f, u0, u1, u2);
+            } else {
+                if (in) M_out[vox] = M_scale * softplusf(y);
+            }
+        }
+            tc_fence_before();
+            __syncthreads();
+            continue;
+        } else {
+            // (s) the forward's saved activations of this tile (loaded during the previous one)
+            mask1 = m1_next;
+            mask2 = m2_next;
+            const float gm_cur = gm_next, y_cur = y_next;
+            const float f_cur[3] = {f_next[0], f_next[1], f_next[2]};
+            load_halo(tile + gridDim.x);
+            if (tid < TM) {
+                const int r = tid;
+                const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
+                const bool in = gx < N && gy < N && gz < N;
+                const float g = in ? gm_cur * M_scale : 0.f;
+                if (TWO_NET) {
+                    // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
+                    const float p = sigmoidf(a * y_cur);
                     float g0, g1, g2;
-                    const float m = mass_net<true>(vec + VEC_MASS, f[0], f[1], f[2], g * p, g0, g1, g2);
+                    const float m = mass_net<true>(vec + VEC_MASS, f_cur[0], f_cur[1], f_cur[2], g * p, g0, g1, g2);
                     gys[r] = g * m * a * p * (1.f - p);
                     gcen[r] = g0;
                     gcen[TM + r] = g1;
                     gcen[2 * TM + r] = g2;
+                } else {
+                    gys[r] = g * sigmoidf(y_cur);
                 }
-            } else if (!BWD) {
-                if (in) M_out[vox] = M_scale * softplusf(y);
-            } else {
-                gys[r] = in ? gm_cur * M_scale * sigmoidf(y) : 0.f;
             }
-        }
-        if (!BWD) {
-            tc_fence_before();
             __syncthreads();
-            continue;
         }
-        __syncthreads();
 
         // (g) backward: A3 = g_a2 = w3 g_y [a2 > 0] (this thread's 8 columns)
         {
@@ -713,11 +761,12 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     const float Ms = (float)c->cfg.M_scale;
     const uint32_t smem = BWD ? L::SMEM_BWD : L::SMEM_FWD;
     float* gv = BWD ? c->gbox : nullptr;
+    const Saved sv{c->nn_y, c->nn_m1, c->nn_m2};  // written by the forward, read by the backward
     if (c->cfg.head == 1)
-        k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv,
+        k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv, sv,
                                                                c->tc_err);
     else
-        k_mlp_tc<BWD, false, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv,
+        k_mlp_tc<BWD, false, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv, sv,
                                                                 c->tc_err);
     return check_launch(c, BWD ? "mlp_tc_bwd" : "mlp_tc_fwd");
 }
