@@ -213,6 +213,17 @@ __global__ void k_sorted_frac(const float* __restrict__ pos, int64_t np, bool la
     sfrac[2 * np + j] = cl.d[2];
 }
 
+// out[m][j] = in[m][perm[j]]: per-particle values into the order of a sort
+__global__ void k_permute3(const uint32_t* __restrict__ perm, const float* __restrict__ in, int64_t np,
+                           float* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const int64_t i = perm[j];
+    out[j] = in[i];
+    out[np + j] = in[np + i];
+    out[2 * np + j] = in[2 * np + i];
+}
+
 // Restore ascending particle index inside each cell segment (atomics above
 // leave it arbitrary): short segments by one thread, long ones queued.
 constexpr int kShort = 16;
@@ -347,7 +358,7 @@ struct PaintTile {
 // (sfrac[a][j], a = axis, j = sorted index), so a bin's loop reads three
 // coalesced floats per particle instead of recomputing its cell from the
 // position; otherwise each particle's offsets are derived from pos here.
-template <int NM, bool FRAC>
+template <int NM, bool FRAC, bool SMASS = false>
 __global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ pos, int64_t np, bool lattice, int N,
                                                     FastDiv fN, const uint32_t* __restrict__ start,
                                                     const uint32_t* __restrict__ perm,
@@ -377,7 +388,7 @@ __global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ po
                 cl.d[0] = sfrac[j];
                 cl.d[1] = sfrac[np + j];
                 cl.d[2] = sfrac[2 * np + j];
-                if (mass) i = perm[j];
+                if (mass) i = SMASS ? (int64_t)j : (int64_t)perm[j];  // SMASS: masses already in sorted order
             } else {
                 i = perm[j];
                 cl = cell_of(pos, np, i, lattice, N, fN);
@@ -624,9 +635,31 @@ int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uin
     return check_launch(c, nmass <= 1 ? "paint" : "paint3");
 }
 
+// Three-mass paint of the lattice particles with their masses first moved into
+// the sort's order, so the paint's bin loop reads offsets and masses as
+// independent, coalesced loads. Scratch: c->F (the adjoint step has used the
+// force by then; the next step recomputes it).
+int paint3_sorted(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
+                  float scale, float* const* rho) {
+    const int N = c->N;
+    const int64_t np = c->N3;
+    float* smass = c->F;
+    k_permute3<<<nblocks(np, kT), kT, 0, c->stream>>>(perm, mass, np, smass);
+    PMR_TRY(check_launch(c, "permute3"));
+    using T = PaintTile<3>;
+    const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
+    k_paint_tile<3, true, true><<<grid, 256, T::smem, c->stream>>>(nullptr, np, true, N, FastDiv((uint32_t)N), start,
+                                                                  perm, sfrac, smass, scale, 0.0f, rho[0], rho[1],
+                                                                  rho[2]);
+    return check_launch(c, "paint3");
+}
+
 int pm_init(pmr_ctx* c) {
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)PaintTile<3>::smem),
+                       "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, true, true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PaintTile<3>::smem),
                        "smem attr"));
     return check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)PaintTile<3>::smem),
@@ -804,8 +837,8 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
         PMR_TRY(density_slot(c, s, d, c->delta, false));  // the forward sweep's sort of x_s
         PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
         PMR_TRY(adj_kick_direct(c, c->F, d, c->lam_x, c->lam_p, (float)c->kick[s], (float)c->drift[s]));
-        PMR_TRY(paint_with(c, d, N3, true, c->perm_all + (int64_t)s * N3, c->start_all + (int64_t)s * (N3 + 1),
-                           c->sfrac_all + (int64_t)s * 3 * N3, c->lam_p, 3, (float)c->kick[s], 0.0f, Gj));
+        PMR_TRY(paint3_sorted(c, c->perm_all + (int64_t)s * N3, c->start_all + (int64_t)s * (N3 + 1),
+                              c->sfrac_all + (int64_t)s * 3 * N3, c->lam_p, (float)c->kick[s], Gj));
         const float* gins[3] = {Gj[0], Gj[1], Gj[2]};
         PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
         PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
