@@ -61,12 +61,14 @@ def algorithmic(name: str, N: int):
         "x_inv_3": ("bytes", 32 * NH), "x_inv_1": ("bytes", 16 * NH),
         "paint": ("bytes", (12 + 4 + 4) * N3),         # sorted offsets, bin starts -> density
         "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),  # sorted offsets, perm, starts, 3 masses -> 3 meshes
-        "sorted_frac": ("bytes", (4 + 12 + 12) * N3),  # perm, positions -> sorted offsets
+        "seg_fix": ("bytes", (4 + 8 + 12 + 12) * N3),  # starts, perm r/w, positions -> sorted offsets
+        "scan_reduce": ("bytes", 4 * N3),
+        "scan_apply": ("bytes", 8 * N3),
         "kick_drift": ("bytes", (12 + 12 + 24 + 12) * N3),  # F, disp in, mom r/w, disp out
         "adj_direct": ("bytes", (12 + 12 + 24 + 24) * N3),  # F, disp, lam_x r/w, lam_p r/w
         "readout_grad": ("bytes", (4 + 12 + 24) * N3),
-        "keys": ("bytes", (12 + 4 + 4) * N3),
-        "scatter": ("bytes", (4 + 4 + 4 + 4) * N3),
+        "keys": ("bytes", (12 + 4 + 4 + 8) * N3),  # positions -> keys, ranks; counts r/w
+        "scatter": ("bytes", (4 + 4 + 4 + 4) * N3),  # keys, ranks, starts -> perm
         "stencil_T": ("bytes", (81 + 3) * 4 * N3),
         "mlp_fwd": ("flops", MLP_FWD_FLOP * N3),
         "mlp_bwd": ("flops", MLP_BWD_FLOP * N3),

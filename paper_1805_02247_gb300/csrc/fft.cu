@@ -701,21 +701,33 @@ struct ZReg {
     static constexpr int M = RG::N, G = RG::G;
     static constexpr int R = (128 / G) < 8 ? 8 : 128 / G;  // rows per block
     static constexpr int T = R * G;
-    static constexpr int LDA = M + 8;                       // row pitch of the staging buffer
-    static constexpr int LDS = RG::N1 * (RG::N2 + 1);       // row pitch of the transpose buffer
-    static constexpr size_t smem() { return sizeof(float2) * (size_t)(M + 2 * M + R * (LDA + 1) + R * LDS); }
+    // Row pitch of the staging buffer, which also holds the row's transpose
+    // (the four-step's S aliases its row): wide enough for both, and = 8 mod 16
+    // float2 so the rows of one warp fall on alternating halves of the banks.
+    static constexpr int NEED = (M + 9) > RG::N1 * (RG::N2 + 1) ? (M + 9) : RG::N1 * (RG::N2 + 1);
+    static constexpr int PITCH = (NEED + 7) / 16 * 16 + 8;
+    static constexpr size_t smem() { return sizeof(float2) * (size_t)(M + 2 * M + R * PITCH); }
+    static_assert(G <= 32 && 32 % G == 0, "a row's threads lie in one warp");
 };
 
-// four-step M-point transform of row r (natural order in A -> natural order in A)
+// four-step M-point transform of row r (natural order in A -> natural order in A).
+// The G threads of a row are lanes of one warp and the transpose buffer S is
+// the row's own staging memory, so warp barriers order the steps.
 template <class RG, bool INV>
-__device__ __forceinline__ void row_fft(float2* A, float2* S, const float2* tw, int g) {
+__device__ __forceinline__ void row_fft(float2* A, const float2* tw, int g) {
     constexpr int N1 = RG::N1, N2 = RG::N2, G = RG::G;
+    float2* S = A;
     float2 v1[RG::A1][N1];
 #pragma unroll
     for (int a = 0; a < RG::A1; ++a) {
         const int n2 = g + G * a;
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) v1[a][n1] = A[N2 * n1 + n2];
+    }
+    __syncwarp();  // the row is in registers before S overwrites it
+#pragma unroll
+    for (int a = 0; a < RG::A1; ++a) {
+        const int n2 = g + G * a;
         dft_reg<N1, INV, N2>(v1[a], tw);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
@@ -728,13 +740,18 @@ __device__ __forceinline__ void row_fft(float2* A, float2* S, const float2* tw, 
             S[k1 * (N2 + 1) + n2] = v;
         }
     }
-    __syncthreads();
+    __syncwarp();
     float2 v2[RG::A2][N2];
 #pragma unroll
     for (int a = 0; a < RG::A2; ++a) {
         const int k1 = g + G * a;
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v2[a][n2] = S[k1 * (N2 + 1) + n2];
+    }
+    __syncwarp();  // S read before the result overwrites it
+#pragma unroll
+    for (int a = 0; a < RG::A2; ++a) {
+        const int k1 = g + G * a;
         dft_reg<N2, INV, N1>(v2[a], tw);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) A[k1 + N1 * k2] = v2[a][k2];
@@ -751,8 +768,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
     extern __shared__ float2 sm[];
     float2* s_twM = sm;
     float2* s_twN = s_twM + M;
-    float2* A = s_twN + N;                    // [R][LDA + 1]
-    float2* S = A + Z::R * (Z::LDA + 1);      // [R][LDS]
+    float2* A = s_twN + N;                    // [R][PITCH]
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * Z::R;
     const int rows = (int)min((int64_t)Z::R, nrows - row0);
@@ -771,17 +787,17 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
 #pragma unroll
         for (int q = 0; q < LD; ++q) {
             const int t = tid + q * Z::T, r = t / M, m = t - r * M;
-            if (t < Z::R * M) A[r * (Z::LDA + 1) + m] = v[q];
+            if (t < Z::R * M) A[r * Z::PITCH + m] = v[q];
         }
     }
     __syncthreads();
     const int r = tid / Z::G, g = tid - r * Z::G;
-    row_fft<RG, false>(A + r * (Z::LDA + 1), S + r * Z::LDS, s_twM, g);
+    row_fft<RG, false>(A + r * Z::PITCH, s_twM, g);
     // X_k = E_k + exp(-2 pi i k / N) O_k from Z_k and conj(Z_(M-k))
     for (int t = tid; t < Z::R * P; t += Z::T) {
         const int rr = t / P, k = t - rr * P;
         if (rr >= rows) continue;
-        const float2* Zr = A + rr * (Z::LDA + 1);
+        const float2* Zr = A + rr * Z::PITCH;
         float2 zk = Zr[k == M ? 0 : k];
         float2 zc = Zr[k == 0 ? 0 : M - k];
         zc.y = -zc.y;
@@ -801,8 +817,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     extern __shared__ float2 sm[];
     float2* s_twM = sm;
     float2* s_twN = s_twM + M;
-    float2* A = s_twN + N;                    // [R][LDA + 1]: the P inputs, then z
-    float2* S = A + Z::R * (Z::LDA + 1);      // [R][LDS]
+    float2* A = s_twN + N;                    // [R][PITCH]: the P inputs, then z
     const int tid = threadIdx.x;
     const int64_t row0 = (int64_t)blockIdx.x * Z::R;
     const int rows = (int)min((int64_t)Z::R, nrows - row0);
@@ -820,7 +835,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
 #pragma unroll
         for (int q = 0; q < LD; ++q) {
             const int t = tid + q * Z::T, r = t / P, k = t - r * P;
-            if (t < Z::R * P) A[r * (Z::LDA + 1) + k] = v[q];
+            if (t < Z::R * P) A[r * Z::PITCH + k] = v[q];
         }
     }
     __syncthreads();
@@ -828,7 +843,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     // are updated by one thread so the row can be rewritten in place
     for (int t = tid; t < Z::R * (M / 2 + 1); t += Z::T) {
         const int rr = t / (M / 2 + 1), k = t - rr * (M / 2 + 1);
-        float2* Xr = A + rr * (Z::LDA + 1);
+        float2* Xr = A + rr * Z::PITCH;
         const int kc = M - k;
         float2 xk = Xr[k], xc = Xr[kc];
         if (k == 0) {  // X_0 and X_M: imaginary parts carry nothing for a real signal
@@ -859,12 +874,12 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     }
     __syncthreads();
     const int r = tid / Z::G, g = tid - r * Z::G;
-    row_fft<RG, true>(A + r * (Z::LDA + 1), S + r * Z::LDS, s_twM, g);
+    row_fft<RG, true>(A + r * Z::PITCH, s_twM, g);
     float2* dst = reinterpret_cast<float2*>(out + row0 * N);
     const float sc = scale * 2.0f / (float)N;
     for (int t = tid; t < Z::R * M; t += Z::T) {
         const int rr = t / M, m = t - rr * M;
-        if (rr < rows) dst[(int64_t)rr * M + m] = cscale(A[rr * (Z::LDA + 1) + m], sc);
+        if (rr < rows) dst[(int64_t)rr * M + m] = cscale(A[rr * Z::PITCH + m], sc);
     }
 }
 

@@ -100,52 +100,44 @@ __device__ __forceinline__ void dwgt(const Cell& c, int o, float g[3]) {
 // ----------------------------------------------------------------------------- sort
 
 __global__ void k_keys(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN, uint32_t* __restrict__ keys,
-                       uint32_t* __restrict__ counts) {
+                       uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     uint32_t k = key_of(cell_of(pos, np, i, lattice, N, fN), N);
     keys[i] = k;
-    atomicAdd(&counts[k], 1u);  // integer: order-independent
+    // the particle's slot in its cell (arbitrary among the cell's particles;
+    // k_seg_fix restores ascending particle index)
+    rank[i] = atomicAdd(&counts[k], 1u);
 }
 
-// Exclusive scan, three phases. Phase 1: per-block scan of 4 * kT elements.
-constexpr int kScanPer = 4;
-__global__ void k_scan_local(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
-                             uint32_t* __restrict__ part) {
-    __shared__ uint32_t warp_tot[kT / 32];
-    const int64_t base = ((int64_t)blockIdx.x * kT + threadIdx.x) * kScanPer;
-    uint32_t v[kScanPer], s = 0;
+// Exclusive scan of the cell counts, reduce-then-scan: k_scan_reduce sums each
+// block's kScanBlock counts, k_scan_part scans the block sums (one block),
+// k_scan_apply scans each block from its offset.
+constexpr int kScanT = 256, kScanPerT = 16, kScanBlock = kScanT * kScanPerT;
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
 #pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        v[k] = (base + k < n) ? in[base + k] : 0u;
-        s += v[k];
-    }
-    // inclusive warp scan of per-thread sums
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t inc = s;
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+__global__ void __launch_bounds__(kScanT) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                                                        uint32_t* __restrict__ part) {
+    __shared__ uint32_t wsum[kScanT / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
+    uint32_t s = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += t;
+    for (int k = 0; k < kScanPerT; ++k) {
+        const int64_t i = b0 + k * kScanT + threadIdx.x;
+        if (i < n) s += in[i];
     }
-    if (lane == 31) warp_tot[wid] = inc;
+    s = warp_sum_u32(s);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (wid == 0) {
-        uint32_t t = (lane < kT / 32) ? warp_tot[lane] : 0u, ti = t;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t u = __shfl_up_sync(0xffffffffu, ti, d);
-            if (lane >= d) ti += u;
-        }
-        if (lane < kT / 32) warp_tot[lane] = ti - t;  // exclusive
-        if (lane == kT / 32 - 1) part[blockIdx.x] = ti;
-    }
-    __syncthreads();
-    uint32_t run = warp_tot[wid] + inc - s;
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-        if (base + k < n) out[base + k] = run;
-        run += v[k];
+    if (threadIdx.x < 32) {
+        uint32_t t = threadIdx.x < kScanT / 32 ? wsum[threadIdx.x] : 0u;
+        t = warp_sum_u32(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
 }
 
@@ -187,30 +179,65 @@ __global__ void __launch_bounds__(kScanPartT) k_scan_part(uint32_t* __restrict__
     if (threadIdx.x == 0) *total_out = carry;
 }
 
-__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t n, const uint32_t* __restrict__ part) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] += part[i / (kT * kScanPer)];
+// shared-memory index with one padding word per 32, so a thread's run of
+// kScanPerT consecutive elements and a warp's run of 32 are both conflict-free
+__device__ __forceinline__ int scan_sidx(int e) { return e + (e >> 5); }
+
+__global__ void __launch_bounds__(kScanT) k_scan_apply(const uint32_t* __restrict__ in, int64_t n,
+                                                       const uint32_t* __restrict__ part, uint32_t* __restrict__ out) {
+    __shared__ uint32_t tile[kScanBlock + kScanBlock / 32];
+    __shared__ uint32_t wtot[kScanT / 32];
+    const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < kScanPerT; ++k) {
+        const int e = k * kScanT + tid;
+        tile[scan_sidx(e)] = b0 + e < n ? in[b0 + e] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanPerT], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPerT; ++k) {
+        v[k] = tile[scan_sidx(tid * kScanPerT + k)];
+        s += v[k];
+    }
+    uint32_t inc = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += t;
+    }
+    if (lane == 31) wtot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < kScanT / 32 ? wtot[lane] : 0u, ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, ti, d);
+            if (lane >= d) ti += u;
+        }
+        if (lane < kScanT / 32) wtot[lane] = ti - t;
+    }
+    __syncthreads();
+    uint32_t run = part[blockIdx.x] + wtot[wid] + inc - s;
+#pragma unroll
+    for (int k = 0; k < kScanPerT; ++k) {
+        tile[scan_sidx(tid * kScanPerT + k)] = run;
+        run += v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanPerT; ++k) {
+        const int e = k * kScanT + tid;
+        if (b0 + e < n) out[b0 + e] = tile[scan_sidx(e)];
+    }
 }
 
-__global__ void k_scatter(const uint32_t* __restrict__ keys, int64_t np, const uint32_t* __restrict__ start,
-                          uint32_t* __restrict__ fill, uint32_t* __restrict__ perm) {
+__global__ void k_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank, int64_t np,
+                          const uint32_t* __restrict__ start, uint32_t* __restrict__ perm) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    uint32_t k = keys[i];
-    uint32_t r = atomicAdd(&fill[k], 1u);
-    perm[start[k] + r] = (uint32_t)i;
-}
-
-// Fractional CIC offsets of the particles in sorted order, for the paints:
-// sfrac[a][j] of particle perm[j] (the same float32 values cell_of gives).
-__global__ void k_sorted_frac(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN,
-                              const uint32_t* __restrict__ perm, float* __restrict__ sfrac) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
-    const Cell cl = cell_of(pos, np, perm[j], lattice, N, fN);
-    sfrac[j] = cl.d[0];
-    sfrac[np + j] = cl.d[1];
-    sfrac[2 * np + j] = cl.d[2];
+    perm[start[keys[i]] + rank[i]] = (uint32_t)i;
 }
 
 // out[m][j] = in[m][perm[j]]: per-particle values into the order of a sort
@@ -224,62 +251,132 @@ __global__ void k_permute3(const uint32_t* __restrict__ perm, const float* __res
     out[2 * np + j] = in[2 * np + i];
 }
 
-// Restore ascending particle index inside each cell segment (atomics above
-// leave it arbitrary): short segments by one thread, long ones queued.
-constexpr int kShort = 16;
-__global__ void k_fix_short(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm, int64_t ncell,
-                            uint32_t* __restrict__ long_list, uint32_t* __restrict__ long_count) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    uint32_t s = start[c], e = start[c + 1], len = e - s;
-    if (len <= 1) return;
-    if (len > kShort) {
-        uint32_t slot = atomicAdd(long_count, 1u);
-        long_list[slot] = (uint32_t)c;
-        return;
+// Ascending particle index inside every cell segment (the scatter leaves it
+// arbitrary), then, with sfrac, every particle's fractional CIC offsets in the
+// sorted order: sfrac[a][j] of particle perm[j] (the float32 values cell_of
+// gives). A block owns kFixCells consecutive cells, whose particles are one
+// contiguous run of perm: the run is staged in shared memory, segments of up
+// to kSegShort particles are insertion-sorted by one thread each, longer ones
+// rank-sorted by the whole block (indices are distinct), and the run is
+// written back with coalesced stores. A run longer than kFixCap is listed in
+// ovf for k_seg_fix_big, which does the same in global memory.
+constexpr int kFixCells = 512, kFixT = 256, kFixCap = 5120, kSegShort = 32;
+
+__device__ __forceinline__ void write_sorted(uint32_t i, int64_t j, const float* __restrict__ pos, int64_t np,
+                                             bool lattice, int N, const FastDiv& fN, uint32_t* __restrict__ perm,
+                                             float* __restrict__ sfrac) {
+    perm[j] = i;
+    if (sfrac) {
+        const Cell cl = cell_of(pos, np, i, lattice, N, fN);
+        sfrac[j] = cl.d[0];
+        sfrac[np + j] = cl.d[1];
+        sfrac[2 * np + j] = cl.d[2];
     }
-    // sorting networks on registers (padding UINT_MAX sorts last): 4 elements
-    // (5 compare-exchanges) for the common short case, else odd-even
-    // transposition over 16
-    uint32_t v[kShort];
-#pragma unroll
-    for (int k = 0; k < kShort; ++k) v[k] = (k < (int)len) ? perm[s + k] : 0xffffffffu;
-#define PMR_CE(a, b)                                 \
-    {                                                \
-        const uint32_t lo_ = min(v[a], v[b]);        \
-        v[b] = max(v[a], v[b]);                      \
-        v[a] = lo_;                                  \
-    }
-    if (len <= 4) {
-        PMR_CE(0, 1) PMR_CE(2, 3) PMR_CE(0, 2) PMR_CE(1, 3) PMR_CE(1, 2)
-    } else {
-#pragma unroll
-        for (int round = 0; round < kShort; ++round) {
-#pragma unroll
-            for (int k = round & 1; k + 1 < kShort; k += 2) PMR_CE(k, k + 1)
-        }
-    }
-#undef PMR_CE
-#pragma unroll
-    for (int k = 0; k < kShort; ++k)
-        if (k < (int)len) perm[s + k] = v[k];
 }
 
-// Long segments: one block per listed cell, rank sort (values are distinct).
-__global__ void k_fix_long(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
-                           const uint32_t* __restrict__ long_list, const uint32_t* __restrict__ long_count,
-                           uint32_t* __restrict__ tmp) {
-    const uint32_t nl = *long_count;
-    for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
-        const uint32_t c = long_list[li];
-        const uint32_t s = start[c], len = start[c + 1] - s;
-        for (uint32_t a = threadIdx.x; a < len; a += blockDim.x) {
-            uint32_t va = perm[s + a], rank = 0;
-            for (uint32_t b = 0; b < len; ++b) rank += (perm[s + b] < va);
-            tmp[s + rank] = va;
+__global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
+                                                   int64_t ncell, const float* __restrict__ pos, int64_t np,
+                                                   bool lattice, int N, FastDiv fN, float* __restrict__ sfrac,
+                                                   uint32_t* __restrict__ ovf, uint32_t* __restrict__ novf) {
+    __shared__ uint32_t buf[kFixCap];
+    __shared__ uint32_t out2[kFixCap];
+    __shared__ uint32_t sst[kFixCells + 1];
+    __shared__ uint32_t longs[kFixCells];
+    __shared__ int nlong;
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * kFixCells;
+    const int nc = (int)min((int64_t)kFixCells, ncell - c0);
+    for (int t = tid; t <= nc; t += kFixT) sst[t] = start[c0 + t];
+    if (tid == 0) nlong = 0;
+    __syncthreads();
+    const uint32_t s0 = sst[0];
+    const int n = (int)(sst[nc] - s0);
+    if (n > kFixCap) {
+        if (tid == 0) ovf[atomicAdd(novf, 1u)] = blockIdx.x;
+        return;
+    }
+    for (int j = tid; j < n; j += kFixT) buf[j] = perm[s0 + j];
+    __syncthreads();
+    for (int cl = tid; cl < nc; cl += kFixT) {
+        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
+        if (e - a <= 1) continue;
+        if (e - a > kSegShort) {
+            longs[atomicAdd(&nlong, 1)] = cl;
+            continue;
+        }
+        for (int p = a + 1; p < e; ++p) {
+            const uint32_t v = buf[p];
+            int q = p - 1;
+            while (q >= a && buf[q] > v) {
+                buf[q + 1] = buf[q];
+                --q;
+            }
+            buf[q + 1] = v;
+        }
+    }
+    __syncthreads();
+    const int nl = nlong;
+    for (int li = 0; li < nl; ++li) {
+        const int cl = longs[li];
+        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
+        for (int p = a + tid; p < e; p += kFixT) {
+            const uint32_t v = buf[p];
+            int r = 0;
+            for (int q = a; q < e; ++q) r += buf[q] < v;
+            out2[a + r] = v;
+        }
+    }
+    __syncthreads();
+    for (int li = 0; li < nl; ++li) {
+        const int cl = longs[li];
+        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
+        for (int p = a + tid; p < e; p += kFixT) buf[p] = out2[p];
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += kFixT) write_sorted(buf[j], (int64_t)s0 + j, pos, np, lattice, N, fN, perm, sfrac);
+}
+
+// The runs k_seg_fix could not stage: the same steps on global memory, one
+// block per listed run; tmp is scratch of np entries.
+__global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
+                                                       int64_t ncell, const float* __restrict__ pos, int64_t np,
+                                                       bool lattice, int N, FastDiv fN, float* __restrict__ sfrac,
+                                                       const uint32_t* __restrict__ ovf,
+                                                       const uint32_t* __restrict__ novf, uint32_t* __restrict__ tmp) {
+    const uint32_t no = *novf;
+    const int tid = threadIdx.x;
+    for (uint32_t bi = blockIdx.x; bi < no; bi += gridDim.x) {
+        const int64_t c0 = (int64_t)ovf[bi] * kFixCells;
+        const int nc = (int)min((int64_t)kFixCells, ncell - c0);
+        for (int cl = tid; cl < nc; cl += kFixT) {
+            const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
+            if (e - a <= 1 || e - a > (uint32_t)kSegShort) continue;
+            for (uint32_t p = a + 1; p < e; ++p) {
+                const uint32_t v = perm[p];
+                uint32_t q = p;
+                while (q > a && perm[q - 1] > v) {
+                    perm[q] = perm[q - 1];
+                    --q;
+                }
+                perm[q] = v;
+            }
         }
         __syncthreads();
-        for (uint32_t a = threadIdx.x; a < len; a += blockDim.x) perm[s + a] = tmp[s + a];
+        for (int cl = 0; cl < nc; ++cl) {
+            const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
+            if (e - a <= (uint32_t)kSegShort) continue;
+            for (uint32_t p = a + tid; p < e; p += kFixT) {
+                const uint32_t v = perm[p];
+                uint32_t r = 0;
+                for (uint32_t q = a; q < e; ++q) r += perm[q] < v;
+                tmp[a + r] = v;
+            }
+            __syncthreads();
+            for (uint32_t p = a + tid; p < e; p += kFixT) perm[p] = tmp[p];
+            __syncthreads();
+        }
+        const uint32_t s0 = start[c0], s1 = start[c0 + nc];
+        for (uint32_t j = s0 + tid; j < s1; j += kFixT) write_sorted(perm[j], j, pos, np, lattice, N, fN, perm, sfrac);
         __syncthreads();
     }
 }
@@ -576,33 +673,31 @@ int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint3
                    uint32_t* start, float* sfrac) {
     const int N = c->N;
     const int64_t N3 = c->N3;
+    const FastDiv fN((uint32_t)N);
     uint32_t* keys = keys_out ? keys_out : c->keys;
-    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
-    if (np > 0) {
-        k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, FastDiv((uint32_t)N), keys, c->counts);
-        PMR_TRY(check_launch(c, "keys"));
-    }
-    const int64_t per = (int64_t)kT * kScanPer;
-    const int nb = (int)((N3 + per - 1) / per);
-    k_scan_local<<<nb, kT, 0, c->stream>>>(c->counts, start, N3, c->scan_part);
-    PMR_TRY(check_launch(c, "scan_local"));
-    k_scan_part<<<1, kScanPartT, 0, c->stream>>>(c->scan_part, nb, start + N3);
-    PMR_TRY(check_launch(c, "scan_part"));
-    k_scan_add<<<nblocks(N3, kT), kT, 0, c->stream>>>(start, N3, c->scan_part);
-    PMR_TRY(check_launch(c, "scan_add"));
+    uint32_t* rank = c->sort_tmp;  // slot of each particle in its cell, until the scatter
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * N3, c->stream), "memset"));
     PMR_TRY(check_cuda(c, cudaMemsetAsync(c->long_count, 0, sizeof(uint32_t), c->stream), "memset"));
     if (np > 0) {
-        k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, np, start, c->counts, perm);
-        PMR_TRY(check_launch(c, "scatter"));
+        k_keys<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, fN, keys, c->counts, rank);
+        PMR_TRY(check_launch(c, "keys"));
     }
-    k_fix_short<<<nblocks(N3, kT), kT, 0, c->stream>>>(start, perm, N3, c->long_list, c->long_count);
-    PMR_TRY(check_launch(c, "fix_short"));
-    k_fix_long<<<304, kT, 0, c->stream>>>(start, perm, c->long_list, c->long_count, c->sort_tmp);
-    PMR_TRY(check_launch(c, "fix_long"));
-    if (!sfrac || np == 0) return PMR_OK;
-    k_sorted_frac<<<nblocks(np, kT), kT, 0, c->stream>>>(pos, np, lattice, N, FastDiv((uint32_t)N), perm, sfrac);
-    return check_launch(c, "sorted_frac");
+    const int nb = (int)((N3 + kScanBlock - 1) / kScanBlock);
+    k_scan_reduce<<<nb, kScanT, 0, c->stream>>>(c->counts, N3, c->scan_part);
+    PMR_TRY(check_launch(c, "scan_reduce"));
+    k_scan_part<<<1, kScanPartT, 0, c->stream>>>(c->scan_part, nb, start + N3);
+    PMR_TRY(check_launch(c, "scan_part"));
+    k_scan_apply<<<nb, kScanT, 0, c->stream>>>(c->counts, N3, c->scan_part, start);
+    PMR_TRY(check_launch(c, "scan_apply"));
+    if (np == 0) return PMR_OK;
+    k_scatter<<<nblocks(np, kT), kT, 0, c->stream>>>(keys, rank, np, start, perm);
+    PMR_TRY(check_launch(c, "scatter"));
+    k_seg_fix<<<nblocks(N3, kFixCells), kFixT, 0, c->stream>>>(start, perm, N3, pos, np, lattice, N, fN, sfrac,
+                                                               c->long_list, c->long_count);
+    PMR_TRY(check_launch(c, "seg_fix"));
+    k_seg_fix_big<<<128, kFixT, 0, c->stream>>>(start, perm, N3, pos, np, lattice, N, fN, sfrac, c->long_list,
+                                               c->long_count, c->sort_tmp);
+    return check_launch(c, "seg_fix_big");
 }
 
 int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out) {

@@ -46,7 +46,26 @@ def test_cell_sort_crowded_cells():
     assert np.array_equal(to_np(start).view(np.uint32), want_start)
 
 
-@pytest.mark.parametrize("N,np_", [(16, 4096), (32, 20000), (16, 0)])
+def test_cell_sort_overfull_block():
+    # more particles in one block's 512 cells than its shared-memory stage holds
+    # (the global-memory path), with long and short segments in that block
+    N = 24
+    rng = np.random.default_rng(11)
+    dense = np.stack([rng.uniform(0.0, 0.9, 7000), rng.uniform(0.0, 2.0, 7000), rng.uniform(0.0, 24.0, 7000)])
+    sparse = np.stack([rng.uniform(0.0, 0.9, 600), rng.uniform(2.0, 21.0, 600), rng.uniform(0.0, 24.0, 600)])
+    rest = synth.uniform_positions(N, N**3 - 7600, seed=12, lo=0.0, hi=float(N))
+    x = np.concatenate([dense, sparse, rest], axis=1).astype(np.float32)
+    x = x[:, rng.permutation(x.shape[1])]
+    ctx, _ = context(N=N)
+    keys, perm, start = ctx.cell_sort(to_dev(x))
+    want_perm, want_start = opm.sort_by_cell(opm.cell_keys(x, N), N)
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+    rho = to_np(ctx.paint(to_dev(x)))
+    assert rel_l2(rho, opm.paint(f32(x), N, f32_wrap=True)) <= FIELD_TOL
+
+
+@pytest.mark.parametrize("N,np_", [(16, 4096), (32, 20000), (16, 0), (24, 9000), (48, 60000), (8, 100)])
 def test_paint_parity_and_mass_conservation(N, np_):
     ctx, _ = context(N=N)
     x = synth.uniform_positions(N, max(np_, 1), seed=5, lo=-N, hi=2 * N)[:, :np_]
