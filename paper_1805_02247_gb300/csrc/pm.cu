@@ -255,11 +255,10 @@ __global__ void k_permute3(const uint32_t* __restrict__ perm, const float* __res
 // arbitrary), then, with sfrac, every particle's fractional CIC offsets in the
 // sorted order: sfrac[a][j] of particle perm[j] (the float32 values cell_of
 // gives). A block owns kFixCells consecutive cells, whose particles are one
-// contiguous run of perm: the run is staged in shared memory, segments of up
-// to kSegShort particles are insertion-sorted by one thread each, longer ones
-// rank-sorted by the whole block (indices are distinct), and the run is
-// written back with coalesced stores. A run longer than kFixCap is listed in
-// ovf for k_seg_fix_big, which does the same in global memory.
+// contiguous run of perm: the run is staged in shared memory, each segment is
+// insertion-sorted by one thread, and the run is written back with coalesced
+// stores. A run longer than kFixCap, or holding a segment longer than
+// kSegShort, is listed in ovf for k_seg_fix_big (global memory).
 constexpr int kFixCells = 512, kFixT = 256, kFixCap = 5120, kSegShort = 32;
 
 __device__ __forceinline__ void write_sorted(uint32_t i, int64_t j, const float* __restrict__ pos, int64_t np,
@@ -279,15 +278,13 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
                                                    bool lattice, int N, FastDiv fN, float* __restrict__ sfrac,
                                                    uint32_t* __restrict__ ovf, uint32_t* __restrict__ novf) {
     __shared__ uint32_t buf[kFixCap];
-    __shared__ uint32_t out2[kFixCap];
     __shared__ uint32_t sst[kFixCells + 1];
-    __shared__ uint32_t longs[kFixCells];
-    __shared__ int nlong;
+    __shared__ int has_long;
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * kFixCells;
     const int nc = (int)min((int64_t)kFixCells, ncell - c0);
     for (int t = tid; t <= nc; t += kFixT) sst[t] = start[c0 + t];
-    if (tid == 0) nlong = 0;
+    if (tid == 0) has_long = 0;
     __syncthreads();
     const uint32_t s0 = sst[0];
     const int n = (int)(sst[nc] - s0);
@@ -301,7 +298,7 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
         if (e - a <= 1) continue;
         if (e - a > kSegShort) {
-            longs[atomicAdd(&nlong, 1)] = cl;
+            has_long = 1;
             continue;
         }
         for (int p = a + 1; p < e; ++p) {
@@ -315,24 +312,10 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         }
     }
     __syncthreads();
-    const int nl = nlong;
-    for (int li = 0; li < nl; ++li) {
-        const int cl = longs[li];
-        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
-        for (int p = a + tid; p < e; p += kFixT) {
-            const uint32_t v = buf[p];
-            int r = 0;
-            for (int q = a; q < e; ++q) r += buf[q] < v;
-            out2[a + r] = v;
-        }
+    if (has_long) {  // nothing written yet: the whole run goes to the global-memory pass
+        if (tid == 0) ovf[atomicAdd(novf, 1u)] = blockIdx.x;
+        return;
     }
-    __syncthreads();
-    for (int li = 0; li < nl; ++li) {
-        const int cl = longs[li];
-        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
-        for (int p = a + tid; p < e; p += kFixT) buf[p] = out2[p];
-    }
-    __syncthreads();
     for (int j = tid; j < n; j += kFixT) write_sorted(buf[j], (int64_t)s0 + j, pos, np, lattice, N, fN, perm, sfrac);
 }
 
@@ -383,144 +366,133 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
 
 // ----------------------------------------------------------------------------- paint / readout
 
-// rho_m(c) = scale * sum over rounds r, then corners o in (ox,oy,oz) lex order, of
-//            mass_m(j) * W_o(x_j) for j the r-th sorted particle of bin(c - o); + offset.
-// Visiting the r-th particle of all 8 bins per round keeps the 8 dependent
-// load chains (offsets -> perm -> position) independent; the order is fixed,
-// so the sum is deterministic.
+// CIC paint as a gather over the cell-sorted particles (Sec. 2: the CIC
+// density): rho_m(c) = scale * sum over the 8 corners o of the sums S_o of
+// mass_m(j) W_o(x_j) over the sorted particles j of bin c - o, + offset, in a
+// fixed order, so the result does not depend on scheduling.
+// A block owns X x Y x 32 cells (32 = the warp: lane l is the cell and bin
+// z0 + l); its bins are the rows (x, y) of the tile grown by one on the low x
+// and y sides. A warp takes one row at a time, each lane summing its bin's 8
+// corner terms over the bin's particles (the loads of a warp fall in one
+// contiguous run of the sorted arrays), then folds z in registers,
+// T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (lane 0 sums the bin
+// z0 - 1 for its left neighbour), so a row leaves 4 values per cell in shared
+// memory. Each cell then adds the 4 rows that hold it:
+// rho = (T_00(x, y) + T_10(x-1, y)) + (T_01(x, y-1) + T_11(x-1, y-1)).
+// MMODE 0: unit masses; 1: mass[perm[j]]; 2: masses in sorted order, mass[m][j].
 template <int NM>
-__global__ void k_paint(const float* __restrict__ pos, int64_t np, bool lattice, int N, FastDiv fN,
-                        const uint32_t* __restrict__ start, const uint32_t* __restrict__ perm,
-                        const float* __restrict__ mass, float scale, float offset, float* r0, float* r1, float* r2) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t N3 = (int64_t)N * N * N;
-    if (c >= N3) return;
-    int cq[3];
-    lattice_of((uint32_t)c, fN, cq);
-    const int cx = cq[0], cy = cq[1], cz = cq[2];
-    float acc[NM];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) acc[m] = 0.f;
-    uint32_t s[8], e[8];
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-        int bx = cx - ox, by = cy - oy, bz = cz - oz;
-        if (bx < 0) bx += N;
-        if (by < 0) by += N;
-        if (bz < 0) bz += N;
-        const int64_t b = ((int64_t)bx * N + by) * N + bz;
-        s[o] = start[b];
-        e[o] = start[b + 1];
-    }
-    for (uint32_t r = 0;; ++r) {
-        bool any = false;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            if (s[o] + r < e[o]) {
-                any = true;
-                const int64_t i = perm[s[o] + r];
-                Cell cl = cell_of(pos, np, i, lattice, N, fN);
-                const float w = wgt(cl, o);
-                if (mass == nullptr) {
-                    acc[0] += w;
-                } else {
-#pragma unroll
-                    for (int m = 0; m < NM; ++m) acc[m] += mass[m * np + i] * w;
-                }
-            }
-        }
-        if (!any) break;
-    }
-    r0[c] = acc[0] * scale + offset;
-    if (NM > 1) r1[c] = acc[1] * scale + offset;
-    if (NM > 2) r2[c] = acc[2] * scale + offset;
-}
-
-// Tiled form of the same reduction. A block owns a PTX x PTY x PTZ tile of
-// cells. Phase 1: for every bin of the tile extended by one cell on the low
-// side, the 8 corner sums S_o(b) = sum_{j in bin b, sorted} mass(j) W_o(x_j)
-// go to shared memory (each particle is read once per tile it feeds).
-// Phase 2: rho(c) = scale * sum_{o lex order} S_o(c - o) + offset.
-// tile shapes: the 3-mass (adjoint) variant keeps 3x the sums per bin, so it
-// uses a thinner tile to keep several blocks resident per SM
-template <int NM>
-struct PaintTile {
-    static constexpr int X = NM == 1 ? 4 : 2, Y = 4, Z = 32;
-    static constexpr int BX = X + 1, BY = Y + 1, BZ = Z + 1, NB = BX * BY * BZ;
-    static constexpr size_t smem = sizeof(float) * NM * 8 * NB;
+struct WTile {
+    static constexpr int X = NM == 1 ? 8 : 4, Y = NM == 1 ? 8 : 4;
+    static constexpr int RX = X + 1, RY = Y + 1, NR = RX * RY;
+    static constexpr int W = 8;  // warps per block
+    static constexpr size_t smem = sizeof(float) * 4 * NM * NR * 32;
 };
 
-// FRAC: the fractional offsets of the sorted particles come precomputed
-// (sfrac[a][j], a = axis, j = sorted index), so a bin's loop reads three
-// coalesced floats per particle instead of recomputing its cell from the
-// position; otherwise each particle's offsets are derived from pos here.
-template <int NM, bool FRAC, bool SMASS = false>
-__global__ void __launch_bounds__(256) k_paint_tile(const float* __restrict__ pos, int64_t np, bool lattice, int N,
-                                                    FastDiv fN, const uint32_t* __restrict__ start,
-                                                    const uint32_t* __restrict__ perm,
-                                                    const float* __restrict__ sfrac, const float* __restrict__ mass,
-                                                    float scale, float offset, float* r0, float* r1, float* r2) {
-    constexpr int PTX = PaintTile<NM>::X, PTY = PaintTile<NM>::Y, PTZ = PaintTile<NM>::Z;
-    constexpr int PBY = PaintTile<NM>::BY, PBZ = PaintTile<NM>::BZ, PNB = PaintTile<NM>::NB;
-    extern __shared__ float S[];  // [NM][8][PNB]
-    const int x0 = blockIdx.z * PTX, y0 = blockIdx.y * PTY, z0 = blockIdx.x * PTZ;
-    for (int t = threadIdx.x; t < PNB; t += blockDim.x) {
-        const int bx = t / (PBY * PBZ), by = (t / PBZ) % PBY, bz = t % PBZ;
-        int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
+template <int NM, int MMODE>
+__global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 5 : 4) k_paint_wtile(const uint32_t* __restrict__ start,
+                                                                     const uint32_t* __restrict__ perm,
+                                                                     const float* __restrict__ sfrac,
+                                                                     const float* __restrict__ mass, int64_t np, int N,
+                                                                     float scale, float offset, float* r0, float* r1,
+                                                                     float* r2) {
+    using WT = WTile<NM>;
+    extern __shared__ float Ts[];  // [4 (ox,oy)][NM][NR rows][32]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int z0 = blockIdx.x * 32, y0 = blockIdx.y * WT::Y, x0 = blockIdx.z * WT::X;
+    const int z = z0 + lane;
+    const bool zin = z < N;
+    const int zh = z0 == 0 ? N - 1 : z0 - 1;  // the bin left of lane 0
+    const float* __restrict__ sf1 = sfrac + np;
+    const float* __restrict__ sf2 = sfrac + 2 * np;
+
+    auto row_base = [&](int r) -> int64_t {
+        const int bx = r / WT::RY, by = r - bx * WT::RY;
+        int gx = x0 - 1 + bx, gy = y0 - 1 + by;
         gx = gx < 0 ? gx + N : (gx >= N ? gx - N : gx);
         gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
-        gz = gz < 0 ? gz + N : (gz >= N ? gz - N : gz);
-        const int64_t b = ((int64_t)gx * N + gy) * N + gz;
-        float acc[NM][8];
+        return ((int64_t)gx * N + gy) * N;
+    };
+    // one particle's corner terms (oz = 1 only when ONLY1)
+    auto acc = [&](uint32_t j, float (&S)[2][2][2][NM], bool only1) {
+        const float dx = sfrac[j], dy = sf1[j], dz = sf2[j];
+        float mv[NM];
 #pragma unroll
-        for (int m = 0; m < NM; ++m)
+        for (int m = 0; m < NM; ++m) mv[m] = 1.f;
+        if (MMODE == 1) mv[0] = mass[perm[j]];
+        if (MMODE == 2)
 #pragma unroll
-            for (int o = 0; o < 8; ++o) acc[m][o] = 0.f;
-        const uint32_t s = start[b], e = start[b + 1];
-        for (uint32_t j = s; j < e; ++j) {
-            Cell cl;
-            int64_t i = 0;
-            if (FRAC) {
-                cl.d[0] = sfrac[j];
-                cl.d[1] = sfrac[np + j];
-                cl.d[2] = sfrac[2 * np + j];
-                if (mass) i = SMASS ? (int64_t)j : (int64_t)perm[j];  // SMASS: masses already in sorted order
-            } else {
-                i = perm[j];
-                cl = cell_of(pos, np, i, lattice, N, fN);
-            }
-            float mv[NM];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) mv[m] = mass ? mass[m * np + i] : 1.f;
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const float w = wgt(cl, o);
-#pragma unroll
-                for (int m = 0; m < NM; ++m) acc[m][o] = fmaf(mv[m], w, acc[m][o]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < NM; ++m)
-#pragma unroll
-            for (int o = 0; o < 8; ++o) S[(m * 8 + o) * PNB + t] = acc[m][o];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < PTX * PTY * PTZ; t += blockDim.x) {
-        const int lx = t / (PTY * PTZ), ly = (t / PTZ) % PTY, lz = t % PTZ;
-        const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-        if (gx >= N || gy >= N || gz >= N) continue;
-        const int64_t c = ((int64_t)gx * N + gy) * N + gz;
+            for (int m = 0; m < NM; ++m) mv[m] = mass[m * np + j];
+        const float ux = 1.f - dx, uy = 1.f - dy, uz = 1.f - dz;
+        const float a[2][2] = {{ux * uy, ux * dy}, {dx * uy, dx * dy}};
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            float acc = 0.f;
+            const float wz0 = MMODE ? uz * mv[m] : uz, wz1 = MMODE ? dz * mv[m] : dz;
 #pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-                acc += S[(m * 8 + o) * PNB + ((lx + 1 - ox) * PBY + (ly + 1 - oy)) * PBZ + (lz + 1 - oz)];
+            for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+                for (int oy = 0; oy < 2; ++oy) {
+                    if (!only1) S[ox][oy][0][m] = fmaf(a[ox][oy], wz0, S[ox][oy][0][m]);
+                    S[ox][oy][1][m] = fmaf(a[ox][oy], wz1, S[ox][oy][1][m]);
+                }
+        }
+    };
+
+    // rows w, w + W, ...; the next row's bin bounds are loaded before this row's particles
+    uint32_t s_n = 0, e_n = 0, hs_n = 0, he_n = 0;
+    if (w < WT::NR) {
+        const int64_t rb = row_base(w);
+        if (zin) {
+            s_n = start[rb + z];
+            e_n = start[rb + z + 1];
+        }
+        if (lane == 0) {
+            hs_n = start[rb + zh];
+            he_n = start[rb + zh + 1];
+        }
+    }
+    for (int r = w; r < WT::NR; r += WT::W) {
+        const uint32_t s = s_n, e = e_n, hs = hs_n, he = he_n;
+        if (r + WT::W < WT::NR) {
+            const int64_t rb = row_base(r + WT::W);
+            if (zin) {
+                s_n = start[rb + z];
+                e_n = start[rb + z + 1];
             }
-            float* r = m == 0 ? r0 : (m == 1 ? r1 : r2);
-            r[c] = acc * scale + offset;
+            if (lane == 0) {
+                hs_n = start[rb + zh];
+                he_n = start[rb + zh + 1];
+            }
+        }
+        float S[2][2][2][NM] = {};
+        for (uint32_t j = s; j < e; ++j) acc(j, S, false);
+        float H[2][2][2][NM] = {};
+        for (uint32_t j = hs; j < he; ++j) acc(j, H, true);  // lane 0 only
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    float left = __shfl_up_sync(0xffffffffu, S[ox][oy][1][m], 1);
+                    if (lane == 0) left = H[ox][oy][1][m];
+                    Ts[(((ox * 2 + oy) * NM + m) * WT::NR + r) * 32 + lane] = S[ox][oy][0][m] + left;
+                }
+    }
+    __syncthreads();
+    for (int q = w; q < WT::X * WT::Y; q += WT::W) {
+        const int lx = q / WT::Y, ly = q - lx * WT::Y;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= N || gy >= N || !zin) continue;
+        const int r11 = (lx + 1) * WT::RY + (ly + 1);  // bin (x, y)
+        const int64_t c = ((int64_t)gx * N + gy) * N + z;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const float t00 = Ts[((0 * NM + m) * WT::NR + r11) * 32 + lane];
+            const float t10 = Ts[((2 * NM + m) * WT::NR + r11 - WT::RY) * 32 + lane];
+            const float t01 = Ts[((1 * NM + m) * WT::NR + r11 - 1) * 32 + lane];
+            const float t11 = Ts[((3 * NM + m) * WT::NR + r11 - WT::RY - 1) * 32 + lane];
+            float* out = m == 0 ? r0 : (m == 1 ? r1 : r2);
+            out[c] = ((t00 + t10) + (t01 + t11)) * scale + offset;
         }
     }
 }
@@ -704,30 +676,25 @@ int cell_sort(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* 
     return cell_sort_into(c, pos, np, lattice, keys_out, c->perm, c->cell_start, c->sfrac);
 }
 
+template <int NM, int MMODE>
+int launch_paint_wtile(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
+                       int64_t np, float scale, float offset, float* const* rho) {
+    using WT = WTile<NM>;
+    const int N = c->N;
+    const dim3 grid((N + 31) / 32, (N + WT::Y - 1) / WT::Y, (N + WT::X - 1) / WT::X);
+    k_paint_wtile<NM, MMODE><<<grid, WT::W * 32, WT::smem, c->stream>>>(
+        start, perm, sfrac, mass, np, N, scale, offset, rho[0], NM > 1 ? rho[1] : nullptr, NM > 2 ? rho[2] : nullptr);
+    return check_launch(c, NM == 1 ? "paint" : "paint3");
+}
+
+// Every paint reads the fractional offsets its sort wrote (sfrac).
 int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uint32_t* perm, const uint32_t* start,
                const float* sfrac, const float* mass, int nmass, float scale, float offset, float* const* rho) {
-    const int N = c->N;
-    const FastDiv fN((uint32_t)N);
-    if (nmass <= 1) {
-        using T = PaintTile<1>;
-        const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-        if (sfrac)
-            k_paint_tile<1, true><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, sfrac, mass,
-                                                                    scale, offset, rho[0], nullptr, nullptr);
-        else
-            k_paint_tile<1, false><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, nullptr,
-                                                                     mass, scale, offset, rho[0], nullptr, nullptr);
-    } else {
-        using T = PaintTile<3>;
-        const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-        if (sfrac)
-            k_paint_tile<3, true><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, sfrac, mass,
-                                                                    scale, offset, rho[0], rho[1], rho[2]);
-        else
-            k_paint_tile<3, false><<<grid, 256, T::smem, c->stream>>>(pos, np, lattice, N, fN, start, perm, nullptr,
-                                                                     mass, scale, offset, rho[0], rho[1], rho[2]);
-    }
-    return check_launch(c, nmass <= 1 ? "paint" : "paint3");
+    (void)pos;
+    (void)lattice;
+    if (!sfrac || nmass != 1) return fail(c, PMR_EINVAL, "paint: one mass and the sort's offsets are required");
+    return mass ? launch_paint_wtile<1, 1>(c, perm, start, sfrac, mass, np, scale, offset, rho)
+                : launch_paint_wtile<1, 0>(c, perm, start, sfrac, nullptr, np, scale, offset, rho);
 }
 
 // Three-mass paint of the lattice particles with their masses first moved into
@@ -736,29 +703,16 @@ int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uin
 // force by then; the next step recomputes it).
 int paint3_sorted(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
                   float scale, float* const* rho) {
-    const int N = c->N;
     const int64_t np = c->N3;
     float* smass = c->F;
     k_permute3<<<nblocks(np, kT), kT, 0, c->stream>>>(perm, mass, np, smass);
     PMR_TRY(check_launch(c, "permute3"));
-    using T = PaintTile<3>;
-    const dim3 grid((N + T::Z - 1) / T::Z, (N + T::Y - 1) / T::Y, (N + T::X - 1) / T::X);
-    k_paint_tile<3, true, true><<<grid, 256, T::smem, c->stream>>>(nullptr, np, true, N, FastDiv((uint32_t)N), start,
-                                                                  perm, sfrac, smass, scale, 0.0f, rho[0], rho[1],
-                                                                  rho[2]);
-    return check_launch(c, "paint3");
+    return launch_paint_wtile<3, 2>(c, perm, start, sfrac, smass, np, scale, 0.0f, rho);
 }
 
 int pm_init(pmr_ctx* c) {
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)PaintTile<3>::smem),
-                       "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, true, true>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PaintTile<3>::smem),
-                       "smem attr"));
-    return check_cuda(c, cudaFuncSetAttribute(k_paint_tile<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)PaintTile<3>::smem),
-                      "smem attr");
+    (void)c;
+    return PMR_OK;
 }
 
 int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,
