@@ -302,6 +302,9 @@ struct XFused {
     int acc;  // add the result to out instead of storing it
     Mul mul[3];
     const float* ptab;  // sqrt power table for MUL_POWER
+    // all multipliers are MUL_ODD with j = their index and one scale and
+    // weighting: the shared factor scale/k^2 is applied once per element
+    int odd3;
 };
 
 __device__ __forceinline__ float2 apply_mul(const Mul& m, float2 v, int nx, int ny, int kz, int N,
@@ -329,6 +332,21 @@ __device__ __forceinline__ float2 apply_mul(const Mul& m, float2 v, int nx, int 
     const float kj = twopi_n * nj;
     const float a = f * kj / k2;
     return make_float2(-a * v.y, a * v.x);
+}
+
+// the parts of MUL_ODD: f / k^2 (0 at k = 0), and k_j (0 on the Nyquist plane of j)
+__device__ __forceinline__ float odd_g(const Mul& m, int nx, int ny, int kz, int N) {
+    const int n2 = nx * nx + ny * ny + kz * kz;
+    if (n2 == 0) return 0.f;
+    const float twopi_n = 6.28318530717958647692f / (float)N;
+    float f = m.scale;
+    if (m.weighted) f *= (kz == 0 || 2 * kz == N) ? 1.0f : 2.0f;
+    const float kx = twopi_n * nx, ky = twopi_n * ny, kzf = twopi_n * kz;
+    return f / (kx * kx + ky * ky + kzf * kzf);
+}
+__device__ __forceinline__ float odd_k(int j, int nx, int ny, int kz, int N) {
+    const int nj = (j == 0) ? nx : (j == 1) ? ny : kz;
+    return 2 * abs(nj) == N ? 0.f : (6.28318530717958647692f / (float)N) * nj;
 }
 
 // x-pass with multipliers. Tile: outer index = ky row, columns = kz block,
@@ -650,26 +668,67 @@ __global__ void __launch_bounds__(RG::T, 65536 / (RG::T * 128)) k_x_reg(XFused p
     } else if constexpr (MODE == 1) {
         to_k(p.in[0], X);
         {
+            // p.odd3: the kept tile is X f/k^2, and output o is i k_o times it
 #pragma unroll
             for (int a = 0; a < RG::A2; ++a)
 #pragma unroll
-                for (int k2 = 0; k2 < RG::N2; ++k2) Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x] = X[a][k2];
+                for (int k2 = 0; k2 < RG::N2; ++k2) {
+                    float2 v = X[a][k2];
+                    if (p.odd3) {
+                        const int mx = g + RG::G * a + RG::N1 * k2;
+                        v = cscale(v, ok ? odd_g(p.mul[0], (2 * mx <= N) ? mx : mx - N, ny, kz, N) : 0.f);
+                    }
+                    Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x] = v;
+                }
 #pragma unroll 1
             for (int o = 0; o < p.nout; ++o) {
 #pragma unroll
                 for (int a = 0; a < RG::A2; ++a)
 #pragma unroll
                     for (int k2 = 0; k2 < RG::N2; ++k2) X[a][k2] = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
-                mul_into(p.mul[o], X, X, false);
+                if (p.odd3) {
+#pragma unroll
+                    for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                        for (int k2 = 0; k2 < RG::N2; ++k2) {
+                            const int mx = g + RG::G * a + RG::N1 * k2;
+                            const float kj = odd_k(o, (2 * mx <= N) ? mx : mx - N, ny, kz, N);
+                            X[a][k2] = make_float2(-kj * X[a][k2].y, kj * X[a][k2].x);
+                        }
+                } else {
+                    mul_into(p.mul[o], X, X, false);
+                }
                 emit(X, p.out[o]);
             }
         }
     } else {
+        // p.odd3: sum_i k_i X_i, then times i f/k^2 once
         float2 acc[RG::A2][RG::N2];
 #pragma unroll 1
         for (int i = 0; i < p.nin; ++i) {
             to_k(p.in[i], X);
-            mul_into(p.mul[i], X, acc, i > 0);
+            if (p.odd3) {
+#pragma unroll
+                for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                    for (int k2 = 0; k2 < RG::N2; ++k2) {
+                        const int mx = g + RG::G * a + RG::N1 * k2;
+                        const float2 v = cscale(X[a][k2], odd_k(i, (2 * mx <= N) ? mx : mx - N, ny, kz, N));
+                        acc[a][k2] = i > 0 ? cadd(acc[a][k2], v) : v;
+                    }
+            } else {
+                mul_into(p.mul[i], X, acc, i > 0);
+            }
+        }
+        if (p.odd3) {
+#pragma unroll
+            for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                for (int k2 = 0; k2 < RG::N2; ++k2) {
+                    const int mx = g + RG::G * a + RG::N1 * k2;
+                    const float gk = ok ? odd_g(p.mul[0], (2 * mx <= N) ? mx : mx - N, ny, kz, N) : 0.f;
+                    acc[a][k2] = make_float2(-gk * acc[a][k2].y, gk * acc[a][k2].x);
+                }
         }
         emit(acc, p.out[0]);
     }
@@ -948,7 +1007,13 @@ int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
     return check_launch(c, "col_pass");
 }
 
-int launch_x_fused(pmr_ctx* c, const XFused& p) {
+int launch_x_fused(pmr_ctx* c, const XFused& p_in) {
+    XFused p = p_in;
+    const int width3 = p.nin > 1 ? p.nin : p.nout;
+    p.odd3 = width3 == 3;
+    for (int o = 0; o < 3 && p.odd3; ++o)
+        p.odd3 = p.mul[o].type == MUL_ODD && p.mul[o].j == o && p.mul[o].scale == p.mul[0].scale &&
+                 p.mul[o].weighted == p.mul[0].weighted;
     bool done = with_reg(c->N, [&](auto rg) {
         using RG = decltype(rg);
         dim3 grid(nblocks(c->P, kRC), c->N);
