@@ -617,6 +617,540 @@ __global__ void __launch_bounds__(NT, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// Forward only, software-pipelined over the CTA's tiles: separate layer-1 and
+// layer-2 operand buffers let the next tile's halo and A1 be built while this
+// tile's layer-2 MMAs run, and this tile's layer-2 epilogue and head run while
+// the next tile's layer-1 MMAs run. Per tile t (t' = the CTA's next tile):
+//   wait MMA1(t); D1 -> A2; issue MMA2(t); halo(t') -> A1; issue MMA1(t');
+//   wait MMA2(t); D2 -> y, M.
+// The tensor pipe runs MMA2(t) before MMA1(t'), so the two completion
+// barriers are waited in issue order. Arithmetic per voxel is that of k_mlp_tc.
+template <bool BF>
+struct LayF {
+    using L = Lay<BF>;
+    static constexpr uint32_t SZ_A1 = L::bytes(TM, L::K1), SZ_A2 = L::bytes(TM, K2);
+    static constexpr uint32_t S_A1 = L::IMG_FWD;
+    static constexpr uint32_t S_A2 = S_A1 + L::NP * SZ_A1;
+    static constexpr uint32_t S_TAIL = S_A2 + L::NP * SZ_A2;
+    // halo, partial sums [4][TM], stencil offsets [K1], 3 barriers + TMEM slot
+    static constexpr uint32_t SMEM = S_TAIL + 4 * HALO + 4 * 4 * TM + 4 * L::K1 + 64;
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0, "aligned regions");
+    static_assert((4 * HALO + 4 * 4 * TM + 4 * L::K1) % 8 == 0, "aligned barriers");
+};
+
+template <bool TWO_NET, bool BF>
+__global__ void __launch_bounds__(NT, 1)
+    k_mlp_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
+              float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err) {
+    using L = Lay<BF>;
+    using F = LayF<BF>;
+    constexpr int K1 = L::K1;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A1h = sm + F::S_A1;
+    unsigned char* A1l = A1h + (L::NP - 1) * F::SZ_A1;  // == A1h with one part
+    unsigned char* A2h = sm + F::S_A2;
+    unsigned char* A2l = A2h + (L::NP - 1) * F::SZ_A2;
+    float* halo = reinterpret_cast<float*>(sm + F::S_TAIL);
+    float* part = halo + HALO;  // [4][TM]
+    int* koff = reinterpret_cast<int*>(part + 4 * TM);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(koff + K1);  // MMA1 done, MMA2 done, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
+    const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cb = warp >> 2;
+    const int row = quad * 32 + lane;
+    constexpr uint32_t ncols = 128;
+    const int N = tm.N;
+    const int64_t N3 = tm.N3;
+
+    {
+        const uint32_t n16 = L::IMG_FWD / 16;
+        float4* dst = reinterpret_cast<float4*>(sm);
+        for (uint32_t i = tid; i < n16; i += NT) dst[i] = img[i];
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid < K1) {
+        const int k = tid;
+        const int c = k / 27, o = k % 27, ox = o / 9, oy = (o / 3) % 3, oz = o % 3;
+        koff[k] = k < NI ? ((c * HX + ox) * HY + oy) * HZ + oz : -1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
+    uint32_t ph1 = 0, ph2 = 0;
+    bool ok = true;
+    // halo offsets of this thread's A1 entries (row tid / 4, k-steps tid % 4 + 4 i); -1: padding
+    constexpr int KS_PER = (K1 / 8 + 3) / 4;
+    int hoff[KS_PER][8];
+    {
+        const int r = tid >> 2, p = tid & 3;
+        const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
+#pragma unroll
+        for (int i = 0; i < KS_PER; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ks = p + 4 * i, ko = ks < K1 / 8 ? koff[ks * 8 + j] : -1;
+                hoff[i][j] = ko >= 0 ? ko + base : -1;
+            }
+    }
+
+    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
+        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
+        const int tz = tile - (int)(t2 * tm.ntz.d);
+        const int tx = (int)tm.nty.div(t2);
+        const int ty = (int)t2 - tx * (int)tm.nty.d;
+        x0 = tx * TX;
+        y0 = ty * TY;
+        z0 = tz * TZ;
+    };
+    float hv[HALO_PER];
+    // this thread's halo entries t = tid + q NT as (field, hx, hy, hz), packed 8 bits each (-1: none)
+    int hq[HALO_PER];
+#pragma unroll
+    for (int q = 0; q < HALO_PER; ++q) {
+        const int t = tid + q * NT;
+        const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
+        hq[q] = t < HALO ? (c << 24) | ((r / (HY * HZ)) << 16) | (((r / HZ) % HY) << 8) | (r % HZ) : -1;
+    }
+    auto load_halo = [&](int tile) {
+        if (tile >= ntiles) return;
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+#pragma unroll
+        for (int q = 0; q < HALO_PER; ++q) {
+            if (hq[q] >= 0) {
+                const int c = hq[q] >> 24, hx = (hq[q] >> 16) & 255, hy = (hq[q] >> 8) & 255, hz = hq[q] & 255;
+                const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
+                hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
+            }
+        }
+    };
+    // halo registers -> shared memory -> A1 (4 threads per row); the voxel's own
+    // three values (two-network head) of rows tid < TM into f
+    auto build_A1 = [&](float (&f)[3]) {
+#pragma unroll
+        for (int q = 0; q < HALO_PER; ++q) {
+            const int t = tid + q * NT;
+            if (t < HALO) halo[t] = hv[q];
+        }
+        __syncthreads();
+        {
+            const int r = tid >> 2, p = tid & 3;
+#pragma unroll
+            for (int i = 0; i < KS_PER; ++i) {
+                const int ks = p + 4 * i;
+                if (ks < K1 / 8) {
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = hoff[i][j] >= 0 ? halo[hoff[i][j]] : 0.f;
+                    put8<BF>(A1h, A1l, r, ks * 8, v);
+                }
+            }
+        }
+        if (TWO_NET && tid < TM) {
+            const int lx = tid >> 6, ly = (tid >> 4) & 3, lz = tid & 15;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer<BF>(tmem + COL_D1, sA1h, sA1l, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1), K1,
+                            N1, nsplit);
+            mma_commit(bars + 0);
+        }
+    };
+
+    int tile = blockIdx.x;
+    float fc[3] = {0.f, 0.f, 0.f};  // the current tile's centre values (two-network head)
+    load_halo(tile);
+    if (tile < ntiles) {
+        build_A1(fc);
+        load_halo(tile + gridDim.x);
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int nxt = tile + gridDim.x;
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+        const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
+        const bool row_in = row_gx < N && row_gy < N && row_gz < N;
+        const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
+
+        // (1) layer 1 of this tile
+        ok = __syncthreads_and(mbar_wait(bars + 0, ph1));
+        ph1 ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+        // (2) relu(D1 + b1) -> A2 and the layer-1 mask; layer 2
+        {
+            float av[16];
+            tmem_ld16(lane_base + COL_D1 + 16 * cb, av);
+            uint32_t mask1 = 0;
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float pre = av[j] + b1[16 * cb + j];
+                mask1 |= (pre > 0.f ? 1u : 0u) << j;
+                z[j] = fmaxf(pre, 0.f);
+            }
+            if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
+            put8<BF>(A2h, A2l, row, 16 * cb, z);
+            put8<BF>(A2h, A2l, row, 16 * cb + 8, z + 8);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2), K2,
+                            N2, nsplit);
+            mma_commit(bars + 1);
+        }
+        // (3) the next tile's layer 1 while layer 2 runs (A1 and D1 are free)
+        float fn[3] = {0.f, 0.f, 0.f};
+        if (nxt < ntiles) {
+            build_A1(fn);
+            load_halo(nxt + gridDim.x);
+        }
+        // (4) layer 2 of this tile
+        ok = __syncthreads_and(mbar_wait(bars + 1, ph2));
+        ph2 ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+        // (5) y = b3 + w3 . relu(D2 + b2) and the head
+        {
+            float av[8];
+            tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
+            uint32_t mask2 = 0;
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float pre = av[j] + b2[8 * cb + j];
+                mask2 |= (pre > 0.f ? 1u : 0u) << j;
+                s = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), s);
+            }
+            part[cb * TM + row] = s;
+            if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (tid < TM) {
+            const int r = tid;
+            const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
+            const bool in = gx < N && gy < N && gz < N;
+            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
+            const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
+            if (sv.y && in) sv.y[vox] = y;
+            if (TWO_NET) {
+                const float pl = sigmoidf(a * y);
+                float u0, u1, u2;
+                if (in) M_out[vox] = M_scale * pl * mass_net<false>(vec + VEC_MASS, fc[0], fc[1], fc[2], 0.f, u0, u1, u2);
+            } else {
+                if (in) M_out[vox] = M_scale * softplusf(y);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fc[c] = fn[c];
+        __syncthreads();  // part is rewritten by the next tile
+    }
+
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mma_commit(bars + 2);  // completes once every MMA this thread issued has
+        }
+        mbar_wait(bars + 2, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Backward (input gradient) from the forward's saved activations, pipelined
+// like k_mlp_fwd: separate A3 / A4 operand buffers and g_v staging, so the
+// next tile's A3 is built and its MMA3 issued while this tile's MMA4 runs, and
+// this tile's box sums run while the next tile's MMA3 runs. Per tile t:
+//   wait MMA3(t); D3 [a1 > 0] -> A4; issue MMA4(t); g_y(t') -> A3; issue MMA3(t');
+//   wait MMA4(t); D4 -> g_v -> box sums.
+// Only the layer-2 and layer-1 weight images (B3 = W2, B4 = W1) and the vector
+// block are staged. Arithmetic per voxel is that of k_mlp_tc<true, ...>.
+template <bool BF>
+struct LayB {
+    using L = Lay<BF>;
+    static constexpr uint32_t IMG_OFF = L::S_VEC;         // staged: vector block, B3, B4 (contiguous in the image)
+    static constexpr uint32_t IMG_BYTES = L::IMG_ALL - L::S_VEC;
+    static constexpr uint32_t S_VEC = 0, S_B3 = L::S_B3 - L::S_VEC, S_B4 = L::S_B4 - L::S_VEC;
+    static constexpr uint32_t SZ_A3 = L::bytes(TM, K3), SZ_A4 = L::bytes(TM, K4);
+    static constexpr uint32_t S_A3 = (IMG_BYTES + 127) / 128 * 128;
+    static constexpr uint32_t S_A4 = S_A3 + L::NP * SZ_A3;
+    static constexpr uint32_t S_GV = S_A4 + L::NP * SZ_A4;
+    static constexpr uint32_t S_TAIL = S_GV + 4 * NI * TM;
+    // g_y [TM], centre-value gradients [2][3][TM], 3 barriers + TMEM slot
+    static constexpr uint32_t SMEM = S_TAIL + 4 * TM + 4 * 6 * TM + 64;
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(S_B3 % 128 == 0 && S_B4 % 128 == 0 && S_A3 % 128 == 0 && S_A4 % 128 == 0 && S_GV % 16 == 0,
+                  "aligned regions");
+    static_assert(IMG_OFF % 16 == 0 && IMG_BYTES % 16 == 0, "16-byte image copy");
+};
+
+template <bool TWO_NET, bool BF>
+__global__ void __launch_bounds__(NT, 1)
+    k_mlp_bwd(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
+              TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ gbox, Saved sv,
+              int* __restrict__ err) {
+    using L = Lay<BF>;
+    using B = LayB<BF>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* A3h = sm + B::S_A3;
+    unsigned char* A3l = A3h + (L::NP - 1) * B::SZ_A3;
+    unsigned char* A4h = sm + B::S_A4;
+    unsigned char* A4l = A4h + (L::NP - 1) * B::SZ_A4;
+    float* gvs = reinterpret_cast<float*>(sm + B::S_GV);  // [81][TM]
+    float* gys = reinterpret_cast<float*>(sm + B::S_TAIL);
+    float* gcen = gys + TM;  // [2 slots][3][TM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gcen + 6 * TM);  // MMA3 done, MMA4 done, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    const float* vec = reinterpret_cast<const float*>(sm + B::S_VEC);
+    const float* w3 = vec + 96;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3, cb = warp >> 2;
+    const int row = quad * 32 + lane;
+    constexpr uint32_t ncols = 256;
+    const int N = tm.N;
+    const int64_t N3 = tm.N3;
+
+    {
+        const uint32_t n16 = B::IMG_BYTES / 16;
+        const float4* src = img + B::IMG_OFF / 16;
+        float4* dst = reinterpret_cast<float4*>(sm);
+        for (uint32_t i = tid; i < n16; i += NT) dst[i] = src[i];
+    }
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + b)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+    const uint32_t sA3h = smem_u32(A3h), sA3l = smem_u32(A3l), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
+    uint32_t ph3 = 0, ph4 = 0;
+    bool ok = true;
+
+    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
+        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
+        const int tz = tile - (int)(t2 * tm.ntz.d);
+        const int tx = (int)tm.nty.div(t2);
+        const int ty = (int)t2 - tx * (int)tm.nty.d;
+        x0 = tx * TX;
+        y0 = ty * TY;
+        z0 = tz * TZ;
+    };
+    // saved forward state of a tile, loaded one tile ahead: g_M, y and the
+    // centre values of rows tid < TM; the masks of this thread's row and column block
+    float L_gm = 0.f, L_y = 0.f, L_f[3] = {0.f, 0.f, 0.f};
+    uint32_t L_m1 = 0, L_m2 = 0;
+    auto load_saved = [&](int tile) {
+        if (tile >= ntiles) return;
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+        if (tid < TM) {
+            const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
+            const bool in = gx < N && gy < N && gz < N;
+            const int64_t v = ((int64_t)gx * N + gy) * N + gz;
+            L_gm = in ? gM[v] : 0.f;
+            L_y = in ? sv.y[v] : 0.f;
+            if (TWO_NET)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) L_f[c] = in ? feat[c * N3 + v] : 0.f;
+        }
+        const int gx = x0 + (row >> 6), gy = y0 + ((row >> 4) & 3), gz = z0 + (row & 15);
+        const bool in = gx < N && gy < N && gz < N;
+        const int64_t v = ((int64_t)gx * N + gy) * N + gz;
+        L_m1 = in ? sv.m1[cb * N3 + v] : 0u;
+        L_m2 = in ? sv.m2[cb * N3 + v] : 0u;
+    };
+    // g_y of the loaded tile, A3 = g_a2 = w3 g_y [a2 > 0], MMA3; gcen slot `slot`
+    auto build_A3 = [&](int tile, int slot) {
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+        if (tid < TM) {
+            const int r = tid;
+            const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
+            const bool in = gx < N && gy < N && gz < N;
+            const float g = in ? L_gm * M_scale : 0.f;
+            if (TWO_NET) {
+                // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
+                const float p = sigmoidf(a * L_y);
+                float g0, g1, g2;
+                const float m = mass_net<true>(vec + VEC_MASS, L_f[0], L_f[1], L_f[2], g * p, g0, g1, g2);
+                gys[r] = g * m * a * p * (1.f - p);
+                gcen[(slot * 3 + 0) * TM + r] = g0;
+                gcen[(slot * 3 + 1) * TM + r] = g1;
+                gcen[(slot * 3 + 2) * TM + r] = g2;
+            } else {
+                gys[r] = g * sigmoidf(L_y);
+            }
+        }
+        __syncthreads();
+        {
+            const float g = gys[row];
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = ((L_m2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
+            put8<BF>(A3h, A3l, row, 8 * cb, v);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3), K3,
+                            NB3, nsplit);
+            mma_commit(bars + 0);
+        }
+    };
+
+    int tile = blockIdx.x;
+    uint32_t m1_cur = 0;
+    load_saved(tile);
+    if (tile < ntiles) {
+        build_A3(tile, 0);
+        m1_cur = L_m1;
+        load_saved(tile + gridDim.x);
+    }
+    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        const int nxt = tile + gridDim.x;
+        const int slot = it & 1;
+        int x0, y0, z0;
+        tile_origin(tile, x0, y0, z0);
+
+        // (1) layer-2 input gradient of this tile
+        ok = __syncthreads_and(mbar_wait(bars + 0, ph3));
+        ph3 ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+        // (2) A4 = g_a1 [a1 > 0]; layer 1
+        {
+            float av[16];
+            tmem_ld16(lane_base + COL_D3 + 16 * cb, av);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) av[j] = ((m1_cur >> j) & 1u) ? av[j] : 0.f;
+            put8<BF>(A4h, A4l, row, 16 * cb, av);
+            put8<BF>(A4h, A4l, row, 16 * cb + 8, av + 8);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_layer<BF>(tmem + COL_D4, sA4h, sA4l, smem_u32(sm + B::S_B4), smem_u32(sm + B::S_B4 + L::SZ_B4), K4,
+                            NB4, nsplit);
+            mma_commit(bars + 1);
+        }
+        // (3) the next tile's A3 and MMA3 while MMA4 runs (A3, D3, g_y are free)
+        uint32_t m1_nxt = 0;
+        if (nxt < ntiles) {
+            build_A3(nxt, slot ^ 1);
+            m1_nxt = L_m1;
+            load_saved(nxt + gridDim.x);
+        }
+        // (4) layer-1 input gradient of this tile
+        ok = __syncthreads_and(mbar_wait(bars + 1, ph4));
+        ph4 ^= 1;
+        if (!ok) break;
+        tc_fence_after();
+        // (5) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
+        {
+            const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
+            const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                float av[8];
+                tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, av);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int k = 24 * cb + 8 * h + j;
+                    float v = av[j];
+                    if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(slot * 3 + k / 27) * TM + row];
+                    if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        // (6) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
+        //     tile voxel at box cell - 1 - o, offsets o in a fixed order
+        for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
+            const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
+            const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
+            float acc = 0.f;
+#pragma unroll
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int lx = hx - 1 - ox;
+                if (lx < 0 || lx >= TX) continue;
+#pragma unroll
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int ly = hy - 1 - oy;
+                    if (ly < 0 || ly >= TY) continue;
+#pragma unroll
+                    for (int oz = -1; oz <= 1; ++oz) {
+                        const int lz = hz - 1 - oz;
+                        if (lz < 0 || lz >= TZ) continue;
+                        const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                        acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
+                    }
+                }
+            }
+            gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
+        }
+        m1_cur = m1_nxt;
+        __syncthreads();  // gvs is rewritten by the next tile
+    }
+
+    if (!ok) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mma_commit(bars + 2);  // completes once every MMA this thread issued has
+        }
+        mbar_wait(bars + 2, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 // host: split into TF32 head and tail (round to nearest, ties away, at bit 13)
 float tf32_round(float x) {
     uint32_t u;
@@ -741,6 +1275,14 @@ std::vector<unsigned char> build_image(const float* W) {
 template <bool BF>
 int set_smem_attrs(pmr_ctx* c) {
     using L = Lay<BF>;
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)LayF<BF>::SMEM), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)LayF<BF>::SMEM), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)LayB<BF>::SMEM), "smem attr"));
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)LayB<BF>::SMEM), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)L::SMEM_FWD), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -762,6 +1304,22 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     const uint32_t smem = BWD ? L::SMEM_BWD : L::SMEM_FWD;
     float* gv = BWD ? c->gbox : nullptr;
     const Saved sv{c->nn_y, c->nn_m1, c->nn_m2};  // written by the forward, read by the backward
+    if (!BWD) {
+        const uint32_t sf = LayF<BF>::SMEM;
+        if (c->cfg.head == 1)
+            k_mlp_fwd<true, BF><<<grid, NT, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+        else
+            k_mlp_fwd<false, BF><<<grid, NT, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+        return check_launch(c, "mlp_tc_fwd");
+    }
+    {
+        const uint32_t sb = LayB<BF>::SMEM;
+        if (c->cfg.head == 1)
+            k_mlp_bwd<true, BF><<<grid, NT, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
+        else
+            k_mlp_bwd<false, BF><<<grid, NT, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
+        return check_launch(c, "mlp_tc_bwd");
+    }
     if (c->cfg.head == 1)
         k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv, sv,
                                                                c->tc_err);
