@@ -617,14 +617,38 @@ __global__ void __launch_bounds__(NT, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// Forward only, software-pipelined over the CTA's tiles: separate layer-1 and
-// layer-2 operand buffers let the next tile's halo and A1 be built while this
-// tile's layer-2 MMAs run, and this tile's layer-2 epilogue and head run while
-// the next tile's layer-1 MMAs run. Per tile t (t' = the CTA's next tile):
-//   wait MMA1(t); D1 -> A2; issue MMA2(t); halo(t') -> A1; issue MMA1(t');
-//   wait MMA2(t); D2 -> y, M.
-// The tensor pipe runs MMA2(t) before MMA1(t'), so the two completion
-// barriers are waited in issue order. Arithmetic per voxel is that of k_mlp_tc.
+// Compute warps synchronise among themselves on named barrier 1 (the
+// MMA-issuing warp never joins it); nbar_and also ANDs a predicate over them.
+__device__ __forceinline__ void nbar_sync(uint32_t n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+__device__ __forceinline__ bool nbar_and(uint32_t n, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(n)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int NTW = NT + 32;  // 16 compute warps + the warp whose lane 0 issues the MMAs
+
+// Forward only, warp-specialised and software-pipelined over the CTA's tiles.
+// Warps 0-15 build operands and read accumulators; lane 0 of warp 16 issues
+// the MMAs. Operand buffers are per layer, so the compute warps build the next
+// tile's A1 while this tile's layer 2 runs, and read this tile's layer 2 while
+// the next tile's layer 1 runs. Handshakes (mbarriers):
+//   A1 full / A2 full: 512 compute-thread arrivals, each after its operand
+//     stores (async-proxy fence) and after its own reads of the accumulator
+//     the next MMA overwrites;
+//   D1 full / D2 full: tcgen05.commit after MMA1 / MMA2.
+// Per tile t (t' = the CTA's next tile), compute warps:
+//   wait D1(t); D1 -> A2, arrive A2; halo(t') -> A1, arrive A1; wait D2(t); D2 -> y, M
+// and the issuing lane: wait A1(t), MMA1(t) -> D1; wait A2(t), MMA2(t) -> D2.
+// Arithmetic per voxel is that of k_mlp_tc.
 template <bool BF>
 struct LayF {
     using L = Lay<BF>;
@@ -632,7 +656,7 @@ struct LayF {
     static constexpr uint32_t S_A1 = L::IMG_FWD;
     static constexpr uint32_t S_A2 = S_A1 + L::NP * SZ_A1;
     static constexpr uint32_t S_TAIL = S_A2 + L::NP * SZ_A2;
-    // halo, partial sums [4][TM], stencil offsets [K1], 3 barriers + TMEM slot
+    // halo, partial sums [4][TM], stencil offsets [K1], 5 barriers + TMEM slot
     static constexpr uint32_t SMEM = S_TAIL + 4 * HALO + 4 * 4 * TM + 4 * L::K1 + 64;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0, "aligned regions");
@@ -640,7 +664,7 @@ struct LayF {
 };
 
 template <bool TWO_NET, bool BF>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NTW, 1)
     k_mlp_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
               float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err) {
     using L = Lay<BF>;
@@ -654,8 +678,8 @@ __global__ void __launch_bounds__(NT, 1)
     float* halo = reinterpret_cast<float*>(sm + F::S_TAIL);
     float* part = halo + HALO;  // [4][TM]
     int* koff = reinterpret_cast<int*>(part + 4 * TM);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(koff + K1);  // MMA1 done, MMA2 done, drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(koff + K1);  // A1 full, A2 full, D1 full, D2 full, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
     const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
     const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
 
@@ -669,11 +693,13 @@ __global__ void __launch_bounds__(NT, 1)
     {
         const uint32_t n16 = L::IMG_FWD / 16;
         float4* dst = reinterpret_cast<float4*>(sm);
-        for (uint32_t i = tid; i < n16; i += NT) dst[i] = img[i];
+        for (uint32_t i = tid; i < n16; i += NTW) dst[i] = img[i];
     }
     if (tid == 0) {
+        const uint32_t cnt[5] = {(uint32_t)NT, (uint32_t)NT, 1u, 1u, 1u};
 #pragma unroll
-        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + b)) : "memory");
+        for (int b = 0; b < 5; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt[b]) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -691,193 +717,206 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
-    uint32_t ph1 = 0, ph2 = 0;
-    bool ok = true;
-    // halo offsets of this thread's A1 entries (row tid / 4, k-steps tid % 4 + 4 i); -1: padding
-    constexpr int KS_PER = (K1 / 8 + 3) / 4;
-    int hoff[KS_PER][8];
-    {
-        const int r = tid >> 2, p = tid & 3;
-        const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
-#pragma unroll
-        for (int i = 0; i < KS_PER; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int ks = p + 4 * i, ko = ks < K1 / 8 ? koff[ks * 8 + j] : -1;
-                hoff[i][j] = ko >= 0 ? ko + base : -1;
-            }
-    }
 
-    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
-        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
-        const int tz = tile - (int)(t2 * tm.ntz.d);
-        const int tx = (int)tm.nty.div(t2);
-        const int ty = (int)t2 - tx * (int)tm.nty.d;
-        x0 = tx * TX;
-        y0 = ty * TY;
-        z0 = tz * TZ;
-    };
-    float hv[HALO_PER];
-    // this thread's halo entries t = tid + q NT as (field, hx, hy, hz), packed 8 bits each (-1: none)
-    int hq[HALO_PER];
-#pragma unroll
-    for (int q = 0; q < HALO_PER; ++q) {
-        const int t = tid + q * NT;
-        const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
-        hq[q] = t < HALO ? (c << 24) | ((r / (HY * HZ)) << 16) | (((r / HZ) % HY) << 8) | (r % HZ) : -1;
-    }
-    auto load_halo = [&](int tile) {
-        if (tile >= ntiles) return;
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-#pragma unroll
-        for (int q = 0; q < HALO_PER; ++q) {
-            if (hq[q] >= 0) {
-                const int c = hq[q] >> 24, hx = (hq[q] >> 16) & 255, hy = (hq[q] >> 8) & 255, hz = hq[q] & 255;
-                const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
-                hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
+    if (warp == NT / 32) {
+        // ---- MMA issue (one lane)
+        if (lane == 0) {
+            const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
+            uint32_t pa1 = 0, pa2 = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                if (!mbar_wait(bars + 0, pa1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                pa1 ^= 1;
+                tc_fence_after();
+                issue_layer<BF>(tmem + COL_D1, sA1h, sA1l, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1),
+                                K1, N1, nsplit);
+                mma_commit(bars + 2);
+                if (!mbar_wait(bars + 1, pa2)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                pa2 ^= 1;
+                tc_fence_after();
+                issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2),
+                                K2, N2, nsplit);
+                mma_commit(bars + 3);
             }
+            mma_commit(bars + 4);  // completes once every MMA issued above has
+            mbar_wait(bars + 4, 0);
         }
-    };
-    // halo registers -> shared memory -> A1 (4 threads per row); the voxel's own
-    // three values (two-network head) of rows tid < TM into f
-    auto build_A1 = [&](float (&f)[3]) {
+        __syncwarp();
+    } else {
+        // ---- compute warps
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        uint32_t ph1 = 0, ph2 = 0;
+        bool ok = true;
+        // halo offsets of this thread's A1 entries (row tid / 4, k-steps tid % 4 + 4 i); -1: padding
+        constexpr int KS_PER = (K1 / 8 + 3) / 4;
+        int hoff[KS_PER][8];
+        {
+            const int r = tid >> 2, p = tid & 3;
+            const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
+#pragma unroll
+            for (int i = 0; i < KS_PER; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int ks = p + 4 * i, ko = ks < K1 / 8 ? koff[ks * 8 + j] : -1;
+                    hoff[i][j] = ko >= 0 ? ko + base : -1;
+                }
+        }
+        auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
+            const uint32_t t2 = tm.ntz.div((uint32_t)tile);
+            const int tz = tile - (int)(t2 * tm.ntz.d);
+            const int tx = (int)tm.nty.div(t2);
+            const int ty = (int)t2 - tx * (int)tm.nty.d;
+            x0 = tx * TX;
+            y0 = ty * TY;
+            z0 = tz * TZ;
+        };
+        float hv[HALO_PER];
+        // this thread's halo entries t = tid + q NT as (field, hx, hy, hz), 8 bits each (-1: none)
+        int hq[HALO_PER];
 #pragma unroll
         for (int q = 0; q < HALO_PER; ++q) {
             const int t = tid + q * NT;
-            if (t < HALO) halo[t] = hv[q];
+            const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
+            hq[q] = t < HALO ? (c << 24) | ((r / (HY * HZ)) << 16) | (((r / HZ) % HY) << 8) | (r % HZ) : -1;
         }
-        __syncthreads();
-        {
-            const int r = tid >> 2, p = tid & 3;
+        auto load_halo = [&](int tile) {
+            if (tile >= ntiles) return;
+            int x0, y0, z0;
+            tile_origin(tile, x0, y0, z0);
 #pragma unroll
-            for (int i = 0; i < KS_PER; ++i) {
-                const int ks = p + 4 * i;
-                if (ks < K1 / 8) {
-                    float v[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) v[j] = hoff[i][j] >= 0 ? halo[hoff[i][j]] : 0.f;
-                    put8<BF>(A1h, A1l, r, ks * 8, v);
+            for (int q = 0; q < HALO_PER; ++q) {
+                if (hq[q] >= 0) {
+                    const int c = hq[q] >> 24, hx = (hq[q] >> 16) & 255, hy = (hq[q] >> 8) & 255, hz = hq[q] & 255;
+                    const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
+                    hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
                 }
             }
-        }
-        if (TWO_NET && tid < TM) {
-            const int lx = tid >> 6, ly = (tid >> 4) & 3, lz = tid & 15;
+        };
+        // halo registers -> shared memory -> A1 (4 threads per row), then arrive on "A1 full";
+        // the voxel's own three values (two-network head) of rows tid < TM into f
+        auto build_A1 = [&](float (&f)[3]) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
+            for (int q = 0; q < HALO_PER; ++q) {
+                const int t = tid + q * NT;
+                if (t < HALO) halo[t] = hv[q];
+            }
+            nbar_sync(NT);
+            {
+                const int r = tid >> 2, p = tid & 3;
+#pragma unroll
+                for (int i = 0; i < KS_PER; ++i) {
+                    const int ks = p + 4 * i;
+                    if (ks < K1 / 8) {
+                        float v[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) v[j] = hoff[i][j] >= 0 ? halo[hoff[i][j]] : 0.f;
+                        put8<BF>(A1h, A1l, r, ks * 8, v);
+                    }
+                }
+            }
+            if (TWO_NET && tid < TM) {
+                const int lx = tid >> 6, ly = (tid >> 4) & 3, lz = tid & 15;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
+            }
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + 0);
+        };
+
+        int tile = blockIdx.x;
+        float fc[3] = {0.f, 0.f, 0.f};  // the current tile's centre values (two-network head)
+        load_halo(tile);
+        if (tile < ntiles) {
+            build_A1(fc);
+            load_halo(tile + gridDim.x);
         }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+        for (; tile < ntiles; tile += gridDim.x) {
+            const int nxt = tile + gridDim.x;
+            int x0, y0, z0;
+            tile_origin(tile, x0, y0, z0);
+            const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
+            const bool row_in = row_gx < N && row_gy < N && row_gz < N;
+            const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
+
+            // (1) layer 1 of this tile
+            ok = nbar_and(NT, mbar_wait(bars + 2, ph1));
+            ph1 ^= 1;
+            if (!ok) break;
             tc_fence_after();
-            issue_layer<BF>(tmem + COL_D1, sA1h, sA1l, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1), K1,
-                            N1, nsplit);
-            mma_commit(bars + 0);
-        }
-    };
-
-    int tile = blockIdx.x;
-    float fc[3] = {0.f, 0.f, 0.f};  // the current tile's centre values (two-network head)
-    load_halo(tile);
-    if (tile < ntiles) {
-        build_A1(fc);
-        load_halo(tile + gridDim.x);
-    }
-    for (; tile < ntiles; tile += gridDim.x) {
-        const int nxt = tile + gridDim.x;
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-        const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
-        const bool row_in = row_gx < N && row_gy < N && row_gz < N;
-        const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
-
-        // (1) layer 1 of this tile
-        ok = __syncthreads_and(mbar_wait(bars + 0, ph1));
-        ph1 ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-        // (2) relu(D1 + b1) -> A2 and the layer-1 mask; layer 2
-        {
-            float av[16];
-            tmem_ld16(lane_base + COL_D1 + 16 * cb, av);
-            uint32_t mask1 = 0;
-            float z[16];
+            // (2) relu(D1 + b1) -> A2 and the layer-1 mask
+            {
+                float av[16];
+                tmem_ld16(lane_base + COL_D1 + 16 * cb, av);
+                uint32_t mask1 = 0;
+                float z[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float pre = av[j] + b1[16 * cb + j];
-                mask1 |= (pre > 0.f ? 1u : 0u) << j;
-                z[j] = fmaxf(pre, 0.f);
+                for (int j = 0; j < 16; ++j) {
+                    const float pre = av[j] + b1[16 * cb + j];
+                    mask1 |= (pre > 0.f ? 1u : 0u) << j;
+                    z[j] = fmaxf(pre, 0.f);
+                }
+                if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
+                put8<BF>(A2h, A2l, row, 16 * cb, z);
+                put8<BF>(A2h, A2l, row, 16 * cb + 8, z + 8);
             }
-            if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
-            put8<BF>(A2h, A2l, row, 16 * cb, z);
-            put8<BF>(A2h, A2l, row, 16 * cb + 8, z + 8);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + 1);
+            // (3) the next tile's A1 while layer 2 runs
+            float fn[3] = {0.f, 0.f, 0.f};
+            if (nxt < ntiles) {
+                build_A1(fn);
+                load_halo(nxt + gridDim.x);
+            }
+            // (4) layer 2 of this tile
+            ok = nbar_and(NT, mbar_wait(bars + 3, ph2));
+            ph2 ^= 1;
+            if (!ok) break;
             tc_fence_after();
-            issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2), K2,
-                            N2, nsplit);
-            mma_commit(bars + 1);
-        }
-        // (3) the next tile's layer 1 while layer 2 runs (A1 and D1 are free)
-        float fn[3] = {0.f, 0.f, 0.f};
-        if (nxt < ntiles) {
-            build_A1(fn);
-            load_halo(nxt + gridDim.x);
-        }
-        // (4) layer 2 of this tile
-        ok = __syncthreads_and(mbar_wait(bars + 1, ph2));
-        ph2 ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-        // (5) y = b3 + w3 . relu(D2 + b2) and the head
-        {
-            float av[8];
-            tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
-            uint32_t mask2 = 0;
-            float s = 0.f;
+            // (5) y = b3 + w3 . relu(D2 + b2) and the head
+            {
+                float av[8];
+                tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
+                uint32_t mask2 = 0;
+                float sacc = 0.f;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float pre = av[j] + b2[8 * cb + j];
-                mask2 |= (pre > 0.f ? 1u : 0u) << j;
-                s = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), s);
+                for (int j = 0; j < 8; ++j) {
+                    const float pre = av[j] + b2[8 * cb + j];
+                    mask2 |= (pre > 0.f ? 1u : 0u) << j;
+                    sacc = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), sacc);
+                }
+                part[cb * TM + row] = sacc;
+                if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
             }
-            part[cb * TM + row] = s;
-            if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (tid < TM) {
-            const int r = tid;
-            const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
-            const bool in = gx < N && gy < N && gz < N;
-            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
-            const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
-            if (sv.y && in) sv.y[vox] = y;
-            if (TWO_NET) {
-                const float pl = sigmoidf(a * y);
-                float u0, u1, u2;
-                if (in) M_out[vox] = M_scale * pl * mass_net<false>(vec + VEC_MASS, fc[0], fc[1], fc[2], 0.f, u0, u1, u2);
-            } else {
-                if (in) M_out[vox] = M_scale * softplusf(y);
+            tc_fence_before();
+            nbar_sync(NT);
+            if (tid < TM) {
+                const int r = tid;
+                const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
+                const bool in = gx < N && gy < N && gz < N;
+                const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
+                const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
+                if (sv.y && in) sv.y[vox] = y;
+                if (TWO_NET) {
+                    const float pl = sigmoidf(a * y);
+                    float u0, u1, u2;
+                    if (in)
+                        M_out[vox] = M_scale * pl * mass_net<false>(vec + VEC_MASS, fc[0], fc[1], fc[2], 0.f, u0, u1, u2);
+                } else {
+                    if (in) M_out[vox] = M_scale * softplusf(y);
+                }
             }
-        }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) fc[c] = fn[c];
-        __syncthreads();  // part is rewritten by the next tile
-    }
-
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mma_commit(bars + 2);  // completes once every MMA this thread issued has
+            for (int c = 0; c < 3; ++c) fc[c] = fn[c];
+            nbar_sync(NT);  // part is rewritten by the next tile
         }
-        mbar_wait(bars + 2, 0);
+        if (!ok && tid == 0) atomicExch(err, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -1307,9 +1346,9 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     if (!BWD) {
         const uint32_t sf = LayF<BF>::SMEM;
         if (c->cfg.head == 1)
-            k_mlp_fwd<true, BF><<<grid, NT, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
         else
-            k_mlp_fwd<false, BF><<<grid, NT, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
         return check_launch(c, "mlp_tc_fwd");
     }
     {
