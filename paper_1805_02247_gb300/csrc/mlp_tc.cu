@@ -925,12 +925,12 @@ __global__ void __launch_bounds__(NTW, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-// Backward (input gradient) from the forward's saved activations, pipelined
-// like k_mlp_fwd: separate A3 / A4 operand buffers and g_v staging, so the
-// next tile's A3 is built and its MMA3 issued while this tile's MMA4 runs, and
-// this tile's box sums run while the next tile's MMA3 runs. Per tile t:
-//   wait MMA3(t); D3 [a1 > 0] -> A4; issue MMA4(t); g_y(t') -> A3; issue MMA3(t');
-//   wait MMA4(t); D4 -> g_v -> box sums.
+// Backward (input gradient) from the forward's saved activations, warp-
+// specialised and pipelined like k_mlp_fwd, with separate A3 / A4 operand
+// buffers and g_v staging. Per tile t (t' = the CTA's next tile), compute warps:
+//   wait D3(t); D3 [a1 > 0] -> A4, arrive A4; g_y(t') -> A3, arrive A3;
+//   wait D4(t); D4 -> g_v -> box sums
+// and the issuing lane: wait A3(t), MMA3(t) -> D3; wait A4(t), MMA4(t) -> D4.
 // Only the layer-2 and layer-1 weight images (B3 = W2, B4 = W1) and the vector
 // block are staged. Arithmetic per voxel is that of k_mlp_tc<true, ...>.
 template <bool BF>
@@ -944,7 +944,7 @@ struct LayB {
     static constexpr uint32_t S_A4 = S_A3 + L::NP * SZ_A3;
     static constexpr uint32_t S_GV = S_A4 + L::NP * SZ_A4;
     static constexpr uint32_t S_TAIL = S_GV + 4 * NI * TM;
-    // g_y [TM], centre-value gradients [2][3][TM], 3 barriers + TMEM slot
+    // g_y [TM], centre-value gradients [2][3][TM], 5 barriers + TMEM slot
     static constexpr uint32_t SMEM = S_TAIL + 4 * TM + 4 * 6 * TM + 64;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(S_B3 % 128 == 0 && S_B4 % 128 == 0 && S_A3 % 128 == 0 && S_A4 % 128 == 0 && S_GV % 16 == 0,
@@ -953,7 +953,7 @@ struct LayB {
 };
 
 template <bool TWO_NET, bool BF>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NTW, 1)
     k_mlp_bwd(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
               TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ gbox, Saved sv,
               int* __restrict__ err) {
@@ -967,8 +967,8 @@ __global__ void __launch_bounds__(NT, 1)
     float* gvs = reinterpret_cast<float*>(sm + B::S_GV);  // [81][TM]
     float* gys = reinterpret_cast<float*>(sm + B::S_TAIL);
     float* gcen = gys + TM;  // [2 slots][3][TM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gcen + 6 * TM);  // MMA3 done, MMA4 done, drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gcen + 6 * TM);  // A3 full, A4 full, D3 full, D4 full, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
     const float* vec = reinterpret_cast<const float*>(sm + B::S_VEC);
     const float* w3 = vec + 96;
 
@@ -983,11 +983,13 @@ __global__ void __launch_bounds__(NT, 1)
         const uint32_t n16 = B::IMG_BYTES / 16;
         const float4* src = img + B::IMG_OFF / 16;
         float4* dst = reinterpret_cast<float4*>(sm);
-        for (uint32_t i = tid; i < n16; i += NT) dst[i] = src[i];
+        for (uint32_t i = tid; i < n16; i += NTW) dst[i] = src[i];
     }
     if (tid == 0) {
+        const uint32_t cnt[5] = {(uint32_t)NT, (uint32_t)NT, 1u, 1u, 1u};
 #pragma unroll
-        for (int b = 0; b < 3; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + b)) : "memory");
+        for (int b = 0; b < 5; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt[b]) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1000,188 +1002,200 @@ __global__ void __launch_bounds__(NT, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    const uint32_t sA3h = smem_u32(A3h), sA3l = smem_u32(A3l), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
-    uint32_t ph3 = 0, ph4 = 0;
-    bool ok = true;
 
-    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
-        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
-        const int tz = tile - (int)(t2 * tm.ntz.d);
-        const int tx = (int)tm.nty.div(t2);
-        const int ty = (int)t2 - tx * (int)tm.nty.d;
-        x0 = tx * TX;
-        y0 = ty * TY;
-        z0 = tz * TZ;
-    };
-    // saved forward state of a tile, loaded one tile ahead: g_M, y and the
-    // centre values of rows tid < TM; the masks of this thread's row and column block
-    float L_gm = 0.f, L_y = 0.f, L_f[3] = {0.f, 0.f, 0.f};
-    uint32_t L_m1 = 0, L_m2 = 0;
-    auto load_saved = [&](int tile) {
-        if (tile >= ntiles) return;
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-        if (tid < TM) {
-            const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
+    if (warp == NT / 32) {
+        // ---- MMA issue (one lane)
+        if (lane == 0) {
+            const uint32_t sA3h = smem_u32(A3h), sA3l = smem_u32(A3l), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
+            uint32_t pa3 = 0, pa4 = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+                if (!mbar_wait(bars + 0, pa3)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                pa3 ^= 1;
+                tc_fence_after();
+                issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3),
+                                K3, NB3, nsplit);
+                mma_commit(bars + 2);
+                if (!mbar_wait(bars + 1, pa4)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                pa4 ^= 1;
+                tc_fence_after();
+                issue_layer<BF>(tmem + COL_D4, sA4h, sA4l, smem_u32(sm + B::S_B4), smem_u32(sm + B::S_B4 + L::SZ_B4),
+                                K4, NB4, nsplit);
+                mma_commit(bars + 3);
+            }
+            mma_commit(bars + 4);  // completes once every MMA issued above has
+            mbar_wait(bars + 4, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---- compute warps
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        uint32_t ph3 = 0, ph4 = 0;
+        bool ok = true;
+        auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
+            const uint32_t t2 = tm.ntz.div((uint32_t)tile);
+            const int tz = tile - (int)(t2 * tm.ntz.d);
+            const int tx = (int)tm.nty.div(t2);
+            const int ty = (int)t2 - tx * (int)tm.nty.d;
+            x0 = tx * TX;
+            y0 = ty * TY;
+            z0 = tz * TZ;
+        };
+        // saved forward state of a tile, loaded one tile ahead: g_M, y and the
+        // centre values of rows tid < TM; the masks of this thread's row and column block
+        float L_gm = 0.f, L_y = 0.f, L_f[3] = {0.f, 0.f, 0.f};
+        uint32_t L_m1 = 0, L_m2 = 0;
+        auto load_saved = [&](int tile) {
+            if (tile >= ntiles) return;
+            int x0, y0, z0;
+            tile_origin(tile, x0, y0, z0);
+            if (tid < TM) {
+                const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
+                const bool in = gx < N && gy < N && gz < N;
+                const int64_t v = ((int64_t)gx * N + gy) * N + gz;
+                L_gm = in ? gM[v] : 0.f;
+                L_y = in ? sv.y[v] : 0.f;
+                if (TWO_NET)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) L_f[c] = in ? feat[c * N3 + v] : 0.f;
+            }
+            const int gx = x0 + (row >> 6), gy = y0 + ((row >> 4) & 3), gz = z0 + (row & 15);
             const bool in = gx < N && gy < N && gz < N;
             const int64_t v = ((int64_t)gx * N + gy) * N + gz;
-            L_gm = in ? gM[v] : 0.f;
-            L_y = in ? sv.y[v] : 0.f;
-            if (TWO_NET)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) L_f[c] = in ? feat[c * N3 + v] : 0.f;
-        }
-        const int gx = x0 + (row >> 6), gy = y0 + ((row >> 4) & 3), gz = z0 + (row & 15);
-        const bool in = gx < N && gy < N && gz < N;
-        const int64_t v = ((int64_t)gx * N + gy) * N + gz;
-        L_m1 = in ? sv.m1[cb * N3 + v] : 0u;
-        L_m2 = in ? sv.m2[cb * N3 + v] : 0u;
-    };
-    // g_y of the loaded tile, A3 = g_a2 = w3 g_y [a2 > 0], MMA3; gcen slot `slot`
-    auto build_A3 = [&](int tile, int slot) {
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-        if (tid < TM) {
-            const int r = tid;
-            const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
-            const bool in = gx < N && gy < N && gz < N;
-            const float g = in ? L_gm * M_scale : 0.f;
-            if (TWO_NET) {
-                // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
-                const float p = sigmoidf(a * L_y);
-                float g0, g1, g2;
-                const float m = mass_net<true>(vec + VEC_MASS, L_f[0], L_f[1], L_f[2], g * p, g0, g1, g2);
-                gys[r] = g * m * a * p * (1.f - p);
-                gcen[(slot * 3 + 0) * TM + r] = g0;
-                gcen[(slot * 3 + 1) * TM + r] = g1;
-                gcen[(slot * 3 + 2) * TM + r] = g2;
-            } else {
-                gys[r] = g * sigmoidf(L_y);
-            }
-        }
-        __syncthreads();
-        {
-            const float g = gys[row];
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = ((L_m2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
-            put8<BF>(A3h, A3l, row, 8 * cb, v);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3), K3,
-                            NB3, nsplit);
-            mma_commit(bars + 0);
-        }
-    };
-
-    int tile = blockIdx.x;
-    uint32_t m1_cur = 0;
-    load_saved(tile);
-    if (tile < ntiles) {
-        build_A3(tile, 0);
-        m1_cur = L_m1;
-        load_saved(tile + gridDim.x);
-    }
-    for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-        const int nxt = tile + gridDim.x;
-        const int slot = it & 1;
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-
-        // (1) layer-2 input gradient of this tile
-        ok = __syncthreads_and(mbar_wait(bars + 0, ph3));
-        ph3 ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-        // (2) A4 = g_a1 [a1 > 0]; layer 1
-        {
-            float av[16];
-            tmem_ld16(lane_base + COL_D3 + 16 * cb, av);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) av[j] = ((m1_cur >> j) & 1u) ? av[j] : 0.f;
-            put8<BF>(A4h, A4l, row, 16 * cb, av);
-            put8<BF>(A4h, A4l, row, 16 * cb + 8, av + 8);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D4, sA4h, sA4l, smem_u32(sm + B::S_B4), smem_u32(sm + B::S_B4 + L::SZ_B4), K4,
-                            NB4, nsplit);
-            mma_commit(bars + 1);
-        }
-        // (3) the next tile's A3 and MMA3 while MMA4 runs (A3, D3, g_y are free)
-        uint32_t m1_nxt = 0;
-        if (nxt < ntiles) {
-            build_A3(nxt, slot ^ 1);
-            m1_nxt = L_m1;
-            load_saved(nxt + gridDim.x);
-        }
-        // (4) layer-1 input gradient of this tile
-        ok = __syncthreads_and(mbar_wait(bars + 1, ph4));
-        ph4 ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-        // (5) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
-        {
-            const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
-            const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                float av[8];
-                tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, av);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int k = 24 * cb + 8 * h + j;
-                    float v = av[j];
-                    if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(slot * 3 + k / 27) * TM + row];
-                    if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
+            L_m1 = in ? sv.m1[cb * N3 + v] : 0u;
+            L_m2 = in ? sv.m2[cb * N3 + v] : 0u;
+        };
+        // g_y of the loaded tile, A3 = g_a2 = w3 g_y [a2 > 0], arrive on "A3 full"; gcen slot `slot`
+        auto build_A3 = [&](int tile, int slot) {
+            int x0, y0, z0;
+            tile_origin(tile, x0, y0, z0);
+            if (tid < TM) {
+                const int r = tid;
+                const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
+                const bool in = gx < N && gy < N && gz < N;
+                const float g = in ? L_gm * M_scale : 0.f;
+                if (TWO_NET) {
+                    // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
+                    const float p = sigmoidf(a * L_y);
+                    float g0, g1, g2;
+                    const float m = mass_net<true>(vec + VEC_MASS, L_f[0], L_f[1], L_f[2], g * p, g0, g1, g2);
+                    gys[r] = g * m * a * p * (1.f - p);
+                    gcen[(slot * 3 + 0) * TM + r] = g0;
+                    gcen[(slot * 3 + 1) * TM + r] = g1;
+                    gcen[(slot * 3 + 2) * TM + r] = g2;
+                } else {
+                    gys[r] = g * sigmoidf(L_y);
                 }
             }
+            nbar_sync(NT);
+            {
+                const float g = gys[row];
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = ((L_m2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
+                put8<BF>(A3h, A3l, row, 8 * cb, v);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + 0);
+        };
+
+        int tile = blockIdx.x;
+        uint32_t m1_cur = 0;
+        load_saved(tile);
+        if (tile < ntiles) {
+            build_A3(tile, 0);
+            m1_cur = L_m1;
+            load_saved(tile + gridDim.x);
         }
-        tc_fence_before();
-        __syncthreads();
-        // (6) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
-        //     tile voxel at box cell - 1 - o, offsets o in a fixed order
-        for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
-            const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
-            const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
-            float acc = 0.f;
+        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+            const int nxt = tile + gridDim.x;
+            const int slot = it & 1;
+            int x0, y0, z0;
+            tile_origin(tile, x0, y0, z0);
+
+            // (1) layer-2 input gradient of this tile
+            ok = nbar_and(NT, mbar_wait(bars + 2, ph3));
+            ph3 ^= 1;
+            if (!ok) break;
+            tc_fence_after();
+            // (2) A4 = g_a1 [a1 > 0]
+            {
+                float av[16];
+                tmem_ld16(lane_base + COL_D3 + 16 * cb, av);
 #pragma unroll
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int lx = hx - 1 - ox;
-                if (lx < 0 || lx >= TX) continue;
+                for (int j = 0; j < 16; ++j) av[j] = ((m1_cur >> j) & 1u) ? av[j] : 0.f;
+                put8<BF>(A4h, A4l, row, 16 * cb, av);
+                put8<BF>(A4h, A4l, row, 16 * cb + 8, av + 8);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + 1);
+            // (3) the next tile's A3 while MMA4 runs
+            uint32_t m1_nxt = 0;
+            if (nxt < ntiles) {
+                build_A3(nxt, slot ^ 1);
+                m1_nxt = L_m1;
+                load_saved(nxt + gridDim.x);
+            }
+            // (4) layer-1 input gradient of this tile
+            ok = nbar_and(NT, mbar_wait(bars + 3, ph4));
+            ph4 ^= 1;
+            if (!ok) break;
+            tc_fence_after();
+            // (5) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
+            {
+                const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
+                const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
 #pragma unroll
-                for (int oy = -1; oy <= 1; ++oy) {
-                    const int ly = hy - 1 - oy;
-                    if (ly < 0 || ly >= TY) continue;
+                for (int h = 0; h < 3; ++h) {
+                    float av[8];
+                    tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, av);
 #pragma unroll
-                    for (int oz = -1; oz <= 1; ++oz) {
-                        const int lz = hz - 1 - oz;
-                        if (lz < 0 || lz >= TZ) continue;
-                        const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
-                        acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
+                    for (int j = 0; j < 8; ++j) {
+                        const int k = 24 * cb + 8 * h + j;
+                        float v = av[j];
+                        if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(slot * 3 + k / 27) * TM + row];
+                        if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
                     }
                 }
             }
-            gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
+            tc_fence_before();
+            nbar_sync(NT);
+            // (6) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
+            //     tile voxel at box cell - 1 - o, offsets o in a fixed order
+            for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
+                const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
+                const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
+                float acc = 0.f;
+#pragma unroll
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int lx = hx - 1 - ox;
+                    if (lx < 0 || lx >= TX) continue;
+#pragma unroll
+                    for (int oy = -1; oy <= 1; ++oy) {
+                        const int ly = hy - 1 - oy;
+                        if (ly < 0 || ly >= TY) continue;
+#pragma unroll
+                        for (int oz = -1; oz <= 1; ++oz) {
+                            const int lz = hz - 1 - oz;
+                            if (lz < 0 || lz >= TZ) continue;
+                            const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                            acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
+                        }
+                    }
+                }
+                gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
+            }
+            m1_cur = m1_nxt;
+            nbar_sync(NT);  // gvs is rewritten by the next tile
         }
-        m1_cur = m1_nxt;
-        __syncthreads();  // gvs is rewritten by the next tile
-    }
-
-    if (!ok) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mma_commit(bars + 2);  // completes once every MMA this thread issued has
-        }
-        mbar_wait(bars + 2, 0);
+        if (!ok && tid == 0) atomicExch(err, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -1354,9 +1368,9 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     {
         const uint32_t sb = LayB<BF>::SMEM;
         if (c->cfg.head == 1)
-            k_mlp_bwd<true, BF><<<grid, NT, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
+            k_mlp_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
         else
-            k_mlp_bwd<false, BF><<<grid, NT, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
+            k_mlp_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
         return check_launch(c, "mlp_tc_bwd");
     }
     if (c->cfg.head == 1)

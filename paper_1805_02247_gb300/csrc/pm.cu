@@ -375,9 +375,9 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
 // and y sides. A warp takes one row at a time, each lane summing its bin's 8
 // corner terms over the bin's particles (the loads of a warp fall in one
 // contiguous run of the sorted arrays), then folds z in registers,
-// T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (lane 0 sums the bin
-// z0 - 1 for its left neighbour), so a row leaves 4 values per cell in shared
-// memory. Each cell then adds the 4 rows that hold it:
+// T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (the bins z0 - 1 of all
+// rows, lane 0's left neighbours, are summed first, one row per thread), so a
+// row leaves 4 values per cell in shared memory. Each cell then adds the 4 rows that hold it:
 // rho = (T_00(x, y) + T_10(x-1, y)) + (T_01(x, y-1) + T_11(x-1, y-1)).
 // MMODE 0: unit masses; 1: mass[perm[j]]; 2: masses in sorted order, mass[m][j].
 template <int NM>
@@ -385,7 +385,8 @@ struct WTile {
     static constexpr int X = NM == 1 ? 8 : 4, Y = NM == 1 ? 8 : 4;
     static constexpr int RX = X + 1, RY = Y + 1, NR = RX * RY;
     static constexpr int W = 8;  // warps per block
-    static constexpr size_t smem = sizeof(float) * 4 * NM * NR * 32;
+    // T values [4][NM][NR][32], then the halo bins' S_(ox,oy,1) [4][NM][NR]
+    static constexpr size_t smem = sizeof(float) * 4 * NM * NR * 33;
 };
 
 template <int NM, int MMODE>
@@ -437,36 +438,35 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 5 : 4) k_paint_wt
         }
     };
 
+    // the halo bin z0 - 1 of every row (lane 0's left neighbour), one row per thread
+    float* Hs = Ts + 4 * NM * WT::NR * 32;  // [4 (ox,oy)][NM][NR]
+    for (int r = threadIdx.x; r < WT::NR; r += WT::W * 32) {
+        const int64_t rb = row_base(r);
+        float H[2][2][2][NM] = {};
+        const uint32_t hs = start[rb + zh], he = start[rb + zh + 1];
+        for (uint32_t j = hs; j < he; ++j) acc(j, H, true);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Hs[(q * NM + m) * WT::NR + r] = H[q >> 1][q & 1][1][m];
+    }
     // rows w, w + W, ...; the next row's bin bounds are loaded before this row's particles
-    uint32_t s_n = 0, e_n = 0, hs_n = 0, he_n = 0;
-    if (w < WT::NR) {
+    uint32_t s_n = 0, e_n = 0;
+    if (w < WT::NR && zin) {
         const int64_t rb = row_base(w);
-        if (zin) {
+        s_n = start[rb + z];
+        e_n = start[rb + z + 1];
+    }
+    __syncthreads();
+    for (int r = w; r < WT::NR; r += WT::W) {
+        const uint32_t s = s_n, e = e_n;
+        if (r + WT::W < WT::NR && zin) {
+            const int64_t rb = row_base(r + WT::W);
             s_n = start[rb + z];
             e_n = start[rb + z + 1];
         }
-        if (lane == 0) {
-            hs_n = start[rb + zh];
-            he_n = start[rb + zh + 1];
-        }
-    }
-    for (int r = w; r < WT::NR; r += WT::W) {
-        const uint32_t s = s_n, e = e_n, hs = hs_n, he = he_n;
-        if (r + WT::W < WT::NR) {
-            const int64_t rb = row_base(r + WT::W);
-            if (zin) {
-                s_n = start[rb + z];
-                e_n = start[rb + z + 1];
-            }
-            if (lane == 0) {
-                hs_n = start[rb + zh];
-                he_n = start[rb + zh + 1];
-            }
-        }
         float S[2][2][2][NM] = {};
         for (uint32_t j = s; j < e; ++j) acc(j, S, false);
-        float H[2][2][2][NM] = {};
-        for (uint32_t j = hs; j < he; ++j) acc(j, H, true);  // lane 0 only
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
 #pragma unroll
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 5 : 4) k_paint_wt
 #pragma unroll
                 for (int m = 0; m < NM; ++m) {
                     float left = __shfl_up_sync(0xffffffffu, S[ox][oy][1][m], 1);
-                    if (lane == 0) left = H[ox][oy][1][m];
+                    if (lane == 0) left = Hs[((ox * 2 + oy) * NM + m) * WT::NR + r];
                     Ts[(((ox * 2 + oy) * NM + m) * WT::NR + r) * 32 + lane] = S[ox][oy][0][m] + left;
                 }
     }
