@@ -23,6 +23,11 @@
 // a tile writes 1296 floats instead of 81 x 128; k_stencil_tiles adds the
 // overlapping boxes of up to 8 tiles per cell in a fixed order.
 //
+// Both kernels are persistent (one CTA of 17 warps per SM) and warp-
+// specialised: 16 warps build operands and read accumulators, lane 0 of the
+// 17th issues the MMAs, and each layer has its own operand buffer, so one
+// tile's MMAs overlap the next tile's operand build.
+//
 // Every mbarrier wait is bounded; on timeout the block records an error flag,
 // waits (bounded) for its MMAs, frees its TMEM and returns.
 #include <algorithm>
@@ -84,18 +89,9 @@ struct Lay {
     static constexpr uint32_t S_VEC = S_B2 + NP * SZ_B2;
     static constexpr uint32_t S_B3 = S_VEC + SZ_VEC;  // backward only
     static constexpr uint32_t S_B4 = S_B3 + NP * SZ_B3;
-    static constexpr uint32_t IMG_FWD = S_B3;         // bytes of the image the forward copies
+    static constexpr uint32_t IMG_FWD = S_B3;         // bytes of the image the forward stages
     static constexpr uint32_t IMG_ALL = S_B4 + NP * SZ_B4;
-    static constexpr uint32_t SZ_A = bytes(TM, K1);   // largest A operand (one part)
-    static constexpr uint32_t S_A_FWD = IMG_FWD, S_A_BWD = IMG_ALL;
-    static constexpr uint32_t SZ_GVS = 4 * NI * TM;   // backward: g_v staged as [81][128] floats over the A region
-    static constexpr uint32_t SZ_AREG = NP * SZ_A > SZ_GVS ? NP * SZ_A : SZ_GVS;
-    // halo, partials, g_y, centre-value gradients, stencil offsets, barrier + TMEM slot
-    static constexpr uint32_t SZ_TAIL = 4 * HALO + 4 * 4 * TM + 4 * TM + 4 * 3 * TM + 4 * K1 + 64;
-    static constexpr uint32_t SMEM_FWD = S_A_FWD + SZ_AREG + SZ_TAIL;
-    static constexpr uint32_t SMEM_BWD = S_A_BWD + SZ_AREG + SZ_TAIL;
-    static_assert(SMEM_BWD <= 232448, "shared memory budget");
-    static_assert((S_B2 | S_VEC | S_B3 | S_B4 | S_A_FWD | S_A_BWD | SZ_A) % 128 == 0, "128-byte aligned regions");
+    static_assert((S_B2 | S_VEC | S_B3 | S_B4) % 128 == 0, "128-byte aligned regions");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -254,368 +250,6 @@ struct Saved {
     uint16_t* m1;
     uint8_t* m2;
 };
-
-template <bool BWD, bool TWO_NET, bool BF>
-__global__ void __launch_bounds__(NT, 1)
-    k_mlp_tc(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
-             TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ M_out,
-             float* __restrict__ gbox, Saved sv, int* __restrict__ err) {
-    using L = Lay<BF>;
-    constexpr int K1 = L::K1;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    const uint32_t S_A = BWD ? L::S_A_BWD : L::S_A_FWD;
-    unsigned char* Ahi = sm + S_A;
-    unsigned char* Alo = Ahi + (L::NP - 1) * L::SZ_A;  // == Ahi with one part
-    float* halo = reinterpret_cast<float*>(Ahi + L::SZ_AREG);
-    float* gvs = reinterpret_cast<float*>(Ahi);  // backward: g_v [81][TM], after the last MMA
-    float* part = halo + HALO;   // [4][TM]
-    float* gys = part + 4 * TM;  // [TM]
-    float* gcen = gys + TM;      // [3][TM]: gradient w.r.t. the voxel's own three values (mass network)
-    int* koff = reinterpret_cast<int*>(gcen + 3 * TM);  // [K1]: halo offset of stencil input k (-1: padding)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(koff + K1);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-    const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
-    const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, cb = warp >> 2;  // TMEM lane quadrant, column block
-    const int row = quad * 32 + lane;           // the voxel row this thread reads back
-    const uint32_t ncols = BWD ? 256u : 128u;
-    const int N = tm.N;
-    const int64_t N3 = tm.N3;
-
-    // weight images -> shared memory (once per block)
-    {
-        const uint32_t n16 = (BWD ? L::IMG_ALL : L::IMG_FWD) / 16;
-        float4* dst = reinterpret_cast<float4*>(sm);
-        for (uint32_t i = tid; i < n16; i += NT) dst[i] = img[i];
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(ncols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-    uint32_t phase = 0;
-    bool ok = true;
-    const uint32_t sA_hi = smem_u32(Ahi), sA_lo = smem_u32(Alo);
-    if (tid < K1) {
-        const int k = tid;
-        const int c = k / 27, o = k % 27, ox = o / 9, oy = (o / 3) % 3, oz = o % 3;
-        koff[k] = k < NI ? ((c * HX + ox) * HY + oy) * HZ + oz : -1;
-    }
-
-    // halo of a tile into registers (issued one tile ahead, stored at the next iteration)
-    auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
-        const uint32_t t2 = tm.ntz.div((uint32_t)tile);
-        const int tz = tile - (int)(t2 * tm.ntz.d);
-        const int tx = (int)tm.nty.div(t2);
-        const int ty = (int)t2 - tx * (int)tm.nty.d;
-        x0 = tx * TX;
-        y0 = ty * TY;
-        z0 = tz * TZ;
-    };
-    float hv[HALO_PER];
-    // backward, loaded one tile ahead: g_M, y and the centre values of rows tid < TM;
-    // the saved masks of this thread's row and column block
-    float gm_next = 0.f, y_next = 0.f, f_next[3] = {0.f, 0.f, 0.f};
-    uint32_t m1_next = 0, m2_next = 0;
-    auto load_halo = [&](int tile) {
-        if (tile >= ntiles) return;
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-        if (BWD) {
-            if (tid < TM) {
-                const int gx = x0 + (tid >> 6), gy = y0 + ((tid >> 4) & 3), gz = z0 + (tid & 15);
-                const bool in = gx < N && gy < N && gz < N;
-                const int64_t v = ((int64_t)gx * N + gy) * N + gz;
-                gm_next = in ? gM[v] : 0.f;
-                y_next = in ? sv.y[v] : 0.f;
-                if (TWO_NET)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) f_next[c] = in ? feat[c * N3 + v] : 0.f;
-            }
-            const int gx = x0 + (row >> 6), gy = y0 + ((row >> 4) & 3), gz = z0 + (row & 15);
-            const bool in = gx < N && gy < N && gz < N;
-            const int64_t v = ((int64_t)gx * N + gy) * N + gz;
-            m1_next = in ? sv.m1[cb * N3 + v] : 0u;
-            m2_next = in ? sv.m2[cb * N3 + v] : 0u;
-            return;  // the backward needs no halo
-        }
-#pragma unroll
-        for (int q = 0; q < HALO_PER; ++q) {
-            const int t = tid + q * NT;
-            if (t < HALO) {
-                const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
-                const int hx = r / (HY * HZ), hy = (r / HZ) % HY, hz = r % HZ;
-                const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
-                hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
-            }
-        }
-    };
-    load_halo(blockIdx.x);
-
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        int x0, y0, z0;
-        tile_origin(tile, x0, y0, z0);
-        // this thread's TMEM row as a voxel
-        const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
-        const bool row_in = row_gx < N && row_gy < N && row_gz < N;
-        const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
-        uint32_t mask1 = 0, mask2 = 0;
-
-        if constexpr (!BWD) {
-        // (a) this tile's halo (loaded during the previous tile) -> shared memory,
-        //     then start loading the next tile's
-#pragma unroll
-        for (int q = 0; q < HALO_PER; ++q) {
-            const int t = tid + q * NT;
-            if (t < HALO) halo[t] = hv[q];
-        }
-        __syncthreads();
-        load_halo(tile + gridDim.x);
-
-        // (b) A1: 4 threads per row, k-steps part, part+4, part+8
-        {
-            const int r = tid >> 2, p = tid & 3;
-            const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
-            for (int ks = p; ks < K1 / 8; ks += 4) {
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int ko = koff[ks * 8 + j];
-                    v[j] = ko >= 0 ? halo[ko + base] : 0.f;
-                }
-                put8<BF>(Ahi, Alo, r, ks * 8, v);
-            }
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-
-        // (c) layer 1
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D1, sA_hi, sA_lo, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1),
-                            K1, N1, nsplit);
-            mma_commit(bar);
-        }
-        ok = __syncthreads_and(mbar_wait(bar, phase));
-        phase ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-
-        // (d) relu(D1 + b1) -> A2; keep the ReLU mask of this thread's 16 columns
-        uint32_t mask1 = 0;
-        {
-            float a[16];
-            tmem_ld16(lane_base + COL_D1 + 16 * cb, a);
-            float z[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float pre = a[j] + b1[16 * cb + j];
-                mask1 |= (pre > 0.f ? 1u : 0u) << j;
-                z[j] = fmaxf(pre, 0.f);
-            }
-            if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
-            put8<BF>(Ahi, Alo, row, 16 * cb, z);
-            put8<BF>(Ahi, Alo, row, 16 * cb + 8, z + 8);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-
-        // (e) layer 2
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D2, sA_hi, sA_lo, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2),
-                            K2, N2, nsplit);
-            mma_commit(bar);
-        }
-        ok = __syncthreads_and(mbar_wait(bar, phase));
-        phase ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-
-        // (f) y = b3 + w3 . relu(D2 + b2): 8 columns per thread, partial sums per column block
-        uint32_t mask2 = 0;
-        {
-            float a[8];
-            tmem_ld8(lane_base + COL_D2 + 8 * cb, a);
-            float s = 0.f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float pre = a[j] + b2[8 * cb + j];
-                mask2 |= (pre > 0.f ? 1u : 0u) << j;
-                s = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), s);
-            }
-            part[cb * TM + row] = s;
-            if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
-        }
-        __syncthreads();
-        if (tid < TM) {
-            const int r = tid;
-            const int lx = r >> 6, ly = (r >> 4) & 3, lz = r & 15;
-            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-            const bool in = gx < N && gy < N && gz < N;
-            const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
-            const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
-            if (sv.y && in) sv.y[vox] = y;
-            if (TWO_NET) {
-                // two-network head (Sec. 2.1): M = M_scale logistic(y, a) NNm(f), f = the voxel's own values
-                float f[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
-                const float p = sigmoidf(a * y);
-                float u0, u1, u2;
-                if (in) M_out[vox] = M_scale * p * mass_net<false>(vec + VEC_MASS, f[0], f[1], f[2], 0.f, u0, u1, u2);
-            } else {
-                if (in) M_out[vox] = M_scale * softplusf(y);
-            }
-        }
-            tc_fence_before();
-            __syncthreads();
-            continue;
-        } else {
-            // (s) the forward's saved activations of this tile (loaded during the previous one)
-            mask1 = m1_next;
-            mask2 = m2_next;
-            const float gm_cur = gm_next, y_cur = y_next;
-            const float f_cur[3] = {f_next[0], f_next[1], f_next[2]};
-            load_halo(tile + gridDim.x);
-            if (tid < TM) {
-                const int r = tid;
-                const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
-                const bool in = gx < N && gy < N && gz < N;
-                const float g = in ? gm_cur * M_scale : 0.f;
-                if (TWO_NET) {
-                    // M = M_scale p m: dM/dy = M_scale m a p (1 - p); dM/dm = M_scale p
-                    const float p = sigmoidf(a * y_cur);
-                    float g0, g1, g2;
-                    const float m = mass_net<true>(vec + VEC_MASS, f_cur[0], f_cur[1], f_cur[2], g * p, g0, g1, g2);
-                    gys[r] = g * m * a * p * (1.f - p);
-                    gcen[r] = g0;
-                    gcen[TM + r] = g1;
-                    gcen[2 * TM + r] = g2;
-                } else {
-                    gys[r] = g * sigmoidf(y_cur);
-                }
-            }
-            __syncthreads();
-        }
-
-        // (g) backward: A3 = g_a2 = w3 g_y [a2 > 0] (this thread's 8 columns)
-        {
-            const float g = gys[row];
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = ((mask2 >> j) & 1u) ? w3[8 * cb + j] * g : 0.f;
-            put8<BF>(Ahi, Alo, row, 8 * cb, v);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D3, sA_hi, sA_lo, smem_u32(sm + L::S_B3), smem_u32(sm + L::S_B3 + L::SZ_B3),
-                            K3, NB3, nsplit);
-            mma_commit(bar);
-        }
-        ok = __syncthreads_and(mbar_wait(bar, phase));
-        phase ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-
-        // (h) A4 = g_a1 [a1 > 0] (16 columns, same mapping as (d))
-        {
-            float a[16];
-            tmem_ld16(lane_base + COL_D3 + 16 * cb, a);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) a[j] = ((mask1 >> j) & 1u) ? a[j] : 0.f;
-            put8<BF>(Ahi, Alo, row, 16 * cb, a);
-            put8<BF>(Ahi, Alo, row, 16 * cb + 8, a + 8);
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            issue_layer<BF>(tmem + COL_D4, sA_hi, sA_lo, smem_u32(sm + L::S_B4), smem_u32(sm + L::S_B4 + L::SZ_B4),
-                            K4, NB4, nsplit);
-            mma_commit(bar);
-        }
-        ok = __syncthreads_and(mbar_wait(bar, phase));
-        phase ^= 1;
-        if (!ok) break;
-        tc_fence_after();
-
-        // (i) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
-        {
-            const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
-            const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
-#pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                float a[8];
-                tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, a);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int k = 24 * cb + 8 * h + j;
-                    float v = a[j];
-                    if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(k / 27) * TM + row];  // mass network's input
-                    if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
-                }
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-        // (j) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
-        //     tile voxel at box cell - 1 - o, offsets o in a fixed order
-        for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
-            const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
-            const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
-            float acc = 0.f;
-#pragma unroll
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int lx = hx - 1 - ox;
-                if (lx < 0 || lx >= TX) continue;
-#pragma unroll
-                for (int oy = -1; oy <= 1; ++oy) {
-                    const int ly = hy - 1 - oy;
-                    if (ly < 0 || ly >= TY) continue;
-#pragma unroll
-                    for (int oz = -1; oz <= 1; ++oz) {
-                        const int lz = hz - 1 - oz;
-                        if (lz < 0 || lz >= TZ) continue;
-                        const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
-                        acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
-                    }
-                }
-            }
-            gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
-        }
-        __syncthreads();
-    }
-
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-        // let any MMA still in flight finish before the TMEM goes away
-        mbar_wait(bar, phase);
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-}
 
 // Compute warps synchronise among themselves on named barrier 1 (the
 // MMA-issuing warp never joins it); nbar_and also ANDs a predicate over them.
@@ -1327,35 +961,23 @@ std::vector<unsigned char> build_image(const float* W) {
 
 template <bool BF>
 int set_smem_attrs(pmr_ctx* c) {
-    using L = Lay<BF>;
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayF<BF>::SMEM), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayF<BF>::SMEM), "smem attr"));
     PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayB<BF>::SMEM), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)LayB<BF>::SMEM), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)L::SMEM_FWD), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<false, true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)L::SMEM_FWD), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)L::SMEM_BWD), "smem attr"));
-    return check_cuda(c, cudaFuncSetAttribute(k_mlp_tc<true, true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)L::SMEM_BWD), "smem attr");
+    return check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)LayB<BF>::SMEM), "smem attr");
 }
 
 template <bool BWD, bool BF>
 int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nsplit, float a) {
-    using L = Lay<BF>;
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
     const int grid = std::min(ntiles, c->num_sms);
     const float4* img = reinterpret_cast<const float4*>(BF ? c->tc_img_bf : c->tc_img);
     const float Ms = (float)c->cfg.M_scale;
-    const uint32_t smem = BWD ? L::SMEM_BWD : L::SMEM_FWD;
-    float* gv = BWD ? c->gbox : nullptr;
     const Saved sv{c->nn_y, c->nn_m1, c->nn_m2};  // written by the forward, read by the backward
     if (!BWD) {
         const uint32_t sf = LayF<BF>::SMEM;
@@ -1365,21 +987,14 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
             k_mlp_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
         return check_launch(c, "mlp_tc_fwd");
     }
-    {
-        const uint32_t sb = LayB<BF>::SMEM;
-        if (c->cfg.head == 1)
-            k_mlp_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
-        else
-            k_mlp_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, gv, sv, c->tc_err);
-        return check_launch(c, "mlp_tc_bwd");
-    }
+    const uint32_t sb = LayB<BF>::SMEM;
     if (c->cfg.head == 1)
-        k_mlp_tc<BWD, true, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv, sv,
-                                                               c->tc_err);
+        k_mlp_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
+                                                          c->tc_err);
     else
-        k_mlp_tc<BWD, false, BF><<<grid, NT, smem, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, M, gv, sv,
-                                                                c->tc_err);
-    return check_launch(c, BWD ? "mlp_tc_bwd" : "mlp_tc_fwd");
+        k_mlp_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
+                                                           c->tc_err);
+    return check_launch(c, "mlp_tc_bwd");
 }
 
 }  // namespace
