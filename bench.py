@@ -67,6 +67,7 @@ def algorithmic(name: str, N: int):
         "kick_drift": ("bytes", (12 + 12 + 24 + 12) * N3),  # F, disp in, mom r/w, disp out
         "adj_direct": ("bytes", (12 + 12 + 24 + 24) * N3),  # F, disp, lam_x r/w, lam_p r/w
         "readout_grad": ("bytes", (4 + 12 + 24) * N3),
+        "adj_readout_direct": ("bytes", (4 + 12 + 12 + 12 + 24 + 24) * N3),  # G, disp_s, F, disp_s-1, lam_x, lam_p r/w
         "keys": ("bytes", (12 + 4 + 4 + 8) * N3),  # positions -> keys, ranks; counts r/w
         "scatter": ("bytes", (4 + 4 + 4 + 4) * N3),  # keys, ranks, starts -> perm
         "stencil_T": ("bytes", (81 + 3) * 4 * N3),

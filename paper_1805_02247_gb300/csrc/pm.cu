@@ -584,6 +584,52 @@ __global__ void k_adj_direct(const float* __restrict__ F, const float* __restric
     for (int a = 0; a < 3; ++a) lam_x[a * np + i] = lx[a] + kick * g[a];
 }
 
+// Two adjoint updates in one pass over the particles: the end of step s
+// (the readout gradient of G at x_s added to lam_x) and the start of step
+// s - 1 (k_adj_direct with F = F(x_{s-1})), reading and writing lam_x once.
+__global__ void k_adj_readout_direct(const float* __restrict__ G, const float* __restrict__ disp_s,
+                                     const float* __restrict__ F, const float* __restrict__ disp_p,
+                                     float* __restrict__ lam_x, float* __restrict__ lam_p, int64_t np, int N,
+                                     FastDiv fN, float kick, float drift) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    float lx[3], lp[3];
+    {
+        const Cell cl = cell_of(disp_s, np, i, true, N, fN);
+        float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            float dw[3];
+            dwgt(cl, o, dw);
+            const float v = G[corner(cl, o, N)];
+            g[0] += dw[0] * v;
+            g[1] += dw[1] * v;
+            g[2] += dw[2] * v;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lx[a] = lam_x[a * np + i] + g[a];
+    }
+    const Cell cl = cell_of(disp_p, np, i, true, N, fN);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lp[a] = lam_p[a * np + i] + drift * lx[a];
+        lam_p[a * np + i] = lp[a];
+    }
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        float dw[3];
+        dwgt(cl, o, dw);
+        const int64_t idx = corner(cl, o, N);
+        const float v = lp[0] * F[idx] + lp[1] * F[np + idx] + lp[2] * F[2 * np + idx];
+        g[0] += dw[0] * v;
+        g[1] += dw[1] * v;
+        g[2] += dw[2] * v;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lam_x[a * np + i] = lx[a] + kick * g[a];
+}
+
 // disp = D0 psi, p = Gp0 psi (psi already in disp)
 __global__ void k_za_finish(float* __restrict__ disp, float* __restrict__ mom, int64_t n, float D0, float Gp0) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -881,16 +927,35 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
     }
     float* Fj[3] = {c->F, c->F + N3, c->F + 2 * N3};
     float* Gj[3] = {c->gfeat, c->gfeat + N3, c->gfeat + 2 * N3};
-    for (int s = c->cfg.nsteps - 1; s >= 0; --s) {
+    // Step s of the adjoint: force F(x_s) recomputed from the forward sweep's
+    // sort; direct kick term; three-mass paint and its force transpose into G;
+    // readout gradient of G at x_s. The readout of step s and the direct term
+    // of step s - 1 share one particle pass, so F(x_{s-1}) is recomputed first.
+    const int S = c->cfg.nsteps;
+    auto force_at = [&](int s) -> int {
+        PMR_TRY(density_slot(c, s, c->disp + (int64_t)s * 3 * N3, c->delta, false));
+        return conv_1toN(c, c->delta, Fj, fm, 3);
+    };
+    if (S > 0) {
+        PMR_TRY(force_at(S - 1));
+        PMR_TRY(adj_kick_direct(c, c->F, c->disp + (int64_t)(S - 1) * 3 * N3, c->lam_x, c->lam_p,
+                                (float)c->kick[S - 1], (float)c->drift[S - 1]));
+    }
+    for (int s = S - 1; s >= 0; --s) {
         const float* d = c->disp + (int64_t)s * 3 * N3;
-        PMR_TRY(density_slot(c, s, d, c->delta, false));  // the forward sweep's sort of x_s
-        PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
-        PMR_TRY(adj_kick_direct(c, c->F, d, c->lam_x, c->lam_p, (float)c->kick[s], (float)c->drift[s]));
         PMR_TRY(paint3_sorted(c, c->perm_all + (int64_t)s * N3, c->start_all + (int64_t)s * (N3 + 1),
                               c->sfrac_all + (int64_t)s * 3 * N3, c->lam_p, (float)c->kick[s], Gj));
         const float* gins[3] = {Gj[0], Gj[1], Gj[2]};
         PMR_TRY(conv_Nto1(c, gins, fmT, 3, c->gm));
-        PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
+        if (s == 0) {
+            PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
+            break;
+        }
+        PMR_TRY(force_at(s - 1));
+        k_adj_readout_direct<<<nblocks(N3, kT), kT, 0, c->stream>>>(
+            c->gm, d, c->F, c->disp + (int64_t)(s - 1) * 3 * N3, c->lam_x, c->lam_p, N3, c->N,
+            FastDiv((uint32_t)c->N), (float)c->kick[s - 1], (float)c->drift[s - 1]);
+        PMR_TRY(check_launch(c, "adj_readout_direct"));
     }
     return lpt_adjoint(c, nullptr, c->lam_x, c->lam_p, grad, true);  // Hessian kept by pm_forward
 }
