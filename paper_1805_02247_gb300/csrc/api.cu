@@ -192,10 +192,8 @@ int loss_and_grad_impl(pmr_ctx* c, const float2* s, const float* data, const pmr
     // adjoint
     PMR_TRY(residual_backward(c, an, c->gm2));
     PMR_TRY(mlp_backward(c, c->feat, c->gm2, c->gfeat, logistic_a(an)));
-    PMR_TRY(features_T(c, c->gfeat, c->gm));
-    PMR_TRY(readout_grad(c, c->gm, dfin, N3, true, 1.0f, false, c->lam_x));
-    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->lam_p, 0, sizeof(float) * 3 * N3, c->stream), "memset"));
-    PMR_TRY(pm_adjoint_impl(c, grad));
+    PMR_TRY(features_T(c, c->gfeat, c->gm2));
+    PMR_TRY(pm_adjoint_impl(c, c->gm2, grad));
     PMR_TRY(prior_grad_add(c, s, grad));
     if (host) return finish_loss(c, host);
     return PMR_OK;
@@ -359,10 +357,7 @@ int pm_adjoint(pmr_ctx* c, const float* grad_delta, void* grad_s_k) {
     PMR_TRY(check_ctx(c));
     if (!grad_delta || !grad_s_k) return fail(c, PMR_EINVAL, "NULL argument");
     if (!c->have_forward) return fail(c, PMR_ESTATE, "pm_adjoint needs a pm_forward on this context first");
-    const float* dfin = c->disp + (int64_t)c->cfg.nsteps * 3 * c->N3;
-    PMR_TRY(readout_grad(c, grad_delta, dfin, c->N3, true, 1.0f, false, c->lam_x));
-    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->lam_p, 0, sizeof(float) * 3 * c->N3, c->stream), "memset"));
-    return pm_adjoint_impl(c, (float2*)grad_s_k);
+    return pm_adjoint_impl(c, grad_delta, (float2*)grad_s_k);
 }
 
 int nn_halo_map(pmr_ctx* c, const float* delta, const pmr_anneal* an, float* mass_out) {

@@ -284,14 +284,12 @@ int readout_grad(pmr_ctx* c, const float* field, const float* pos, int64_t np, b
 int za_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom);
 int kick_drift(pmr_ctx* c, const float* F, const float* disp_in, float* disp_out, float* mom, float kick,
                float drift);
-int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
-                    float drift);
 int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad);
 int lpt_ics(pmr_ctx* c, const float2* s_k, float* disp, float* mom);
 int pm_init(pmr_ctx* c);
 int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* lam_p, float2* grad, bool have_H);
 int pm_forward_impl(pmr_ctx* c, const float2* s_k);
-int pm_adjoint_impl(pmr_ctx* c, float2* grad);  // uses c->lam_x, c->lam_p at the final state
+int pm_adjoint_impl(pmr_ctx* c, const float* gfin, float2* grad);  // gfin: gradient w.r.t. the final density
 int density_from(pmr_ctx* c, const float* disp, float* delta);
 // sfrac (nullable): also write the particles' fractional offsets in sorted order, [3][np]
 int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint32_t* keys_out, uint32_t* perm,

@@ -555,38 +555,14 @@ __global__ void k_kick_drift(const float* __restrict__ F, const float* __restric
     }
 }
 
-// Adjoint of drift then the direct (weight-gradient) part of the kick adjoint:
-// lam_p += drift * lam_x;  lam_x += kick * sum_j lam_p_j grad_x R_j(x).
-__global__ void k_adj_direct(const float* __restrict__ F, const float* __restrict__ disp, float* __restrict__ lam_x,
-                             float* __restrict__ lam_p, int64_t np, int N, FastDiv fN, float kick, float drift) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    Cell cl = cell_of(disp, np, i, true, N, fN);
-    float lp[3], lx[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        lx[a] = lam_x[a * np + i];
-        lp[a] = lam_p[a * np + i] + drift * lx[a];
-        lam_p[a * np + i] = lp[a];
-    }
-    float g[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        float dw[3];
-        dwgt(cl, o, dw);
-        const int64_t idx = corner(cl, o, N);
-        const float v = lp[0] * F[idx] + lp[1] * F[np + idx] + lp[2] * F[2 * np + idx];
-        g[0] += dw[0] * v;
-        g[1] += dw[1] * v;
-        g[2] += dw[2] * v;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) lam_x[a * np + i] = lx[a] + kick * g[a];
-}
-
 // Two adjoint updates in one pass over the particles: the end of step s
 // (the readout gradient of G at x_s added to lam_x) and the start of step
-// s - 1 (k_adj_direct with F = F(x_{s-1})), reading and writing lam_x once.
+// s - 1, the adjoint of its drift then the direct (weight-gradient) part of
+// its kick: lam_p += drift lam_x; lam_x += kick sum_j lam_p_j grad_x R_j(x)
+// with R the readout of F = F(x_{s-1}). lam_x is read and written once.
+// INIT: the first pass of the adjoint, whose lam_x is the readout gradient of
+// the final density's gradient G alone and whose lam_p starts at zero.
+template <bool INIT>
 __global__ void k_adj_readout_direct(const float* __restrict__ G, const float* __restrict__ disp_s,
                                      const float* __restrict__ F, const float* __restrict__ disp_p,
                                      float* __restrict__ lam_x, float* __restrict__ lam_p, int64_t np, int N,
@@ -607,12 +583,12 @@ __global__ void k_adj_readout_direct(const float* __restrict__ G, const float* _
             g[2] += dw[2] * v;
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) lx[a] = lam_x[a * np + i] + g[a];
+        for (int a = 0; a < 3; ++a) lx[a] = INIT ? g[a] : lam_x[a * np + i] + g[a];
     }
     const Cell cl = cell_of(disp_p, np, i, true, N, fN);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lp[a] = lam_p[a * np + i] + drift * lx[a];
+        lp[a] = INIT ? drift * lx[a] : lam_p[a * np + i] + drift * lx[a];
         lam_p[a * np + i] = lp[a];
     }
     float g[3] = {0.f, 0.f, 0.f};
@@ -879,11 +855,6 @@ int kick_drift(pmr_ctx* c, const float* F, const float* din, float* dout, float*
     return check_launch(c, "kick_drift");
 }
 
-int adj_kick_direct(pmr_ctx* c, const float* F, const float* disp, float* lam_x, float* lam_p, float kick,
-                    float drift) {
-    k_adj_direct<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, disp, lam_x, lam_p, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
-    return check_launch(c, "adj_direct");
-}
 
 // grad_s = sum_j conj(i k_j / k^2) (w / N^3) rfft(D0 lam_x_j + Gp0 lam_p_j)
 int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad) {
@@ -917,7 +888,9 @@ int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
 }
 
 // Reverse sweep. On entry lam_x holds dL/dx at the final positions and lam_p = 0.
-int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
+// gfin: the loss gradient with respect to the final density (N^3); the
+// adjoint starts with lam_x = its readout gradient at x_nsteps and lam_p = 0.
+int pm_adjoint_impl(pmr_ctx* c, const float* gfin, float2* grad) {
     const int64_t N3 = c->N3;
     const float om15 = (float)(1.5 * c->cfg.omega_m);
     Mul fm[3], fmT[3];
@@ -930,16 +903,23 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
     // Step s of the adjoint: force F(x_s) recomputed from the forward sweep's
     // sort; direct kick term; three-mass paint and its force transpose into G;
     // readout gradient of G at x_s. The readout of step s and the direct term
-    // of step s - 1 share one particle pass, so F(x_{s-1}) is recomputed first.
+    // of step s - 1 share one particle pass (as do the final density's readout
+    // and the direct term of the last step), so F(x_{s-1}) is recomputed first.
     const int S = c->cfg.nsteps;
+    const FastDiv fN((uint32_t)c->N);
     auto force_at = [&](int s) -> int {
         PMR_TRY(density_slot(c, s, c->disp + (int64_t)s * 3 * N3, c->delta, false));
         return conv_1toN(c, c->delta, Fj, fm, 3);
     };
-    if (S > 0) {
+    if (S == 0) {
+        PMR_TRY(readout_grad(c, gfin, c->disp, N3, true, 1.0f, false, c->lam_x));
+        PMR_TRY(check_cuda(c, cudaMemsetAsync(c->lam_p, 0, sizeof(float) * 3 * N3, c->stream), "memset"));
+    } else {
         PMR_TRY(force_at(S - 1));
-        PMR_TRY(adj_kick_direct(c, c->F, c->disp + (int64_t)(S - 1) * 3 * N3, c->lam_x, c->lam_p,
-                                (float)c->kick[S - 1], (float)c->drift[S - 1]));
+        k_adj_readout_direct<true><<<nblocks(N3, kT), kT, 0, c->stream>>>(
+            gfin, c->disp + (int64_t)S * 3 * N3, c->F, c->disp + (int64_t)(S - 1) * 3 * N3, c->lam_x, c->lam_p, N3,
+            c->N, fN, (float)c->kick[S - 1], (float)c->drift[S - 1]);
+        PMR_TRY(check_launch(c, "adj_readout_direct"));
     }
     for (int s = S - 1; s >= 0; --s) {
         const float* d = c->disp + (int64_t)s * 3 * N3;
@@ -952,9 +932,9 @@ int pm_adjoint_impl(pmr_ctx* c, float2* grad) {
             break;
         }
         PMR_TRY(force_at(s - 1));
-        k_adj_readout_direct<<<nblocks(N3, kT), kT, 0, c->stream>>>(
-            c->gm, d, c->F, c->disp + (int64_t)(s - 1) * 3 * N3, c->lam_x, c->lam_p, N3, c->N,
-            FastDiv((uint32_t)c->N), (float)c->kick[s - 1], (float)c->drift[s - 1]);
+        k_adj_readout_direct<false><<<nblocks(N3, kT), kT, 0, c->stream>>>(
+            c->gm, d, c->F, c->disp + (int64_t)(s - 1) * 3 * N3, c->lam_x, c->lam_p, N3, c->N, fN,
+            (float)c->kick[s - 1], (float)c->drift[s - 1]);
         PMR_TRY(check_launch(c, "adj_readout_direct"));
     }
     return lpt_adjoint(c, nullptr, c->lam_x, c->lam_p, grad, true);  // Hessian kept by pm_forward
