@@ -299,7 +299,7 @@ struct LayF {
 
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
-    k_mlp_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
+    k_mlp_tc_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
               float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err) {
     using L = Lay<BF>;
     using F = LayF<BF>;
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(NTW, 1)
 }
 
 // Backward (input gradient) from the forward's saved activations, warp-
-// specialised and pipelined like k_mlp_fwd, with separate A3 / A4 operand
+// specialised and pipelined like k_mlp_tc_fwd, with separate A3 / A4 operand
 // buffers and g_v staging. Per tile t (t' = the CTA's next tile), compute warps:
 //   wait D3(t); D3 [a1 > 0] -> A4, arrive A4; g_y(t') -> A3, arrive A3;
 //   wait D4(t); D4 -> g_v -> box sums
@@ -588,7 +588,7 @@ struct LayB {
 
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
-    k_mlp_bwd(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
+    k_mlp_tc_bwd(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
               TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ gbox, Saved sv,
               int* __restrict__ err) {
     using L = Lay<BF>;
@@ -961,13 +961,13 @@ std::vector<unsigned char> build_image(const float* W) {
 
 template <bool BF>
 int set_smem_attrs(pmr_ctx* c) {
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc_fwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayF<BF>::SMEM), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_fwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc_fwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayF<BF>::SMEM), "smem attr"));
-    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PMR_TRY(check_cuda(c, cudaFuncSetAttribute(k_mlp_tc_bwd<false, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)LayB<BF>::SMEM), "smem attr"));
-    return check_cuda(c, cudaFuncSetAttribute(k_mlp_bwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return check_cuda(c, cudaFuncSetAttribute(k_mlp_tc_bwd<true, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)LayB<BF>::SMEM), "smem attr");
 }
 
@@ -982,17 +982,17 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     if (!BWD) {
         const uint32_t sf = LayF<BF>::SMEM;
         if (c->cfg.head == 1)
-            k_mlp_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_tc_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
         else
-            k_mlp_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_tc_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
         return check_launch(c, "mlp_tc_fwd");
     }
     const uint32_t sb = LayB<BF>::SMEM;
     if (c->cfg.head == 1)
-        k_mlp_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
+        k_mlp_tc_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
                                                           c->tc_err);
     else
-        k_mlp_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
+        k_mlp_tc_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
                                                            c->tc_err);
     return check_launch(c, "mlp_tc_bwd");
 }

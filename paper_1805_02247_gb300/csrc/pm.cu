@@ -533,25 +533,50 @@ __global__ void k_readout_grad(const float* __restrict__ f, const float* __restr
 // ----------------------------------------------------------------------------- stepping
 
 // Forward step: p += kick * R(x) (force read out at x), disp' = disp + drift * p.
+// Each thread takes KP particles, blockDim apart, with every load of all of
+// them issued before their arithmetic (more memory requests in flight).
+constexpr int KP = 2;
 __global__ void k_kick_drift(const float* __restrict__ F, const float* __restrict__ din, float* __restrict__ dout,
                              float* __restrict__ mom, int64_t np, int N, FastDiv fN, float kick, float drift) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    Cell cl = cell_of(din, np, i, true, N, fN);
-    float r[3] = {0.f, 0.f, 0.f};
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * KP + threadIdx.x;
+    Cell cl[KP];
+    float r[KP][3], p[KP][3], d[KP][3];
 #pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        const int64_t idx = corner(cl, o, N);
-        const float w = wgt(cl, o);
-        r[0] += w * F[idx];
-        r[1] += w * F[np + idx];
-        r[2] += w * F[2 * np + idx];
+    for (int u = 0; u < KP; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i < np) {
+            cl[u] = cell_of(din, np, i, true, N, fN);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                p[u][a] = mom[a * np + i];
+                d[u][a] = din[a * np + i];
+            }
+        }
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float p = mom[a * np + i] + kick * r[a];
-        mom[a * np + i] = p;
-        dout[a * np + i] = din[a * np + i] + drift * p;
+    for (int u = 0; u < KP; ++u) {
+        r[u][0] = r[u][1] = r[u][2] = 0.f;
+        if (i0 + (int64_t)u * blockDim.x < np) {
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                const int64_t idx = corner(cl[u], o, N);
+                const float w = wgt(cl[u], o);
+                r[u][0] += w * F[idx];
+                r[u][1] += w * F[np + idx];
+                r[u][2] += w * F[2 * np + idx];
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i >= np) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float pa = p[u][a] + kick * r[u][a];
+            mom[a * np + i] = pa;
+            dout[a * np + i] = d[u][a] + drift * pa;
+        }
     }
 }
 
@@ -851,7 +876,7 @@ int lpt_adjoint(pmr_ctx* c, const float2* s_k, const float* lam_x, const float* 
 }
 
 int kick_drift(pmr_ctx* c, const float* F, const float* din, float* dout, float* mom, float kick, float drift) {
-    k_kick_drift<<<nblocks(c->N3, kT), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
+    k_kick_drift<<<nblocks(c->N3, kT * KP), kT, 0, c->stream>>>(F, din, dout, mom, c->N3, c->N, FastDiv((uint32_t)c->N), kick, drift);
     return check_launch(c, "kick_drift");
 }
 
