@@ -255,11 +255,45 @@ __global__ void k_permute3(const uint32_t* __restrict__ perm, const float* __res
 // arbitrary), then, with sfrac, every particle's fractional CIC offsets in the
 // sorted order: sfrac[a][j] of particle perm[j] (the float32 values cell_of
 // gives). A block owns kFixCells consecutive cells, whose particles are one
-// contiguous run of perm: the run is staged in shared memory, each segment is
-// insertion-sorted by one thread, and the run is written back with coalesced
-// stores. A run longer than kFixCap, or holding a segment longer than
-// kSegShort, is listed in ovf for k_seg_fix_big (global memory).
+// contiguous run of perm: the run is staged in shared memory, segments of up to
+// kSegShort particles are insertion-sorted by one thread each, longer ones
+// (crowded cells of a clustered field) by the whole block with seg_sort, and
+// the run is written back with coalesced stores. A run longer than kFixCap is
+// listed in ovf for k_seg_fix_big, which does the same in global memory.
 constexpr int kFixCells = 512, kFixT = 256, kFixCap = 5120, kSegShort = 32;
+
+// Sorts a[0, len) ascending with every thread of the block (a bitonic network
+// over the next power of two P >= len, in the form whose every compare-exchange
+// puts the smaller value at the lower index: the first step of each merge pairs
+// mirrored positions. Positions >= len act as +infinity and are never touched.)
+// All threads of the block must call it; it ends with a block barrier.
+__device__ void seg_sort(uint32_t* a, int len) {
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                int lo, hi;
+                if (j == (k >> 1)) {  // mirrored pairs within blocks of k
+                    const int blk = t / j, o = t - blk * j;
+                    lo = blk * k + o;
+                    hi = blk * k + k - 1 - o;
+                } else {  // half-cleaner at distance j
+                    lo = (t / j) * 2 * j + (t % j);
+                    hi = lo + j;
+                }
+                if (hi < len) {
+                    const uint32_t x = a[lo], y = a[hi];
+                    if (x > y) {
+                        a[lo] = y;
+                        a[hi] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
 
 __device__ __forceinline__ void write_sorted(uint32_t i, int64_t j, const float* __restrict__ pos, int64_t np,
                                              bool lattice, int N, const FastDiv& fN, uint32_t* __restrict__ perm,
@@ -279,12 +313,13 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
                                                    uint32_t* __restrict__ ovf, uint32_t* __restrict__ novf) {
     __shared__ uint32_t buf[kFixCap];
     __shared__ uint32_t sst[kFixCells + 1];
-    __shared__ int has_long;
+    __shared__ uint32_t longs[kFixCells];
+    __shared__ int nlong;
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * kFixCells;
     const int nc = (int)min((int64_t)kFixCells, ncell - c0);
     for (int t = tid; t <= nc; t += kFixT) sst[t] = start[c0 + t];
-    if (tid == 0) has_long = 0;
+    if (tid == 0) nlong = 0;
     __syncthreads();
     const uint32_t s0 = sst[0];
     const int n = (int)(sst[nc] - s0);
@@ -298,7 +333,7 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
         if (e - a <= 1) continue;
         if (e - a > kSegShort) {
-            has_long = 1;
+            longs[atomicAdd(&nlong, 1)] = (uint32_t)cl;
             continue;
         }
         for (int p = a + 1; p < e; ++p) {
@@ -312,20 +347,22 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         }
     }
     __syncthreads();
-    if (has_long) {  // nothing written yet: the whole run goes to the global-memory pass
-        if (tid == 0) ovf[atomicAdd(novf, 1u)] = blockIdx.x;
-        return;
+    const int nl = nlong;
+    for (int li = 0; li < nl; ++li) {
+        const int cl = (int)longs[li];
+        const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
+        seg_sort(buf + a, e - a);
     }
     for (int j = tid; j < n; j += kFixT) write_sorted(buf[j], (int64_t)s0 + j, pos, np, lattice, N, fN, perm, sfrac);
 }
 
 // The runs k_seg_fix could not stage: the same steps on global memory, one
-// block per listed run; tmp is scratch of np entries.
+// block per listed run.
 __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
                                                        int64_t ncell, const float* __restrict__ pos, int64_t np,
                                                        bool lattice, int N, FastDiv fN, float* __restrict__ sfrac,
                                                        const uint32_t* __restrict__ ovf,
-                                                       const uint32_t* __restrict__ novf, uint32_t* __restrict__ tmp) {
+                                                       const uint32_t* __restrict__ novf) {
     const uint32_t no = *novf;
     const int tid = threadIdx.x;
     for (uint32_t bi = blockIdx.x; bi < no; bi += gridDim.x) {
@@ -347,16 +384,7 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
         __syncthreads();
         for (int cl = 0; cl < nc; ++cl) {
             const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
-            if (e - a <= (uint32_t)kSegShort) continue;
-            for (uint32_t p = a + tid; p < e; p += kFixT) {
-                const uint32_t v = perm[p];
-                uint32_t r = 0;
-                for (uint32_t q = a; q < e; ++q) r += perm[q] < v;
-                tmp[a + r] = v;
-            }
-            __syncthreads();
-            for (uint32_t p = a + tid; p < e; p += kFixT) perm[p] = tmp[p];
-            __syncthreads();
+            if (e - a > (uint32_t)kSegShort) seg_sort(perm + a, (int)(e - a));
         }
         const uint32_t s0 = start[c0], s1 = start[c0 + nc];
         for (uint32_t j = s0 + tid; j < s1; j += kFixT) write_sorted(perm[j], j, pos, np, lattice, N, fN, perm, sfrac);
@@ -714,8 +742,8 @@ int cell_sort_into(pmr_ctx* c, const float* pos, int64_t np, bool lattice, uint3
     k_seg_fix<<<nblocks(N3, kFixCells), kFixT, 0, c->stream>>>(start, perm, N3, pos, np, lattice, N, fN, sfrac,
                                                                c->long_list, c->long_count);
     PMR_TRY(check_launch(c, "seg_fix"));
-    k_seg_fix_big<<<128, kFixT, 0, c->stream>>>(start, perm, N3, pos, np, lattice, N, fN, sfrac, c->long_list,
-                                               c->long_count, c->sort_tmp);
+    k_seg_fix_big<<<256, kFixT, 0, c->stream>>>(start, perm, N3, pos, np, lattice, N, fN, sfrac, c->long_list,
+                                               c->long_count);
     return check_launch(c, "seg_fix_big");
 }
 
