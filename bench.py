@@ -61,6 +61,7 @@ def algorithmic(name: str, N: int):
         "x_inv_3": ("bytes", 32 * NH), "x_inv_1": ("bytes", 16 * NH),
         "paint": ("bytes", (12 + 4 + 4) * N3),         # sorted offsets, bin starts -> density
         "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),  # sorted offsets, perm, starts, 3 masses -> 3 meshes
+        "permute3": ("bytes", (4 + 12 + 12) * N3),  # perm, 3 masses -> 3 masses in sorted order
         "seg_fix": ("bytes", (4 + 8 + 12 + 12) * N3),  # starts, perm r/w, positions -> sorted offsets
         "scan_reduce": ("bytes", 4 * N3),
         "scan_apply": ("bytes", 8 * N3),
@@ -93,9 +94,14 @@ def algorithmic(name: str, N: int):
 # kernels on this workload (profiles/dram_traffic_256cubed.md); kernels changed
 # since their counters were taken have no entry. Valid for N = 256 only.
 TRAFFIC_256 = {
+    "paint3": 471.6e6 + 177.3e6,
+    "paint": 269.5e6 + 50.2e6,
+    "adj_readout_direct": 1076.5e6 + 373.5e6,
+    "x_conv_3": 67.9e6 + 144.7e6,
+    "x_conv_in3": 203.0e6 + 43.6e6,
     "col_pass": 67.7e6 + 8.9e6,
-    "z_c2r": 67.7e6 + 18.0e6,
-    "z_r2c": 67.1e6 + 18.2e6,
+    "z_c2r": 67.7e6 + 14.3e6,
+    "z_r2c": 67.1e6 + 15.3e6,
 }
 
 
