@@ -660,6 +660,33 @@ __global__ void __launch_bounds__(RG::T, 65536 / (RG::T * 128)) k_x_reg(XFused p
         }
     };
 
+    // i s1 R to dst1 and i s2 R to dst2 through one inverse transform (s1, s2
+    // constant along the transform axis)
+    auto emit2 = [&](float2 (&R)[RG::A2][RG::N2], float2* dst1, float s1, float2* dst2, float s2) {
+        if (p.inv) {
+            four_step_inv<RG, true>(R, v1, S, s_tw, c, g);
+            if (ok)
+#pragma unroll
+                for (int a = 0; a < RG::A1; ++a)
+#pragma unroll
+                    for (int n1 = 0; n1 < RG::N1; ++n1) {
+                        const int64_t o = base + (int64_t)(g + RG::G * a + RG::N2 * n1) * geo.es;
+                        const float2 v = v1[a][n1];
+                        put(dst1 + o, make_float2(-s1 * v.y, s1 * v.x), p.acc);
+                        put(dst2 + o, make_float2(-s2 * v.y, s2 * v.x), p.acc);
+                    }
+        } else if (ok) {
+#pragma unroll
+            for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                for (int k2 = 0; k2 < RG::N2; ++k2) {
+                    const int64_t o = base + (int64_t)(g + RG::G * a + RG::N1 * k2) * geo.es;
+                    const float2 v = R[a][k2];
+                    put(dst1 + o, make_float2(-s1 * v.y, s1 * v.x), p.acc);
+                    put(dst2 + o, make_float2(-s2 * v.y, s2 * v.x), p.acc);
+                }
+        }
+    };
     float2 X[RG::A2][RG::N2];
     if constexpr (MODE == 0) {
         to_k(p.in[0], X);
@@ -680,25 +707,35 @@ __global__ void __launch_bounds__(RG::T, 65536 / (RG::T * 128)) k_x_reg(XFused p
                     }
                     Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x] = v;
                 }
-#pragma unroll 1
-            for (int o = 0; o < p.nout; ++o) {
+            if (p.odd3) {
+                // x component: its k_x varies along the transform axis
+#pragma unroll
+                for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+                    for (int k2 = 0; k2 < RG::N2; ++k2) {
+                        const int mx = g + RG::G * a + RG::N1 * k2;
+                        const float kj = odd_k(0, (2 * mx <= N) ? mx : mx - N, ny, kz, N);
+                        const float2 v = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
+                        X[a][k2] = make_float2(-kj * v.y, kj * v.x);
+                    }
+                emit(X, p.out[0]);
+                // y and z components: k_y, k_z are constant along it, so both come
+                // from one inverse transform of the kept tile
 #pragma unroll
                 for (int a = 0; a < RG::A2; ++a)
 #pragma unroll
                     for (int k2 = 0; k2 < RG::N2; ++k2) X[a][k2] = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
-                if (p.odd3) {
+                emit2(X, p.out[1], odd_k(1, 0, ny, kz, N), p.out[2], odd_k(2, 0, ny, kz, N));
+            } else {
+#pragma unroll 1
+                for (int o = 0; o < p.nout; ++o) {
 #pragma unroll
                     for (int a = 0; a < RG::A2; ++a)
 #pragma unroll
-                        for (int k2 = 0; k2 < RG::N2; ++k2) {
-                            const int mx = g + RG::G * a + RG::N1 * k2;
-                            const float kj = odd_k(o, (2 * mx <= N) ? mx : mx - N, ny, kz, N);
-                            X[a][k2] = make_float2(-kj * X[a][k2].y, kj * X[a][k2].x);
-                        }
-                } else {
+                        for (int k2 = 0; k2 < RG::N2; ++k2) X[a][k2] = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
                     mul_into(p.mul[o], X, X, false);
+                    emit(X, p.out[o]);
                 }
-                emit(X, p.out[o]);
             }
         }
     } else {

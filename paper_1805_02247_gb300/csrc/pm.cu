@@ -412,13 +412,13 @@ template <int NM>
 struct WTile {
     static constexpr int X = NM == 1 ? 8 : 4, Y = NM == 1 ? 8 : 4;
     static constexpr int RX = X + 1, RY = Y + 1, NR = RX * RY;
-    static constexpr int W = 8;  // warps per block
+    static constexpr int W = NM == 1 ? 9 : 8;  // warps per block (one mass: 9 rows each)
     // T values [4][NM][NR][32], then the halo bins' S_(ox,oy,1) [4][NM][NR]
     static constexpr size_t smem = sizeof(float) * 4 * NM * NR * 33;
 };
 
 template <int NM, int MMODE>
-__global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 5 : 4) k_paint_wtile(const uint32_t* __restrict__ start,
+__global__ void __launch_bounds__(WTile<NM>::W * 32, 4) k_paint_wtile(const uint32_t* __restrict__ start,
                                                                      const uint32_t* __restrict__ perm,
                                                                      const float* __restrict__ sfrac,
                                                                      const float* __restrict__ mass, int64_t np, int N,
