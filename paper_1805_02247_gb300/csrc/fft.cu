@@ -1168,7 +1168,8 @@ int conv_1toN(pmr_ctx* c, const float* in, float* const* out, const Mul* mul, in
     PMR_TRY(launch_col(c, c->cA, c->cA, geom_y(c), false));
     const float2* ins[1] = {c->cA};
     PMR_TRY(launch_x_fused(c, make_x(ins, 1, outs, nout, mul, nout, true, true, c)));
-    for (int j = 0; j < nout; ++j) {
+    // last-written output first: more of it is still in L2
+    for (int j = nout - 1; j >= 0; --j) {
         PMR_TRY(launch_col(c, outs[j], outs[j], geom_y(c), true));
         PMR_TRY(launch_z_c2r(c, outs[j], out[j]));
     }
@@ -1177,7 +1178,8 @@ int conv_1toN(pmr_ctx* c, const float* in, float* const* out, const Mul* mul, in
 
 int conv_Nto1(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float* out) {
     float2* ks[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
-    for (int i = 0; i < nin; ++i) {
+    // input 0 last: the fused pass reads it first, so more of it is still in L2
+    for (int i = nin - 1; i >= 0; --i) {
         PMR_TRY(launch_z_r2c(c, in[i], ks[i]));
         PMR_TRY(launch_col(c, ks[i], ks[i], geom_y(c), false));
     }
