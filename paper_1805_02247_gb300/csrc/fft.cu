@@ -809,11 +809,15 @@ struct ZReg {
 // four-step M-point transform of row r (natural order in A -> natural order in A).
 // The G threads of a row are lanes of one warp and the transpose buffer S is
 // the row's own staging memory, so warp barriers order the steps.
-template <class RG, bool INV>
-__device__ __forceinline__ void row_fft(float2* A, const float2* tw, int g) {
+// TO_REGS: the result stays in v2 (element k1 + N1 k2 in v2[a][k2],
+// k1 = g + G a) instead of going back to A, and there is no closing block
+// barrier. (Loading the input the same way, straight from global memory with
+// G-strided 8-byte elements, was slower than the staged coalesced loads.)
+template <class RG, bool INV, bool TO_REGS = false>
+__device__ __forceinline__ void row_fft(float2* A, const float2* tw, int g, float2 (&v1)[RG::A1][RG::N1],
+                                        float2 (&v2)[RG::A2][RG::N2]) {
     constexpr int N1 = RG::N1, N2 = RG::N2, G = RG::G;
     float2* S = A;
-    float2 v1[RG::A1][N1];
 #pragma unroll
     for (int a = 0; a < RG::A1; ++a) {
         const int n2 = g + G * a;
@@ -837,22 +841,22 @@ __device__ __forceinline__ void row_fft(float2* A, const float2* tw, int g) {
         }
     }
     __syncwarp();
-    float2 v2[RG::A2][N2];
 #pragma unroll
     for (int a = 0; a < RG::A2; ++a) {
         const int k1 = g + G * a;
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) v2[a][n2] = S[k1 * (N2 + 1) + n2];
     }
-    __syncwarp();  // S read before the result overwrites it
+    if (!TO_REGS) __syncwarp();  // S read before the result overwrites it
 #pragma unroll
     for (int a = 0; a < RG::A2; ++a) {
         const int k1 = g + G * a;
         dft_reg<N2, INV, N1>(v2[a], tw);
+        if (!TO_REGS)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) A[k1 + N1 * k2] = v2[a][k2];
+            for (int k2 = 0; k2 < N2; ++k2) A[k1 + N1 * k2] = v2[a][k2];
     }
-    __syncthreads();
+    if (!TO_REGS) __syncthreads();
 }
 
 template <class RG>
@@ -887,8 +891,11 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
         }
     }
     __syncthreads();
-    const int r = tid / Z::G, g = tid - r * Z::G;
-    row_fft<RG, false>(A + r * Z::PITCH, s_twM, g);
+    {
+        const int r = tid / Z::G, g = tid - r * Z::G;
+        float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
+        row_fft<RG, false>(A + r * Z::PITCH, s_twM, g, v1, v2);
+    }
     // X_k = E_k + exp(-2 pi i k / N) O_k from Z_k and conj(Z_(M-k))
     for (int t = tid; t < Z::R * P; t += Z::T) {
         const int rr = t / P, k = t - rr * P;
@@ -970,12 +977,16 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     }
     __syncthreads();
     const int r = tid / Z::G, g = tid - r * Z::G;
-    row_fft<RG, true>(A + r * Z::PITCH, s_twM, g);
-    float2* dst = reinterpret_cast<float2*>(out + row0 * N);
-    const float sc = scale * 2.0f / (float)N;
-    for (int t = tid; t < Z::R * M; t += Z::T) {
-        const int rr = t / M, m = t - rr * M;
-        if (rr < rows) dst[(int64_t)rr * M + m] = cscale(A[rr * Z::PITCH + m], sc);
+    float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
+    row_fft<RG, true, true>(A + r * Z::PITCH, s_twM, g, v1, v2);
+    // the row from the four-step's registers straight to global memory
+    if (r < rows) {
+        float2* drow = reinterpret_cast<float2*>(out + (row0 + r) * N);
+        const float sc = scale * 2.0f / (float)N;
+#pragma unroll
+        for (int a = 0; a < RG::A2; ++a)
+#pragma unroll
+            for (int k2 = 0; k2 < RG::N2; ++k2) drow[g + Z::G * a + RG::N1 * k2] = cscale(v2[a][k2], sc);
     }
 }
 

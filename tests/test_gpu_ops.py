@@ -65,6 +65,31 @@ def test_cell_sort_overfull_block():
     assert rel_l2(rho, opm.paint(f32(x), N, f32_wrap=True)) <= FIELD_TOL
 
 
+@pytest.mark.parametrize("N", [16, 18])
+def test_cell_sort_many_crowded_cells(N):
+    # several cells of 33 to about 1000 particles inside one staged block (the block-wide
+    # sort of long segments in shared memory), short segments beside them, and
+    # for N = 18 a last block of fewer than 512 cells
+    rng = np.random.default_rng(21 + N)
+    centres = rng.integers(0, 2, size=(20, 3)) + np.array([0, 0, 0])
+    counts = rng.integers(33, 300, size=20)
+    parts = [np.stack([np.full(k, cx + 0.5), np.full(k, cy + 0.5), np.full(k, cz * 3 + 0.25)])
+             + rng.uniform(-0.45, 0.45, size=(3, k)) * np.array([[1.0], [1.0], [0.2]])
+             for (cx, cy, cz), k in zip(centres, counts)]
+    dense = np.concatenate(parts, axis=1)
+    rest = synth.uniform_positions(N, N**3 - dense.shape[1], seed=22 + N, lo=0.0, hi=float(N))
+    x = np.concatenate([dense, rest], axis=1).astype(np.float32)
+    x = x[:, rng.permutation(x.shape[1])]
+    ctx, _ = context(N=N)
+    keys, perm, start = ctx.cell_sort(to_dev(x))
+    want_perm, want_start = opm.sort_by_cell(opm.cell_keys(x, N), N)
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+    assert np.diff(want_start).max() > 32
+    rho = to_np(ctx.paint(to_dev(x)))
+    assert rel_l2(rho, opm.paint(f32(x), N, f32_wrap=True)) <= FIELD_TOL
+
+
 @pytest.mark.parametrize("N,np_", [(16, 4096), (32, 20000), (16, 0), (24, 9000), (48, 60000), (8, 100)])
 def test_paint_parity_and_mass_conservation(N, np_):
     ctx, _ = context(N=N)
