@@ -282,7 +282,7 @@ constexpr int NTW = NT + 32;  // 16 compute warps + the warp whose lane 0 issues
 // Per tile t (t' = the CTA's next tile), compute warps:
 //   wait D1(t); D1 -> A2, arrive A2; halo(t') -> A1, arrive A1; wait D2(t); D2 -> y, M
 // and the issuing lane: wait A1(t), MMA1(t) -> D1; wait A2(t), MMA2(t) -> D2.
-// Arithmetic per voxel is that of k_mlp_tc.
+
 template <bool BF>
 struct LayF {
     using L = Lay<BF>;
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(NTW, 1)
 //   wait D4(t); D4 -> g_v -> box sums
 // and the issuing lane: wait A3(t), MMA3(t) -> D3; wait A4(t), MMA4(t) -> D4.
 // Only the layer-2 and layer-1 weight images (B3 = W2, B4 = W1) and the vector
-// block are staged. Arithmetic per voxel is that of k_mlp_tc<true, ...>.
+// block are staged.
 template <bool BF>
 struct LayB {
     using L = Lay<BF>;
