@@ -94,6 +94,24 @@ def uniform_positions(n: int, npart: int, seed: int, lo: float = 0.0, hi: float 
     return rng(seed).uniform(lo, hi, size=(3, npart)).astype(np.float32)
 
 
+def clustered_positions(n: int, npart: int, seed: int, ncentres: int = 20000, frac: float = 0.5,
+                        sigma: float = 0.4) -> np.ndarray:
+    """Particle positions in grid units, float32 SoA [3][npart], the crowded
+    cells of an evolved field: a fraction `frac` of the particles in Gaussian
+    clumps (width `sigma` cells) around uniform centres with log-normally
+    distributed occupations, the rest uniform in [0, n)."""
+    g = rng(seed)
+    nc = int(frac * npart)
+    w = g.lognormal(0.0, 1.5, size=ncentres)
+    occ = np.floor(w / w.sum() * nc).astype(np.int64)
+    occ[: nc - occ.sum()] += 1
+    centres = g.uniform(0.0, n, size=(3, ncentres))
+    clumps = np.repeat(centres, occ, axis=1) + g.normal(0.0, sigma, size=(3, int(occ.sum())))
+    rest = g.uniform(0.0, n, size=(3, npart - clumps.shape[1]))
+    x = np.concatenate([clumps, rest], axis=1)
+    return x[:, g.permutation(npart)].astype(np.float32)
+
+
 def edge_positions(n: int) -> np.ndarray:
     """Hand-picked positions that stress the wrap and floor rules, float32 [3][k].
 

@@ -58,6 +58,23 @@ def test_cell_sort_bit_exact_full(job, positions):
     assert np.array_equal(to_np(start).view(np.uint32), want_start)
 
 
+def test_cell_sort_and_paint_clustered_full(job):
+    # the crowded cells of an evolved field: segments of up to ~10^4 particles,
+    # block-wide sorts of long segments in shared memory and, for runs past
+    # the stage, in global memory
+    ctx, _, _ = job
+    xc = synth.clustered_positions(N, N ** 3, seed=105)
+    keys, perm, start = ctx.cell_sort(to_dev(xc))
+    want_perm, want_start = opm.sort_by_cell(opm.cell_keys(xc, N), N)
+    assert np.diff(want_start.astype(np.int64)).max() > 5120
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+    x = to_dev(xc)
+    rho = to_np(ctx.paint(x))
+    assert rel_l2(rho, opm.paint(f32(xc), N, f32_wrap=True)) <= FIELD_TOL
+    assert np.array_equal(rho, to_np(ctx.paint(x)))  # same bits twice
+
+
 def test_paint_and_readout_full(job, positions):
     ctx, _, _ = job
     x = to_dev(positions)
