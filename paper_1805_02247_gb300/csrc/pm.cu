@@ -256,23 +256,29 @@ __global__ void k_permute3(const uint32_t* __restrict__ perm, const float* __res
 // sorted order: sfrac[a][j] of particle perm[j] (the float32 values cell_of
 // gives). A block owns kFixCells consecutive cells, whose particles are one
 // contiguous run of perm: the run is staged in shared memory, segments of up to
-// kSegShort particles are insertion-sorted by one thread each, longer ones
-// (crowded cells of a clustered field) by the whole block with seg_sort, and
+// kSegThread particles are insertion-sorted by one thread each, up to
+// kSegWarp by one warp (warp_seg_sort in registers up to 32, seg_sort<true>
+// in shared memory beyond), longer ones (crowded cells of a clustered field)
+// by the whole block with seg_sort<false>, and
 // the run is written back with coalesced stores. A run longer than kFixCap is
 // listed in ovf for k_seg_fix_big, which does the same in global memory.
-constexpr int kFixCells = 512, kFixT = 256, kFixCap = 5120, kSegShort = 32;
+constexpr int kFixCells = 512, kFixT = 256, kFixCap = 5120, kSegThread = 8, kSegWarp = 512;
 
-// Sorts a[0, len) ascending with every thread of the block (a bitonic network
-// over the next power of two P >= len, in the form whose every compare-exchange
-// puts the smaller value at the lower index: the first step of each merge pairs
-// mirrored positions. Positions >= len act as +infinity and are never touched.)
-// All threads of the block must call it; it ends with a block barrier.
+// Sorts a[0, len) ascending with every thread of the block, or with the 32
+// lanes of the calling warp when WARP (a bitonic network over the next power of
+// two P >= len, in the form whose every compare-exchange puts the smaller value
+// at the lower index: the first step of each merge pairs mirrored positions.
+// Positions >= len act as +infinity and are never touched.) All threads of the
+// block (of the warp) must call it; it ends with a block (warp) barrier.
+template <bool WARP>
 __device__ void seg_sort(uint32_t* a, int len) {
     int P = 1;
     while (P < len) P <<= 1;
+    const int t0 = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int dt = WARP ? 32 : (int)blockDim.x;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+            for (int t = t0; t < (P >> 1); t += dt) {
                 int lo, hi;
                 if (j == (k >> 1)) {  // mirrored pairs within blocks of k
                     const int blk = t / j, o = t - blk * j;
@@ -290,7 +296,10 @@ __device__ void seg_sort(uint32_t* a, int len) {
                     }
                 }
             }
-            __syncthreads();
+            if (WARP)
+                __syncwarp();
+            else
+                __syncthreads();
         }
     }
 }
@@ -307,6 +316,23 @@ __device__ __forceinline__ void write_sorted(uint32_t i, int64_t j, const float*
     }
 }
 
+// Sorts a[0, len), len <= 32, ascending with the 32 lanes of a warp: a bitonic
+// network on one value per lane (UINT_MAX padding) through shuffles.
+__device__ __forceinline__ void warp_seg_sort(uint32_t* a, int len) {
+    const int lane = threadIdx.x & 31;
+    uint32_t v = lane < len ? a[lane] : 0xffffffffu;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = (lane & k) == 0, lo = (lane & j) == 0;
+            v = (lo == up) ? min(v, o) : max(v, o);
+        }
+    __syncwarp();
+    if (lane < len) a[lane] = v;
+}
+
 __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
                                                    int64_t ncell, const float* __restrict__ pos, int64_t np,
                                                    bool lattice, int N, FastDiv fN, float* __restrict__ sfrac,
@@ -314,12 +340,13 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
     __shared__ uint32_t buf[kFixCap];
     __shared__ uint32_t sst[kFixCells + 1];
     __shared__ uint32_t longs[kFixCells];
-    __shared__ int nlong;
+    __shared__ uint32_t meds[kFixCells];
+    __shared__ int nlong, nmed;
     const int tid = threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.x * kFixCells;
     const int nc = (int)min((int64_t)kFixCells, ncell - c0);
     for (int t = tid; t <= nc; t += kFixT) sst[t] = start[c0 + t];
-    if (tid == 0) nlong = 0;
+    if (tid == 0) nlong = nmed = 0;
     __syncthreads();
     const uint32_t s0 = sst[0];
     const int n = (int)(sst[nc] - s0);
@@ -332,8 +359,12 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
     for (int cl = tid; cl < nc; cl += kFixT) {
         const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
         if (e - a <= 1) continue;
-        if (e - a > kSegShort) {
+        if (e - a > kSegWarp) {
             longs[atomicAdd(&nlong, 1)] = (uint32_t)cl;
+            continue;
+        }
+        if (e - a > kSegThread) {  // one warp per segment, below
+            meds[atomicAdd(&nmed, 1)] = (uint32_t)cl;
             continue;
         }
         for (int p = a + 1; p < e; ++p) {
@@ -347,11 +378,20 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         }
     }
     __syncthreads();
+    for (int mi = tid >> 5; mi < nmed; mi += kFixT / 32) {
+        const int cl = (int)meds[mi];
+        const int a = (int)(sst[cl] - s0), len = (int)(sst[cl + 1] - s0) - a;
+        if (len <= 32)
+            warp_seg_sort(buf + a, len);
+        else
+            seg_sort<true>(buf + a, len);
+    }
+    __syncthreads();
     const int nl = nlong;
     for (int li = 0; li < nl; ++li) {
         const int cl = (int)longs[li];
         const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
-        seg_sort(buf + a, e - a);
+        seg_sort<false>(buf + a, e - a);
     }
     for (int j = tid; j < n; j += kFixT) write_sorted(buf[j], (int64_t)s0 + j, pos, np, lattice, N, fN, perm, sfrac);
 }
@@ -370,7 +410,7 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
         const int nc = (int)min((int64_t)kFixCells, ncell - c0);
         for (int cl = tid; cl < nc; cl += kFixT) {
             const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
-            if (e - a <= 1 || e - a > (uint32_t)kSegShort) continue;
+            if (e - a <= 1 || e - a > (uint32_t)kSegThread) continue;
             for (uint32_t p = a + 1; p < e; ++p) {
                 const uint32_t v = perm[p];
                 uint32_t q = p;
@@ -381,10 +421,18 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
                 perm[q] = v;
             }
         }
+        for (int cl = tid >> 5; cl < nc; cl += kFixT / 32) {
+            const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
+            if (e - a <= (uint32_t)kSegThread || e - a > (uint32_t)kSegWarp) continue;
+            if (e - a <= 32u)
+                warp_seg_sort(perm + a, (int)(e - a));
+            else
+                seg_sort<true>(perm + a, (int)(e - a));
+        }
         __syncthreads();
         for (int cl = 0; cl < nc; ++cl) {
             const uint32_t a = start[c0 + cl], e = start[c0 + cl + 1];
-            if (e - a > (uint32_t)kSegShort) seg_sort(perm + a, (int)(e - a));
+            if (e - a > (uint32_t)kSegWarp) seg_sort<false>(perm + a, (int)(e - a));
         }
         const uint32_t s0 = start[c0], s1 = start[c0 + nc];
         for (uint32_t j = s0 + tid; j < s1; j += kFixT) write_sorted(perm[j], j, pos, np, lattice, N, fN, perm, sfrac);

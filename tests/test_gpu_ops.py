@@ -65,6 +65,37 @@ def test_cell_sort_overfull_block():
     assert rel_l2(rho, opm.paint(f32(x), N, f32_wrap=True)) <= FIELD_TOL
 
 
+def test_cell_sort_segment_length_classes():
+    # cells of exactly the lengths where the segment sort changes method (8 | 9: one
+    # thread / one warp in registers, 32 | 33: one warp in shared memory, 512 | 513:
+    # the whole block), in a block of 512 cells staged in shared memory (keys 0-511)
+    # and in one past the stage's capacity of 5120 (keys 1024-1535, the global-memory path)
+    N = 32
+    rng = np.random.default_rng(5)
+    staged = [1, 2, 8, 9, 31, 32, 33, 100, 512, 513, 1200]
+    overfull = [2, 8, 9, 32, 33, 511, 512, 513, 4100]
+    parts = []
+    for k0, counts in ((0, staged), (1024, overfull)):
+        keys = k0 + rng.choice(512, size=len(counts), replace=False)
+        for key, k in zip(keys, counts):
+            corner = np.array([[key // (N * N)], [(key // N) % N], [key % N]], dtype=np.float64)
+            parts.append(corner + rng.uniform(0.02, 0.98, size=(3, k)))
+    parts.append(np.stack([rng.uniform(4.0, 32.0, 5000), rng.uniform(0.0, 32.0, 5000),
+                           rng.uniform(0.0, 32.0, 5000)]))
+    x = np.concatenate(parts, axis=1).astype(np.float32)
+    x = x[:, rng.permutation(x.shape[1])]
+    ctx, _ = context(N=N)
+    keys, perm, start = ctx.cell_sort(to_dev(x))
+    want_perm, want_start = opm.sort_by_cell(opm.cell_keys(x, N), N)
+    counts = np.diff(want_start.astype(np.int64))
+    assert all(k in counts[:512] for k in staged) and all(k in counts[1024:1536] for k in overfull)
+    assert counts[:512].sum() <= 5120 < counts[1024:1536].sum()
+    assert np.array_equal(to_np(perm).view(np.uint32), want_perm)
+    assert np.array_equal(to_np(start).view(np.uint32), want_start)
+    rho = to_np(ctx.paint(to_dev(x)))
+    assert rel_l2(rho, opm.paint(f32(x), N, f32_wrap=True)) <= FIELD_TOL
+
+
 @pytest.mark.parametrize("N", [16, 18])
 def test_cell_sort_many_crowded_cells(N):
     # several cells of 33 to about 1000 particles inside one staged block (the block-wide
