@@ -94,8 +94,6 @@ def algorithmic(name: str, N: int):
 # kernels on this workload (profiles/dram_traffic_256cubed.md); kernels changed
 # since their counters were taken have no entry. Valid for N = 256 only.
 TRAFFIC_256 = {
-    "paint3": 471.6e6 + 177.3e6,
-    "paint": 269.5e6 + 50.7e6,
     "x_conv_3": 68.6e6 + 140.9e6,
     "adj_readout_direct": 1076.5e6 + 373.5e6,
     "x_conv_in3": 203.0e6 + 43.6e6,

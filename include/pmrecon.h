@@ -185,7 +185,7 @@ int pmr_cell_sort(pmr_ctx* ctx, const float* x, int64_t np, uint32_t* keys, uint
 /* CIC density by a cell-sorted segmented gather (no float atomics; fixed
  * summation order): rho(c) = sum of mass * CIC weight over the particles of
  * the 8 bins c - o, each bin's corner sums taken over its particles in sorted
- * order and then combined along z, x and y in a fixed order, so repeated calls
+ * order and then combined along z, y and x in a fixed order, so repeated calls
  * give the same bits. mass: float32[np] or NULL for unit mass. rho: float32 mesh. */
 int pmr_paint(pmr_ctx* ctx, const float* x, int64_t np, const float* mass, float* rho);
 

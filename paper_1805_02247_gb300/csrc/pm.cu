@@ -448,32 +448,34 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
 // fixed order, so the result does not depend on scheduling.
 // A block owns X x Y x 32 cells (32 = the warp: lane l is the cell and bin
 // z0 + l); its bins are the rows (x, y) of the tile grown by one on the low x
-// and y sides. A warp takes one row at a time, each lane summing its bin's 8
-// corner terms over the bin's particles (the loads of a warp fall in one
-// contiguous run of the sorted arrays), then folds z in registers,
-// T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (the bins z0 - 1 of all
-// rows, lane 0's left neighbours, are summed first, one row per thread), so a
-// row leaves 4 values per cell in shared memory. Each cell then adds the 4 rows that hold it:
-// rho = (T_00(x, y) + T_10(x-1, y)) + (T_01(x, y-1) + T_11(x-1, y-1)).
+// and y sides. Warp w walks the rows of x = x0 - 1 + w along y, each lane
+// summing its bin's 8 corner terms over the bin's particles (the loads of a
+// warp fall in one contiguous run of the sorted arrays), and folds in
+// registers first z, T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (the
+// bins z0 - 1 of all rows, lane 0's left neighbours, are summed first, one row
+// per thread), then y, U_ox(x, y) = T_(ox,0)(x, y) + T_(ox,1)(x, y - 1) (the
+// previous row's T_(ox,1) carried in registers), so a row leaves 2 values per
+// cell in shared memory. Each cell then adds the 2 rows that hold it:
+// rho = U_0(x, y) + U_1(x - 1, y).
 // MMODE 0: unit masses; 1: mass[perm[j]]; 2: masses in sorted order, mass[m][j].
 template <int NM>
 struct WTile {
-    static constexpr int X = NM == 1 ? 8 : 4, Y = NM == 1 ? 8 : 4;
+    static constexpr int X = 8, Y = NM == 1 ? 16 : 8;
     static constexpr int RX = X + 1, RY = Y + 1, NR = RX * RY;
-    static constexpr int W = NM == 1 ? 9 : 8;  // warps per block (one mass: 9 rows each)
-    // T values [4][NM][NR][32], then the halo bins' S_(ox,oy,1) [4][NM][NR]
-    static constexpr size_t smem = sizeof(float) * 4 * NM * NR * 33;
+    static constexpr int W = RX;  // warps per block: one per x-row of bins
+    // U values [2 (ox)][NM][RX][Y][32], then the halo bins' S_(ox,oy,1) [4][NM][NR]
+    static constexpr size_t smem = sizeof(float) * (2 * NM * RX * Y * 32 + 4 * NM * NR);
 };
 
 template <int NM, int MMODE>
-__global__ void __launch_bounds__(WTile<NM>::W * 32, 4) k_paint_wtile(const uint32_t* __restrict__ start,
+__global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wtile(const uint32_t* __restrict__ start,
                                                                      const uint32_t* __restrict__ perm,
                                                                      const float* __restrict__ sfrac,
                                                                      const float* __restrict__ mass, int64_t np, int N,
                                                                      float scale, float offset, float* r0, float* r1,
                                                                      float* r2) {
     using WT = WTile<NM>;
-    extern __shared__ float Ts[];  // [4 (ox,oy)][NM][NR rows][32]
+    extern __shared__ float Us[];  // [2 (ox)][NM][RX][Y][32]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int z0 = blockIdx.x * 32, y0 = blockIdx.y * WT::Y, x0 = blockIdx.z * WT::X;
     const int z = z0 + lane;
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, 4) k_paint_wtile(const uint
     };
 
     // the halo bin z0 - 1 of every row (lane 0's left neighbour), one row per thread
-    float* Hs = Ts + 4 * NM * WT::NR * 32;  // [4 (ox,oy)][NM][NR]
+    float* Hs = Us + 2 * NM * WT::RX * WT::Y * 32;  // [4 (ox,oy)][NM][NR]
     for (int r = threadIdx.x; r < WT::NR; r += WT::W * 32) {
         const int64_t rb = row_base(r);
         float H[2][2][2][NM] = {};
@@ -526,18 +528,22 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, 4) k_paint_wtile(const uint
 #pragma unroll
             for (int m = 0; m < NM; ++m) Hs[(q * NM + m) * WT::NR + r] = H[q >> 1][q & 1][1][m];
     }
-    // rows w, w + W, ...; the next row's bin bounds are loaded before this row's particles
+    // warp w walks the bins of x-row w along y; the next row's bin bounds are
+    // loaded before this row's particles
+    const int bx = w;
     uint32_t s_n = 0, e_n = 0;
-    if (w < WT::NR && zin) {
-        const int64_t rb = row_base(w);
+    if (zin) {
+        const int64_t rb = row_base(bx * WT::RY);
         s_n = start[rb + z];
         e_n = start[rb + z + 1];
     }
-    __syncthreads();
-    for (int r = w; r < WT::NR; r += WT::W) {
+    __syncthreads();  // Hs
+    float C[2][NM];   // T_(ox,1) of the previous row
+    for (int by = 0; by < WT::RY; ++by) {
+        const int r = bx * WT::RY + by;
         const uint32_t s = s_n, e = e_n;
-        if (r + WT::W < WT::NR && zin) {
-            const int64_t rb = row_base(r + WT::W);
+        if (by + 1 < WT::RY && zin) {
+            const int64_t rb = row_base(r + 1);
             s_n = start[rb + z];
             e_n = start[rb + z + 1];
         }
@@ -546,29 +552,30 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, 4) k_paint_wtile(const uint
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
 #pragma unroll
-            for (int oy = 0; oy < 2; ++oy)
+            for (int m = 0; m < NM; ++m) {
+                float T[2];
 #pragma unroll
-                for (int m = 0; m < NM; ++m) {
+                for (int oy = 0; oy < 2; ++oy) {
                     float left = __shfl_up_sync(0xffffffffu, S[ox][oy][1][m], 1);
                     if (lane == 0) left = Hs[((ox * 2 + oy) * NM + m) * WT::NR + r];
-                    Ts[(((ox * 2 + oy) * NM + m) * WT::NR + r) * 32 + lane] = S[ox][oy][0][m] + left;
+                    T[oy] = S[ox][oy][0][m] + left;
                 }
+                if (by > 0) Us[(((ox * NM + m) * WT::RX + bx) * WT::Y + by - 1) * 32 + lane] = T[0] + C[ox][m];
+                C[ox][m] = T[1];
+            }
     }
     __syncthreads();
     for (int q = w; q < WT::X * WT::Y; q += WT::W) {
         const int lx = q / WT::Y, ly = q - lx * WT::Y;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= N || gy >= N || !zin) continue;
-        const int r11 = (lx + 1) * WT::RY + (ly + 1);  // bin (x, y)
         const int64_t c = ((int64_t)gx * N + gy) * N + z;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            const float t00 = Ts[((0 * NM + m) * WT::NR + r11) * 32 + lane];
-            const float t10 = Ts[((2 * NM + m) * WT::NR + r11 - WT::RY) * 32 + lane];
-            const float t01 = Ts[((1 * NM + m) * WT::NR + r11 - 1) * 32 + lane];
-            const float t11 = Ts[((3 * NM + m) * WT::NR + r11 - WT::RY - 1) * 32 + lane];
+            const float u0 = Us[(((0 * NM + m) * WT::RX + lx + 1) * WT::Y + ly) * 32 + lane];
+            const float u1 = Us[(((1 * NM + m) * WT::RX + lx) * WT::Y + ly) * 32 + lane];
             float* out = m == 0 ? r0 : (m == 1 ? r1 : r2);
-            out[c] = ((t00 + t10) + (t01 + t11)) * scale + offset;
+            out[c] = (u0 + u1) * scale + offset;
         }
     }
 }
@@ -803,6 +810,10 @@ template <int NM, int MMODE>
 int launch_paint_wtile(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
                        int64_t np, float scale, float offset, float* const* rho) {
     using WT = WTile<NM>;
+    // the shared-memory limit, raised once per process (the paint runs on one device)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_paint_wtile<NM, MMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WT::smem);
+    PMR_TRY(check_cuda(c, attr, "paint smem attr"));
     const int N = c->N;
     const dim3 grid((N + 31) / 32, (N + WT::Y - 1) / WT::Y, (N + WT::X - 1) / WT::X);
     k_paint_wtile<NM, MMODE><<<grid, WT::W * 32, WT::smem, c->stream>>>(
