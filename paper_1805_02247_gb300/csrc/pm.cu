@@ -452,8 +452,8 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix_big(const uint32_t* __restric
 // summing its bin's 8 corner terms over the bin's particles (the loads of a
 // warp fall in one contiguous run of the sorted arrays), and folds in
 // registers first z, T_(ox,oy)(z) = S_(ox,oy,0)(z) + S_(ox,oy,1)(z - 1) (the
-// bins z0 - 1 of all rows, lane 0's left neighbours, are summed first, one row
-// per thread), then y, U_ox(x, y) = T_(ox,0)(x, y) + T_(ox,1)(x, y - 1) (the
+// bins z0 - 1 of the warp's rows, lane 0's left neighbours, are summed first,
+// one row per lane), then y, U_ox(x, y) = T_(ox,0)(x, y) + T_(ox,1)(x, y - 1) (the
 // previous row's T_(ox,1) carried in registers), so a row leaves 2 values per
 // cell in shared memory. Each cell then adds the 2 rows that hold it:
 // rho = U_0(x, y) + U_1(x - 1, y).
@@ -516,18 +516,6 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
         }
     };
 
-    // the halo bin z0 - 1 of every row (lane 0's left neighbour), one row per thread
-    float* Hs = Us + 2 * NM * WT::RX * WT::Y * 32;  // [4 (ox,oy)][NM][NR]
-    for (int r = threadIdx.x; r < WT::NR; r += WT::W * 32) {
-        const int64_t rb = row_base(r);
-        float H[2][2][2][NM] = {};
-        const uint32_t hs = start[rb + zh], he = start[rb + zh + 1];
-        for (uint32_t j = hs; j < he; ++j) acc(j, H, true);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int m = 0; m < NM; ++m) Hs[(q * NM + m) * WT::NR + r] = H[q >> 1][q & 1][1][m];
-    }
     // warp w walks the bins of x-row w along y; the next row's bin bounds are
     // loaded before this row's particles
     const int bx = w;
@@ -537,7 +525,22 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
         s_n = start[rb + z];
         e_n = start[rb + z + 1];
     }
-    __syncthreads();  // Hs
+    // first the halo bin z0 - 1 of each of the warp's rows (lane 0's left
+    // neighbour there), one row per lane; only this warp reads them
+    float* Hs = Us + 2 * NM * WT::RX * WT::Y * 32;  // [4 (ox,oy)][NM][NR]
+    static_assert(WTile<NM>::RY <= 32, "one halo row per lane");
+    if (lane < WT::RY) {
+        const int r = bx * WT::RY + lane;
+        const int64_t rb = row_base(r);
+        float H[2][2][2][NM] = {};
+        const uint32_t hs = start[rb + zh], he = start[rb + zh + 1];
+        for (uint32_t j = hs; j < he; ++j) acc(j, H, true);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) Hs[(q * NM + m) * WT::NR + r] = H[q >> 1][q & 1][1][m];
+    }
+    __syncwarp();
     float C[2][NM];   // T_(ox,1) of the previous row
     for (int by = 0; by < WT::RY; ++by) {
         const int r = bx * WT::RY + by;
