@@ -393,7 +393,26 @@ __global__ void __launch_bounds__(kFixT) k_seg_fix(const uint32_t* __restrict__ 
         const int a = (int)(sst[cl] - s0), e = (int)(sst[cl + 1] - s0);
         seg_sort<false>(buf + a, e - a);
     }
-    for (int j = tid; j < n; j += kFixT) write_sorted(buf[j], (int64_t)s0 + j, pos, np, lattice, N, fN, perm, sfrac);
+    for (int j = tid; j < n; j += 2 * kFixT) {
+        const int j2 = j + kFixT;
+        const uint32_t i1 = buf[j], i2 = buf[j2 < n ? j2 : j];
+        const Cell c1 = cell_of(pos, np, i1, lattice, N, fN);
+        const Cell c2 = cell_of(pos, np, i2, lattice, N, fN);
+        perm[s0 + j] = i1;
+        if (sfrac) {
+            sfrac[s0 + j] = c1.d[0];
+            sfrac[np + s0 + j] = c1.d[1];
+            sfrac[2 * np + s0 + j] = c1.d[2];
+        }
+        if (j2 < n) {
+            perm[s0 + j2] = i2;
+            if (sfrac) {
+                sfrac[s0 + j2] = c2.d[0];
+                sfrac[np + s0 + j2] = c2.d[1];
+                sfrac[2 * np + s0 + j2] = c2.d[2];
+            }
+        }
+    }
 }
 
 // The runs k_seg_fix could not stage: the same steps on global memory, one
