@@ -91,15 +91,23 @@ def algorithmic(name: str, N: int):
 
 
 # DRAM bytes (read + write) per launch from one-pass ncu counters of the current
-# kernels on this workload (profiles/dram_traffic_256cubed.md); kernels changed
-# since their counters were taken have no entry. Valid for N = 256 only.
+# kernels on this workload, one evaluation's launches averaged
+# (profiles/dram_traffic_256cubed.md); kernels changed since their counters
+# were taken have no entry. Valid for N = 256 only.
 TRAFFIC_256 = {
-    "x_conv_3": 68.6e6 + 140.9e6,
-    "adj_readout_direct": 1076.5e6 + 373.5e6,
-    "x_conv_in3": 203.0e6 + 43.6e6,
+    "paint3": 472.8e6 + 174.1e6,
+    "paint": 271.1e6 + 48.5e6,
+    "x_conv_3": 68.6e6 + 141.2e6,
+    "adj_readout_direct": 1035.9e6 + 373.0e6,  # mean of the 9 + 1 launches of its two forms
+    "x_conv_in3": 203.0e6 + 43.5e6,
     "col_pass": 67.7e6 + 8.9e6,
-    "z_c2r": 67.7e6 + 14.3e6,
-    "z_r2c": 67.1e6 + 15.3e6,
+    "z_c2r": 67.7e6 + 17.1e6,
+    "z_r2c": 67.1e6 + 15.2e6,
+    "kick_drift": 605.8e6 + 360.3e6,
+    "seg_fix": 336.5e6 + 223.5e6,
+    "keys": 268.6e6 + 152.1e6,
+    "permute3": 269.3e6 + 167.0e6,
+    "scatter": 201.8e6 + 43.6e6,
 }
 
 
