@@ -309,7 +309,7 @@ def extras(dev, steps):
         ctx.close()
         del ctx, s, data, s_true
         torch.cuda.empty_cache()
-    # L-BFGS iterations (Sec. 4.2): each is one or more loss+gradient evaluations
+    # L-BFGS iterations (Sec. 5.2): each is one or more loss+gradient evaluations
     ctx, s, data, s_true = _setup_job(dev)
     # the same evaluation at the truth's full-power linear field: clustered
     # positions, crowded cells in the sort and the paints (late iterations)
@@ -330,7 +330,7 @@ def extras(dev, steps):
     evals = rep.get("prior", (0, 0.0))[0] / iters  # one prior reduction per loss evaluation
     out["recon_step"] = {"ms_per_iteration": dt * 1e3, "loss_evals_per_iteration": evals,
                          "note": "wall clock, host reads the loss after each line-search trial"}
-    # two-point statistics of two 256^3 meshes (Sec. 3.3)
+    # two-point statistics of two 256^3 meshes (Sec. 4.3)
     delta = ctx.pm_forward(s_true)
     ctx.power_spectra(delta, delta)
     torch.cuda.synchronize()

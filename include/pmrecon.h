@@ -3,14 +3,14 @@
  * Modi, Feng & Seljak (2018), "Cosmological reconstruction from galaxy light:
  * neural network based light-matter connection".
  *
- * One call of loss_and_grad() evaluates the loss of Eq. (loss) (Sec. 4.1) at
+ * One call of loss_and_grad() evaluates the loss of Eq. (loss) (Sec. 5.1) at
  * the linear modes s(k) and its gradient w.r.t. s(k): Zel'dovich initial
  * conditions at a0, nsteps particle-mesh kick/drift steps (Sec. 3), the
  * 27-point, 3-field, 81-50-30-1 network of Sec. 2 on the final density, the
  * smoothed displaced-log-normal residual (Eq. probnoise) with the annealed
- * residual smoothing of Sec. 4.2, the Gaussian prior (Eq. priorpdf), and the
+ * residual smoothing of Sec. 5.2, the Gaussian prior (Eq. priorpdf), and the
  * hand-written adjoint of all of it. recon_step() is one L-BFGS iteration
- * (Sec. 4.2) around it.
+ * (Sec. 5.2) around it.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -21,7 +21,7 @@
  * - Fourier arrays ("c64") are interleaved complex float32 in the half layout
  *   [N][N][N/2+1] (the real-to-complex layout), with the field defined as
  *   f(x) = N^-3 sum_k s(k) exp(i k.x). Real and imaginary parts of every entry
- *   are independent real variables (Sec. 4.1); gradients are w.r.t. them.
+ *   are independent real variables (Sec. 5.1); gradients are w.r.t. them.
  * - Particle arrays are float32 SoA [3][np] in grid units (cell = L/N Mpc/h);
  *   the j-th component of particle i is at p[j*np + i].
  * - All work is enqueued on the context's stream and is asynchronous unless a
@@ -58,13 +58,13 @@ typedef struct pmr_config {
     double sigma8;      /* linear amplitude of the BBKS spectrum */
     double gamma_bbks;  /* BBKS shape parameter */
     double R_feat[3];   /* Gaussian scales of the three network input fields, Mpc/h (Sec. 2.2) */
-    double R_M;         /* smoothing of model and data mass inside the log, Mpc/h (Sec. 3.2: 3) */
-    double sigma_N2;    /* noise variance of Eq. (loss) (Sec. 4.3: 0.25) */
+    double R_M;         /* smoothing of model and data mass inside the log, Mpc/h (Sec. 4.2: 3) */
+    double sigma_N2;    /* noise variance of Eq. (loss) (Sec. 5.3: 0.25) */
     double mu_N;        /* offset of Eq. (loss) */
-    double f_eff;       /* effective-points factor of Eq. (loss) (Sec. 4.1: 1) */
+    double f_eff;       /* effective-points factor of Eq. (loss) (Sec. 5.1: 1) */
     double M_scale;     /* halo mass per unit softplus output, M_sun/h */
     int lbfgs_m;        /* L-BFGS memory (correction pairs), 1..64 */
-    double lbfgs_tol;   /* relative loss decrease that counts as converged (Sec. 4.3: 1e-3) */
+    double lbfgs_tol;   /* relative loss decrease that counts as converged (Sec. 5.3: 1e-3) */
     int nn_path;        /* network arithmetic: 0 = tensor cores (tcgen05), each operand split
                            into two TF32 parts, float32 accuracy (default); 1 = tensor cores,
                            plain TF32 (~1e-3 relative); 2 = float32 CUDA cores; 3 = tensor
@@ -79,7 +79,7 @@ typedef struct pmr_config {
                            potential (lap phi = delta). Needs 12 more float32 meshes. */
 } pmr_config;
 
-/* Per-stage annealing parameters of Sec. 4.2. */
+/* Per-stage annealing parameters of Sec. 5.2. */
 typedef struct pmr_anneal {
     double R_sm;       /* Gaussian smoothing of the residual, Mpc/h; 0 = none */
     double M0;         /* nuisance mass added inside the log, M_sun/h (Eq. var) */
@@ -129,7 +129,7 @@ const char* pmr_last_error(const pmr_ctx* ctx);
 /* Linear modes from white noise: s(k) = amplitude * sqrt(P(k) N^6 / L^3 / N^3)
  * * rfft(white)(k), s(0) = 0, so <|s|^2> = amplitude^2 P(k) N^6/L^3 (the
  * Gaussian field of Eq. priorpdf; amplitude^2 = 0.1 gives the 10%-power
- * starting point of Sec. 4.3). white: float32 mesh. s_k: c64 half array. */
+ * starting point of Sec. 5.3). white: float32 mesh. s_k: c64 half array. */
 int pmr_linear_field(pmr_ctx* ctx, const float* white, double amplitude, void* s_k);
 
 /* Forward PM model (Sec. 3): s(k) -> final overdensity delta = rho/rho_bar - 1
@@ -137,7 +137,7 @@ int pmr_linear_field(pmr_ctx* ctx, const float* white, double amplitude, void* s
  * pm_adjoint(). s_k: c64 half array; delta_out: float32 mesh. */
 int pm_forward(pmr_ctx* ctx, const void* s_k, float* delta_out);
 
-/* Adjoint of the last pm_forward() on this context (Sec. 4.2, PM derivatives
+/* Adjoint of the last pm_forward() on this context (Sec. 5.2, PM derivatives
  * written by hand): grad_s_k = (d delta/d s)^T grad_delta. Force fields are
  * recomputed from the stored positions. Returns PMR_ESTATE without a forward. */
 int pm_adjoint(pmr_ctx* ctx, const float* grad_delta, void* grad_s_k);
@@ -152,7 +152,7 @@ int nn_halo_map(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, float* m
 int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, const float* grad_mass,
                         float* grad_delta);
 
-/* Loss of Eq. (loss) at s(k) and its gradient (Sec. 4.1-4.2).
+/* Loss of Eq. (loss) at s(k) and its gradient (Sec. 5.1-5.2).
  * data_mass: float32 mesh of the observed halo mass M^data (unsmoothed).
  * loss_out: HOST double[3] = {total, prior, residual}; the call synchronises
  *   the stream to return it. May be NULL (then nothing is read back).
@@ -160,7 +160,7 @@ int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, 
 int loss_and_grad(pmr_ctx* ctx, const void* s_k, const float* data_mass, const pmr_anneal* an,
                   double* loss_out, void* grad_s_k);
 
-/* One L-BFGS iteration (Sec. 4.2) on s(k) in place: two-loop direction from the
+/* One L-BFGS iteration (Sec. 5.2) on s(k) in place: two-loop direction from the
  * context's history (float64 on the device), Armijo backtracking (step 1,
  * halved up to 20 times, c1 = 1e-4), history update. The initial inverse
  * Hessian is gamma D with D = P~(k)/w_k, the Gaussian prior's exact inverse
@@ -168,7 +168,7 @@ int loss_and_grad(pmr_ctx* ctx, const void* s_k, const float* data_mass, const p
  * pmr_lbfgs_reset() (or after any annealing parameter changes) evaluates the
  * gradient at s first and searches along -D g.
  * loss_out: HOST double[3] of the accepted point. converged: HOST int, set to 1
- * when (L_old - L_new) < lbfgs_tol * |L_old| (Sec. 4.3 stop rule). Synchronises. */
+ * when (L_old - L_new) < lbfgs_tol * |L_old| (Sec. 5.3 stop rule). Synchronises. */
 int recon_step(pmr_ctx* ctx, void* s_k, const float* data_mass, const pmr_anneal* an,
                double* loss_out, int* converged);
 int pmr_lbfgs_reset(pmr_ctx* ctx);
@@ -249,12 +249,12 @@ int pmr_lpt_ics_adjoint(pmr_ctx* ctx, const void* s_k, const float* lam_x, const
 /* Growth factors the stepping uses (float64, host): D(a), G_p(a), G_f(a). */
 int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* Gf);
 
-/* L-BFGS two-loop direction d = -H g (Sec. 4.2) for k pairs, float64 device
+/* L-BFGS two-loop direction d = -H g (Sec. 5.2) for k pairs, float64 device
  * vectors of length n: S and Y are [k][n], oldest first. */
 int pmr_lbfgs_direction(pmr_ctx* ctx, const double* g, const double* S, const double* Y, int k,
                         int64_t n, double* d);
 
-/* Two-point statistics of Sec. 3.3: binned auto and cross power spectra of two
+/* Two-point statistics of Sec. 4.3: binned auto and cross power spectra of two
  * float32 meshes a (e.g. the data, "h") and b (the model, "N"), from which the
  * host forms r_c = P_ab / sqrt(P_aa P_bb), s = P_aa (1 - r_c^2) and
  * TF = sqrt(P_bb / P_aa). Shell i (i < N/2) holds the modes with integer

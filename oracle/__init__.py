@@ -18,8 +18,8 @@ cosmo   background expansion, linear growth D(a), BBKS power spectrum, sigma8
 pm      mesh conventions, linear field, Zel'dovich ICs, CIC paint/readout,
         PM force, kick-drift-kick stepping and the hand-written adjoint
 nn      the 81-50-30-1 network of Sec. 2.1 on the 27-point stencil of Sec. 2.2
-loss    the loss of Eq. (loss) (Sec. 4.1) and its gradient w.r.t. s(k)
-lbfgs   the L-BFGS step of Sec. 4.2 (two-loop recursion, Armijo backtracking)
+loss    the loss of Eq. (loss) (Sec. 5.1) and its gradient w.r.t. s(k)
+lbfgs   the L-BFGS step of Sec. 5.2 (two-loop recursion, Armijo backtracking)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 (closed forms, invariants, brute force, finite differences) except the whole

@@ -1,7 +1,7 @@
-"""L-BFGS step of Sec. 4.2 (FP64, numpy).
+"""L-BFGS step of Sec. 5.2 (FP64, numpy).
 
 The paper names L-BFGS and its stop rule (the loss per degree of freedom stops
-decreasing by 0.1% between iterations, Sec. 4.3) but not its memory, initial
+decreasing by 0.1% between iterations, Sec. 5.3) but not its memory, initial
 Hessian or line search. Readings:
 * memory m = 10 correction pairs; a pair is stored only if s^T y > 1e-10 |s| |y|;
 * initial inverse Hessian: for the reconstruction, a diagonal D = P~(k) / w_k,
@@ -17,7 +17,7 @@ Hessian or line search. Readings:
   L(s + t d) <= L(s) + c1 t g.d with c1 = 1e-4; failure is an error;
 * converged when (L_old - L_new) / |L_old| < tol (tol = 1e-3).
 Inner products are the plain real inner product over the half-array entries
-(real and imaginary parts are independent variables, Sec. 4.1).
+(real and imaginary parts are independent variables, Sec. 5.1).
 """
 from __future__ import annotations
 

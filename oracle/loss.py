@@ -1,4 +1,4 @@
-"""The reconstruction loss of Sec. 4.1 and its gradient w.r.t. s(k) (FP64).
+"""The reconstruction loss of Sec. 5.1 and its gradient w.r.t. s(k) (FP64).
 
 Eq. (loss): L(s) = 1/2 s S^-1 s^dagger
                  + f_eff sum_i ((mu_N + log(M^NN_R,i + M0) - log(M^data_R,i + M0)) / (2 sigma_N))^2
@@ -6,10 +6,10 @@ Eq. (loss): L(s) = 1/2 s S^-1 s^dagger
 Readings (the paper is silent or ambiguous on these):
 * log is the natural logarithm.
 * The residual square is taken literally as printed, r^2 / (4 sigma_N^2);
-  Sec. 4.3 fixes sigma_N^2 = 0.25, f_eff = 1 (Sec. 4.1).
+  Sec. 5.3 fixes sigma_N^2 = 0.25, f_eff = 1 (Sec. 5.1).
 * M_R is the model (or data) mass field smoothed with a Gaussian of R_M =
-  3 Mpc/h (Sec. 3.2 smooths both fields at 3 Mpc/h before comparing).
-* The annealed residual smoothing of Sec. 4.2 is a Gaussian of R_sm applied to
+  3 Mpc/h (Sec. 4.2 smooths both fields at 3 Mpc/h before comparing).
+* The annealed residual smoothing of Sec. 5.2 is a Gaussian of R_sm applied to
   the residual field before squaring; R_sm = 0 means none.
 * mu_N defaults to 0 (the mass-dependent offsets of Fig. noise are not printed).
 * The three network input fields are the final overdensity smoothed with
@@ -41,7 +41,7 @@ class LossSetup:
 class Anneal:
     R_sm: float  # Mpc/h
     M0: float  # M_sun/h
-    a: float = 3.0  # logistic sharpness of the two-network head (annealed 1, 2, 3 in Sec. 4.2)
+    a: float = 3.0  # logistic sharpness of the two-network head (annealed 1, 2, 3 in Sec. 5.2)
 
 
 def _head_forward(f, weights, ls: LossSetup, a: float):

@@ -1,7 +1,7 @@
 """Particle-mesh forward model and its hand-written adjoint (FP64, numpy).
 
 Follows Sec. 3 (FastPM forward model: LPT initial conditions at a = 0.1, a few
-PM steps) and Sec. 4.2 (gradients of the PM evolution, written here by hand).
+PM steps) and Sec. 5.2 (gradients of the PM evolution, written here by hand).
 Where the paper is silent the readings below are used; each is a stated
 convention, identical on the CUDA side.
 
@@ -12,7 +12,7 @@ Conventions
   is ``irfftn(s)`` (1/N^3 on the inverse). Grid-unit wavenumber k = 2 pi n / N,
   n in (-N/2, N/2]. The linear field has <|s_k|^2> = P(k) N^6 / L^3.
 * The half-array entries (real and imaginary parts) are the independent real
-  variables of the problem (Sec. 4.1 treats real and imaginary parts as
+  variables of the problem (Sec. 5.1 treats real and imaginary parts as
   independent modes). Gradients are w.r.t. those entries; the prior weights a
   mode by w_k = 2 for 0 < k_z < N/2 and 1 on the k_z = 0 and k_z = N/2 planes
   so that it equals the full-grid sum for a Hermitian field.

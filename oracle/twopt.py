@@ -1,4 +1,4 @@
-"""Two-point statistics of Sec. 3.3 (FP64, numpy).
+"""Two-point statistics of Sec. 4.3 (FP64, numpy).
 
 Cross-correlation r_c = P_hN / sqrt(P_hh P_NN), stochasticity s = P_hh (1 - r_c^2)
 and transfer function TF = sqrt(P_NN / P_hh), with P_ab(k) the (cross) power
@@ -54,7 +54,7 @@ def shell_k(N: int, L: float) -> np.ndarray:
 
 
 def statistics(P_hh, P_NN, P_hN):
-    """(r_c, s, TF) of Sec. 3.3 from binned spectra (h: truth/data, N: model)."""
+    """(r_c, s, TF) of Sec. 4.3 from binned spectra (h: truth/data, N: model)."""
     with np.errstate(divide="ignore", invalid="ignore"):
         rc = P_hN / np.sqrt(P_hh * P_NN)
         s = P_hh * (1.0 - rc**2)

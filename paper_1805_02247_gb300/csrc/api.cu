@@ -1,6 +1,6 @@
 // C ABI of the reconstruction library: context lifetime, validation, the
 // workspace layout, and the host orchestration of the forward model, its
-// adjoint, the loss and the L-BFGS step (Sec. 3, 4.1, 4.2).
+// adjoint, the loss and the L-BFGS step (Sec. 3, 5.1, 5.2).
 #include <cmath>
 #include <cstring>
 

@@ -1,7 +1,7 @@
-// L-BFGS (Sec. 4.2) on the device in float64: deterministic dot products and
+// L-BFGS (Sec. 5.2) on the device in float64: deterministic dot products and
 // the two-loop recursion with every scalar kept on the device, so a direction
 // costs no host round trip. Vectors are the half-array modes viewed as 2*NH
-// reals (real and imaginary parts are independent variables, Sec. 4.1).
+// reals (real and imaginary parts are independent variables, Sec. 5.1).
 #include "common.cuh"
 
 namespace pmr {

@@ -1,6 +1,6 @@
-// Loss of Eq. (loss) (Sec. 4.1): the Gaussian prior of Eq. (priorpdf) on the
+// Loss of Eq. (loss) (Sec. 5.1): the Gaussian prior of Eq. (priorpdf) on the
 // half-array modes and the smoothed displaced-log-normal residual of
-// Eq. (probnoise), with the annealed residual smoothing of Sec. 4.2, plus the
+// Eq. (probnoise), with the annealed residual smoothing of Sec. 5.2, plus the
 // elementwise parts of their gradients. Sums are float64 and deterministic:
 // a fixed grid accumulates per-block partials that one block adds in order.
 #include <cmath>

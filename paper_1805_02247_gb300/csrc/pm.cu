@@ -2,7 +2,7 @@
 // paint as a cell-sorted segmented gather (no float atomics, fixed summation
 // order), CIC readout and its position gradient, the fused readout + kick +
 // drift step, Zel'dovich initial conditions, and the adjoints (Sec. 3 forward
-// model; Sec. 4.2 gradients written by hand).
+// model; Sec. 5.2 gradients written by hand).
 //
 // Particles carry a float32 displacement from their Lagrangian lattice point q
 // (x = q + disp), so the cell index q + floor(disp) and the CIC fraction

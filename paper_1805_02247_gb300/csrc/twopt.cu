@@ -1,4 +1,4 @@
-// Two-point statistics of Sec. 3.3 on the GPU: binned auto and cross power
+// Two-point statistics of Sec. 4.3 on the GPU: binned auto and cross power
 // spectra of two mesh fields, from which r_c = P_hN / sqrt(P_hh P_NN),
 // s = P_hh (1 - r_c^2) and TF = sqrt(P_NN / P_hh) follow.
 //

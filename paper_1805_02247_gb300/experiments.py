@@ -1,4 +1,4 @@
-"""Reconstruction runs of the kind the paper reports (Sec. 4.3), on synthetic data.
+"""Reconstruction runs of the kind the paper reports (Sec. 5.3), on synthetic data.
 
   python -m paper_1805_02247_gb300.experiments recon [--N 128] [--iters 100] [--out run.json]
   python -m paper_1805_02247_gb300.experiments precision [--N 256] [--iters 200] [--out run.json]
@@ -7,9 +7,9 @@
 annealed L-BFGS reconstruction on the GPU from a start at 10% of the fiducial
 power. It reports the loss history and, per |k| shell, the cross-correlation,
 transfer function and stochasticity of the reconstructed linear field and of
-its final density against the truth (Sec. 3.3).
+its final density against the truth (Sec. 4.3).
 
-Data (Sec. 3 and 4.3, with the paper's FOF catalogue replaced by the model):
+Data (Sec. 3 and 5.3, with the paper's FOF catalogue replaced by the model):
 the network's halo-mass field of the truth, times log-normal scatter
 exp(0.3 g), keeping only the ceil(8 n L^3) most massive voxels (a halo number
 density n spread over its 8 CIC cells) and zeroing the rest, as the paper's

@@ -221,7 +221,7 @@ class Context:
         return tuple(host), bool(conv.value)
 
     def power_spectra(self, a: torch.Tensor, b: torch.Tensor):
-        """(counts, P_aa, P_bb, P_ab) per |k| shell as float64 host tensors (Sec. 3.3)."""
+        """(counts, P_aa, P_bb, P_ab) per |k| shell as float64 host tensors (Sec. 4.3)."""
         nb = self.N // 2
         out = (ctypes.c_double * (4 * nb))()
         self._check(self._lib.pmr_power_spectra(self._h, _ptr(a), _ptr(b), out))

@@ -167,7 +167,7 @@ def gpu_runner(device, use_graphs=True, keep_result=False):
                 s = ctx.linear_field(torch.from_numpy(synth.white_noise(N, spec.data_seed + 1000)).to(device),
                                      math.sqrt(0.1))
                 cell = spec.L / N
-                # the first M0 of the paper's schedule (Sec. 4.3): large enough that the
+                # the first M0 of the paper's schedule (Sec. 5.3): large enough that the
                 # smoothed masses stay above -M0 on coarse meshes
                 stages = spec.stages or [anneal.Stage(2 * cell, 1e12), anneal.Stage(1 * cell, 1e12)]
                 hist = anneal.reconstruct(ctx, s, data, stages, max_iter=spec.max_iter)

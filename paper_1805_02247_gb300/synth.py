@@ -6,7 +6,7 @@ Every stochastic quantity the method needs is drawn here once, on the host,
 with numpy's PCG64, and handed to both implementations as plain arrays, so
 parity never depends on two random-number generators agreeing.
 
-Workload shapes follow the paper's setting (Sec. 3 and Sec. 4.3): a periodic
+Workload shapes follow the paper's setting (Sec. 3 and Sec. 5.3): a periodic
 cube of side L Mpc/h, an N^3 mesh with one particle per cell, a linear field
 drawn from Gaussian white noise, Xavier-initialised weights for the
 81-50-30-1 network of Sec. 2.1, and per-voxel log-normal scatter for the data.

@@ -160,7 +160,7 @@ def test_network_adjoint_sparse_full(job):
 
 
 def _start_point(ctx):
-    # 10% of the fiducial power (the starting point of Sec. 4.3)
+    # 10% of the fiducial power (the starting point of Sec. 5.3)
     return ctx.linear_field(to_dev(synth.white_noise(N, 111)), float(np.sqrt(0.1)))
 
 

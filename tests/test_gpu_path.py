@@ -232,7 +232,7 @@ def test_recon_step_follows_oracle_lbfgs(nn_path, later_loss_tol):
 
 
 def test_annealed_reconstruction_follows_oracle():
-    # Sec. 4.2 annealing: residual smoothing 2 -> 1 -> 0 cells, then M0 1e9 -> 1e8,
+    # Sec. 5.2 annealing: residual smoothing 2 -> 1 -> 0 cells, then M0 1e9 -> 1e8,
     # one L-BFGS iteration per stage, so every stage starts afresh from the last
     # iterate (memory reset, new loss). A longer stay in one stage is not compared
     # point by point: after a short backtracked first step the curvature pair
@@ -262,7 +262,7 @@ def test_annealed_reconstruction_follows_oracle():
 
 
 def test_two_network_annealing_over_sharpness_follows_oracle():
-    # Sec. 4.2: the logistic sharpness a is annealed between stages (1 -> 2),
+    # Sec. 5.2: the logistic sharpness a is annealed between stages (1 -> 2),
     # one iteration per stage. The two-network loss is steeper: under 1e-6
     # relative gradient noise the oracle's second-stage loss moves by 6.4e-5
     # (7.4e-5 under 1e-5), so it is held to 5e-4; the first to the loss tolerance.

@@ -124,7 +124,7 @@ def test_two_net_loss_gradient_by_finite_differences():
     N = 8
     pms = pm.PMSetup(N=N, L=50.0, nsteps=2)
     ls = loss.LossSetup(head="two_net")
-    # M0 = 1e11 (second stage of Sec. 4.3) dominates the ringing of the sub-cell
+    # M0 = 1e11 (second stage of Sec. 5.3) dominates the ringing of the sub-cell
     # R_M smoothing of the spiky logistic-head mass field at this coarse mesh
     an = loss.Anneal(R_sm=3.0, M0=1e11, a=2.0)
     w = np.concatenate([synth.xavier_weights(1), synth.mass_net_weights(3)])
