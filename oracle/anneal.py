@@ -1,4 +1,4 @@
-"""Annealed reconstruction (Sec. 4.2-4.3) on the FP64 oracle: stages of
+"""Annealed reconstruction (Sec. 5.2-5.3) on the FP64 oracle: stages of
 (R_sm, M0[, a]), each iterating the oracle L-BFGS step until the loss stops
 decreasing by tol (relative) or max_iter iterations pass."""
 from __future__ import annotations

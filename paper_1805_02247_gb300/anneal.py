@@ -1,4 +1,4 @@
-"""Annealed reconstruction driver (Sec. 4.2-4.3), sequencing recon_step().
+"""Annealed reconstruction driver (Sec. 5.2-5.3), sequencing recon_step().
 
 The paper anneals three knobs of the loss while L-BFGS runs: the Gaussian
 smoothing of the residual (N_sm = 4, 2, 1, 0.5, 0 cells), the nuisance mass M0
@@ -23,7 +23,7 @@ class Stage:
 
 
 def paper_schedule(cell: float) -> list[Stage]:
-    """The schedule of Sec. 4.3 for a single-network head (no sharpness knob):
+    """The schedule of Sec. 5.3 for a single-network head (no sharpness knob):
     M0 = 1e12 with N_sm = 4, 2, 1, 0.5, 0 cells, then M0 = 1e11 with N_sm = 1, 0.5, 0."""
     stages = [Stage(n * cell, 1e12) for n in (4, 2, 1, 0.5, 0)]
     stages += [Stage(n * cell, 1e11) for n in (1, 0.5, 0)]
@@ -31,12 +31,10 @@ def paper_schedule(cell: float) -> list[Stage]:
 
 
 def two_network_schedule(cell: float) -> list[Stage]:
-    """Sec. 4.3 with the two-network head: the logistic sharpness steps through
-    a = 1, 2, 3; at each a the smoothing runs N_sm = 4, 2, 1, 0.5, 0 cells with
-    M0 = 1e12, and the last a finishes with M0 = 1e11 at N_sm = 1, 0.5, 0."""
-    stages = []
-    for a in (1.0, 2.0, 3.0):
-        stages += [Stage(n * cell, 1e12, a) for n in (4, 2, 1, 0.5, 0)]
+    """Sec. 5.3 with the two-network head: at M0 = 1e12 the smoothing steps
+    through N_sm = 4, 2, 1, 0.5, 0 cells, and at each N_sm the logistic
+    sharpness runs a = 1, 2, 3; then M0 = 1e11 with a = 3 at N_sm = 1, 0.5, 0."""
+    stages = [Stage(n * cell, 1e12, a) for n in (4, 2, 1, 0.5, 0) for a in (1.0, 2.0, 3.0)]
     stages += [Stage(n * cell, 1e11, 3.0) for n in (1, 0.5, 0)]
     return stages
 
