@@ -68,3 +68,12 @@ def test_reconstruction_run_uses_the_printed_setting():
     d = inspect.signature(experiments.full_reconstruction).parameters
     assert (d["N"].default, d["L"].default, d["nsteps"].default, d["nbar"].default) == (
         int(p["N"]), float(p["L"]), int(p["pm_steps"]), float(p["nbar"]))
+
+
+def test_network_shapes_are_the_printed_ones():
+    from oracle import nn
+    p = _params()
+    assert [nn.N_IN, nn.N_H1, nn.N_H2, 1] == [int(v) for v in p["NNp_layers"].split(",")]
+    assert [nn.NM_IN, nn.NM_H1, nn.NM_H2, 1] == [int(v) for v in p["NNm_layers"].split(",")]
+    assert len(nn.STENCIL) * 3 == nn.N_IN
+    assert oloss.Anneal(1.0, 1e12).a == float(p["logistic_a"])
