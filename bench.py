@@ -318,18 +318,26 @@ def extras(dev, steps):
                               "config": {"s": "the truth's linear field at full power"}}
     ctx.lbfgs_reset()
     ctx.recon_step(s, data, WORK["R_sm"], WORK["M0"])  # first iteration evaluates at s first
-    ctx.timing(True)
-    t0 = time.perf_counter()
-    iters = steps
-    for _ in range(iters):
+    iters = max(steps, 20)
+    lat = []
+    for _ in range(iters):  # recon_step synchronises: each wall-clock interval is one iteration's latency
+        t0 = time.perf_counter()
         ctx.recon_step(s, data, WORK["R_sm"], WORK["M0"])
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / iters
+        lat.append(time.perf_counter() - t0)
+    # the loss evaluations per iteration, counted on further iterations with the per-kernel timer
+    # on (one prior reduction per evaluation)
+    ctx.timing(True)
+    for _ in range(steps):
+        ctx.recon_step(s, data, WORK["R_sm"], WORK["M0"])
     rep = ctx.timing_report()
     ctx.timing(False)
-    evals = rep.get("prior", (0, 0.0))[0] / iters  # one prior reduction per loss evaluation
-    out["recon_step"] = {"ms_per_iteration": dt * 1e3, "loss_evals_per_iteration": evals,
-                         "note": "wall clock, host reads the loss after each line-search trial"}
+    evals = rep.get("prior", (0, 0.0))[0] / steps
+    lat_ms = sorted(1e3 * t for t in lat)
+    out["recon_step"] = {"ms_per_iteration": sum(lat_ms) / iters,
+                         "p50_ms": lat_ms[(iters - 1) // 2], "p99_ms": lat_ms[min(iters - 1, int(0.99 * iters))],
+                         "iterations": iters, "loss_evals_per_iteration": evals,
+                         "note": "wall clock per L-BFGS iteration (host reads the loss after each line-search "
+                                 "trial); time to a converged reconstruction is the serving benchmark's"}
     # two-point statistics of two 256^3 meshes (Sec. 4.3)
     delta = ctx.pm_forward(s_true)
     ctx.power_spectra(delta, delta)
