@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     # GPU tests are skipped (not failed) when no device is present, so the CPU
-    # suite can be collected everywhere; -m gpu on a GPU machine runs them.
+    # suite can be collected everywhere; -m gpu on a machine with a GPU runs them.
     try:
         import torch
         has_gpu = torch.cuda.is_available()
