@@ -832,10 +832,10 @@ template <int NM, int MMODE>
 int launch_paint_wtile(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
                        int64_t np, float scale, float offset, float* const* rho) {
     using WT = WTile<NM>;
-    // the shared-memory limit, raised once per process (the paint runs on one device)
-    static const cudaError_t attr = cudaFuncSetAttribute(
-        k_paint_wtile<NM, MMODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WT::smem);
-    PMR_TRY(check_cuda(c, attr, "paint smem attr"));
+    // one mass fits the default 48 KB of dynamic shared memory, so the
+    // allocation-free paint (no context, possibly inside a graph capture) needs
+    // no attribute; pm_init raises the limit for three masses
+    static_assert(WTile<1>::smem <= 48 * 1024, "one-mass paint within the default shared-memory limit");
     const int N = c->N;
     const dim3 grid((N + 31) / 32, (N + WT::Y - 1) / WT::Y, (N + WT::X - 1) / WT::X);
     k_paint_wtile<NM, MMODE><<<grid, WT::W * 32, WT::smem, c->stream>>>(
@@ -867,8 +867,10 @@ int paint3_sorted(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const
 }
 
 int pm_init(pmr_ctx* c) {
-    (void)c;
-    return PMR_OK;
+    return check_cuda(c,
+                      cudaFuncSetAttribute(k_paint_wtile<3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)WTile<3>::smem),
+                      "paint smem attr");
 }
 
 int paint(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const float* mass, int nmass, float scale,
