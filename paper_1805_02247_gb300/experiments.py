@@ -1,6 +1,6 @@
 """Reconstruction runs of the kind the paper reports (Sec. 5.3), on synthetic data.
 
-  python -m paper_1805_02247_gb300.experiments recon [--N 128] [--iters 100] [--out run.json]
+  python -m paper_1805_02247_gb300.experiments recon [--N 128] [--iters 100] [--schedule radii|paper] [--out run.json]
   python -m paper_1805_02247_gb300.experiments precision [--N 256] [--iters 200] [--out run.json]
 
 `full_reconstruction` builds a truth field, its halo-mass data, and runs the
@@ -39,8 +39,20 @@ def _stats(ctx, a, b):
             "stochasticity": (1 - rc ** 2).tolist()}
 
 
+def stages_for(schedule: str, head: int, N: int, L: float, radii, M0: float):
+    """The annealing stages of a run: "radii" anneals the residual smoothing
+    over the given radii (Mpc/h) at one M0; "paper" is the procedure of
+    Sec. 5.3 in grid cells of L/N (with the sharpness loop for the two-network head)."""
+    if schedule == "paper":
+        cell = L / N
+        return anneal.two_network_schedule(cell) if head == 1 else anneal.paper_schedule(cell)
+    if schedule == "radii":
+        return [anneal.Stage(float(r), M0) for r in radii]
+    raise ValueError(f"unknown schedule {schedule!r}")
+
+
 def full_reconstruction(N=128, L=400.0, nsteps=5, lpt_order=2, nbar=1e-3, radii=(4.0, 2.0, 1.0, 0.5), M0=1e12,
-                        iters=100, min_iter=10, nn_path=0, head=0, device="cuda", progress=None):
+                        iters=100, min_iter=10, nn_path=0, head=0, device="cuda", progress=None, schedule="radii"):
     cfg = pmrecon.default_config(N=N, L=L, nsteps=nsteps, lpt_order=lpt_order, nn_path=nn_path, head=head)
     w = synth.two_net_weights(1) if head == 1 else synth.xavier_weights(1)
     ctx = pmrecon.Context(cfg, torch.from_numpy(w).to(device))
@@ -54,7 +66,7 @@ def full_reconstruction(N=128, L=400.0, nsteps=5, lpt_order=2, nbar=1e-3, radii=
     thr = torch.topk(data.flatten(), keep).values[-1]
     data = torch.where(data >= thr, data, torch.zeros_like(data)).contiguous()
     s = ctx.linear_field(torch.from_numpy(synth.white_noise(N, 0)).to(dev), math.sqrt(0.1))
-    stages = [anneal.Stage(r, M0) for r in radii]
+    stages = stages_for(schedule, head, N, L, radii, M0)
     lin_true = ctx.irfft(s_true)
     before = {"linear": _stats(ctx, lin_true, ctx.irfft(s)), "final": _stats(ctx, d_true, ctx.pm_forward(s))}
     torch.cuda.synchronize()
@@ -66,13 +78,13 @@ def full_reconstruction(N=128, L=400.0, nsteps=5, lpt_order=2, nbar=1e-3, radii=
     per_stage = []
     for si, st in enumerate(stages):
         rec = [h for h in hist if h["stage"] == si]
-        per_stage.append({"R_sm": st.R_sm, "M0": st.M0, "iterations": len(rec),
+        per_stage.append({"R_sm": st.R_sm, "M0": st.M0, "a": st.a, "iterations": len(rec),
                           "loss_first": rec[0]["loss"] if rec else None, "loss_last": rec[-1]["loss"] if rec else None,
                           "converged": bool(rec and rec[-1]["converged"]),
                           "seconds": sum(h["seconds"] for h in rec)})
     out = {"config": {"N": N, "L": L, "nsteps": nsteps, "lpt_order": lpt_order, "nbar": nbar, "kept_voxels": keep,
-                      "radii": list(radii), "M0": M0, "max_iter": iters, "min_iter": min_iter, "nn_path": nn_path,
-                      "head": head},
+                      "schedule": schedule, "radii": list(radii), "M0": M0, "max_iter": iters, "min_iter": min_iter,
+                      "nn_path": nn_path, "head": head},
            "setup_seconds": t1 - t0, "reconstruction_seconds": t2 - t1,
            "iterations": len(hist), "stages": per_stage, "before": before, "after": after}
     ctx.close()
@@ -137,6 +149,8 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--nn-path", type=int, default=0)
     ap.add_argument("--head", type=int, default=0)
+    ap.add_argument("--schedule", choices=["radii", "paper"], default="radii",
+                    help="radii: R_sm = 4, 2, 1, 0.5 Mpc/h at M0 = 1e12; paper: the procedure of Sec. 5.3")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     if args.run == "precision":
@@ -147,7 +161,7 @@ def main(argv=None):
         print(json.dumps(res))
         return
     res = full_reconstruction(N=args.N or 128, L=args.L, nsteps=args.nsteps, iters=args.iters or 100,
-                              nn_path=args.nn_path, head=args.head)
+                              nn_path=args.nn_path, head=args.head, schedule=args.schedule)
     text = json.dumps(res)
     if args.out:
         with open(args.out, "w") as f:

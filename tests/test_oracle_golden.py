@@ -77,3 +77,13 @@ def test_network_shapes_are_the_printed_ones():
     assert [nn.NM_IN, nn.NM_H1, nn.NM_H2, 1] == [int(v) for v in p["NNm_layers"].split(",")]
     assert len(nn.STENCIL) * 3 == nn.N_IN
     assert oloss.Anneal(1.0, 1e12).a == float(p["logistic_a"])
+
+
+def test_reconstruction_run_can_take_the_printed_schedule():
+    from paper_1805_02247_gb300 import anneal, experiments
+    p = _params()
+    N, L = int(p["N"]), float(p["L"])
+    assert experiments.stages_for("paper", 1, N, L, (), 0.0) == anneal.two_network_schedule(L / N)
+    assert experiments.stages_for("paper", 0, N, L, (), 0.0) == anneal.paper_schedule(L / N)
+    assert [(st.R_sm, st.M0) for st in experiments.stages_for("radii", 0, N, L, (4.0, 2.0), 1e12)] == [
+        (4.0, 1e12), (2.0, 1e12)]
