@@ -60,7 +60,7 @@ def algorithmic(name: str, N: int):
         "x_fwd_1": ("bytes", 16 * NH), "x_fwd_in3": ("bytes", 32 * NH),
         "x_inv_3": ("bytes", 32 * NH), "x_inv_1": ("bytes", 16 * NH),
         "paint": ("bytes", (12 + 4 + 4) * N3),         # sorted offsets, bin starts -> density
-        "paint3": ("bytes", (12 + 4 + 4 + 12 + 12) * N3),  # sorted offsets, perm, starts, 3 masses -> 3 meshes
+        "paint3": ("bytes", (12 + 4 + 12 + 12) * N3),  # sorted offsets, starts, 3 sorted masses -> 3 meshes
         "permute3": ("bytes", (4 + 12 + 12) * N3),  # perm, 3 masses -> 3 masses in sorted order
         "seg_fix": ("bytes", (4 + 8 + 12 + 12) * N3),  # starts, perm r/w, positions -> sorted offsets
         "scan_reduce": ("bytes", 4 * N3),
