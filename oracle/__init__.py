@@ -20,8 +20,13 @@ pm      mesh conventions, linear field, Zel'dovich ICs, CIC paint/readout,
 nn      the 81-50-30-1 network of Sec. 2.1 on the 27-point stencil of Sec. 2.2
 loss    the loss of Eq. (loss) (Sec. 5.1) and its gradient w.r.t. s(k)
 lbfgs   the L-BFGS step of Sec. 5.2 (two-loop recursion, Armijo backtracking)
+anneal  the stages of the annealed reconstruction (Sec. 5.2-5.3)
+twopt   the binned two-point statistics of Sec. 4.3
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
-(closed forms, invariants, brute force, finite differences) except the whole
-annealed reconstruction outcome, which the paper cannot fix on synthetic data.
+(closed forms, invariants, brute force, finite differences, and the values the
+paper prints, kept under tests/golden/) except the whole annealed
+reconstruction outcome, which the paper cannot fix on synthetic data; the
+annealing driver itself (stage order, stop rule, line search) is pinned on
+hand-solvable objectives.
 """
