@@ -197,8 +197,9 @@ int pmr_paint(pmr_ctx* ctx, const float* x, int64_t np, const float* mass, float
  * let cudaMalloc/cudaFree synchronise the device cannot make that call. This
  * variant allocates nothing: its sorting scratch (about 9.4 MB) is one fixed
  * array in device memory that every GPU loading the library holds until the
- * process exits. Limits: N^3 <= 262144 (N <= 64) and np <= 262144; larger
- * sizes return PMR_EINVAL. The first call on a device looks up the array's
+ * process exits. Limits: 8 <= N <= 64 (N^3 <= 262144 cells) and
+ * 0 <= np <= N^3 particles (the bounds of pmr_paint() on a context);
+ * other sizes return PMR_EINVAL. The first call on a device looks up the array's
  * device address (with that device current), so make that first call before
  * any stream capture. All calls share the one array, whose contents are left
  * from the previous call: calls whose work overlaps on the GPU (different
@@ -265,10 +266,29 @@ int pmr_lbfgs_direction(pmr_ctx* ctx, const double* g, const double* S, const do
  * The first call allocates the context's shell table. Synchronises. */
 int pmr_power_spectra(pmr_ctx* ctx, const float* a, const float* b, double* out);
 
+/* The statistics of Sec. 4.3 per |k| shell, formed on the device in float64
+ * from the spectra of pmr_power_spectra() with a = h (the truth or data) and
+ * b = m (the model): cross-correlation r_c = P_hm / sqrt(P_hh P_mm),
+ * stochasticity s = P_hh (1 - r_c^2) ((Mpc/h)^3) and transfer function
+ * TF = sqrt(P_mm / P_hh). Shells as in pmr_power_spectra(); a shell whose
+ * spectrum is zero gives NaN statistics.
+ * out: HOST double[7][N/2] = {mode counts, P_hh, P_mm, P_hm, r_c, s, TF}.
+ * Synchronises. */
+int pmr_two_point(pmr_ctx* ctx, const float* h, const float* m, double* out);
+
 /* ------------------------------------------------------------- instrumentation */
 
 /* Number of kernels this context has launched since creation. */
 int64_t pmr_launch_count(const pmr_ctx* ctx);
+
+/* Identifier of the forward trajectory (Sec. 5.2: the stored per-step particle
+ * positions) that the next pm_adjoint() would differentiate: a count of the
+ * forward sweeps this context has completed (pm_forward, loss_and_grad,
+ * recon_step each run one), or -1 when there is none (no forward yet, a failed
+ * sweep, or a call that replaced the state pm_adjoint needs). A caller that
+ * holds the value from its own forward can detect that another call has
+ * replaced the trajectory since. No synchronisation. */
+int64_t pmr_forward_id(const pmr_ctx* ctx);
 
 /* Per-kernel timing with CUDA events on the context stream. enable != 0
  * starts recording one event after every kernel launch (cost: one event

@@ -641,6 +641,8 @@ int pmr_growth(const pmr_config* cfg, double a, double* D, double* Gp, double* G
 
 int64_t pmr_launch_count(const pmr_ctx* c) { return c ? c->launches : -1; }
 
+int64_t pmr_forward_id(const pmr_ctx* c) { return (c && c->have_forward) ? c->fwd_id : -1; }
+
 int pmr_timing(pmr_ctx* c, int enable) {
     PMR_TRY(check_ctx(c));
     c->timing = enable != 0;

@@ -172,6 +172,7 @@ struct pmr_ctx {
     float* lam_x = nullptr;
     float* lam_p = nullptr;
     bool have_forward = false;
+    int64_t fwd_id = 0;  // counts completed forward sweeps (pmr_forward_id)
 
     // cell sort
     uint32_t* keys = nullptr;

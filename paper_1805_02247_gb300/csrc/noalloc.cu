@@ -61,10 +61,12 @@ int scratch_address(unsigned char** out) {
 }  // namespace
 
 extern "C" int pmr_paint_noalloc(int N, const float* x, int64_t np, const float* mass, float* rho, void* stream) {
-    if (N < 1 || (int64_t)N * N * N > kMaxCells)
-        return pmr::fail(nullptr, PMR_EINVAL, "pmr_paint_noalloc: N^3 must be in [1, 262144] (N <= 64)");
-    if (np < 0 || np > kMaxParticles)
-        return pmr::fail(nullptr, PMR_EINVAL, "pmr_paint_noalloc: np must be in [0, 262144]");
+    // The paint's tiles wrap their halo rows once, which needs N >= 8 (the
+    // smallest mesh pmr_create accepts); the fixed array holds N <= 64.
+    if (N < 8 || (int64_t)N * N * N > kMaxCells)
+        return pmr::fail(nullptr, PMR_EINVAL, "pmr_paint_noalloc: N must be in [8, 64] (N^3 <= 262144)");
+    if (np < 0 || np > (int64_t)N * N * N)
+        return pmr::fail(nullptr, PMR_EINVAL, "pmr_paint_noalloc: np must be in [0, N^3]");
     if (!rho || (np > 0 && !x)) return pmr::fail(nullptr, PMR_EINVAL, "pmr_paint_noalloc: NULL argument");
     unsigned char* base = nullptr;
     PMR_TRY(scratch_address(&base));

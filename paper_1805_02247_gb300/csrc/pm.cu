@@ -1007,6 +1007,7 @@ int za_adjoint(pmr_ctx* c, const float* lam_x, const float* lam_p, float2* grad)
 
 int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
     const int64_t N3 = c->N3;
+    c->have_forward = false;  // the stored trajectory is being replaced
     PMR_TRY(lpt_ics(c, s_k, c->disp, c->mom));
     const float om15 = (float)(1.5 * c->cfg.omega_m);
     Mul fm[3];
@@ -1020,6 +1021,7 @@ int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
         PMR_TRY(kick_drift(c, c->F, din, dout, c->mom, (float)c->kick[s], (float)c->drift[s]));
     }
     c->have_forward = true;
+    c->fwd_id++;
     return PMR_OK;
 }
 

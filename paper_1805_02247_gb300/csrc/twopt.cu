@@ -5,7 +5,8 @@
 // Shell i holds the modes with integer wavevector norm i + 1/2 <= |n| < i + 3/2
 // (k = 2 pi n / L), i < N/2. The half-array entries of each shell are listed
 // once per context (host counting sort by shell); one block per shell then
-// sums its modes in a fixed order in float64, so the result is deterministic.
+// sums its modes in a fixed order in float64, so the result is deterministic,
+// and one thread per shell forms the spectra and the statistics.
 #include <cmath>
 
 #include "common.cuh"
@@ -47,6 +48,23 @@ __global__ void __launch_bounds__(kT) k_shell_reduce(const float2* __restrict__ 
     }
 }
 
+// Per shell, from the sums: mode count, the three spectra P = sum / count * L^3 / N^6,
+// and r_c = P_ab / sqrt(P_aa P_bb), s = P_aa (1 - r_c^2), TF = sqrt(P_bb / P_aa)
+// (a = h, the truth or data; b = N, the model). Rows of out: [7][nb]. A shell
+// without modes gives zero spectra; a zero spectrum gives NaN statistics (0/0).
+__global__ void k_shell_stats(double* __restrict__ sums, int nb, double norm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const double n = sums[i];
+    double P[3];
+    for (int q = 0; q < 3; ++q) P[q] = n > 0 ? sums[(q + 1) * nb + i] / n * norm : 0.0;
+    const double rc = P[2] / sqrt(P[0] * P[1]);
+    for (int q = 0; q < 3; ++q) sums[(q + 1) * nb + i] = P[q];
+    sums[4 * nb + i] = rc;
+    sums[5 * nb + i] = P[0] * (1.0 - rc * rc);
+    sums[6 * nb + i] = sqrt(P[1] / P[0]);
+}
+
 // list the half-array entries of each shell (ascending index inside a shell)
 int build_shells(pmr_ctx* c) {
     if (c->shell_order) return PMR_OK;
@@ -66,7 +84,7 @@ int build_shells(pmr_ctx* c) {
         if (shell[i] != 0xffffffffu) order[fill[shell[i]]++] = (uint32_t)i;
     PMR_TRY(check_cuda(c, cudaMalloc(&c->shell_order, sizeof(uint32_t) * order.size()), "shells"));
     PMR_TRY(check_cuda(c, cudaMalloc(&c->shell_off, sizeof(uint32_t) * (nb + 1)), "shells"));
-    PMR_TRY(check_cuda(c, cudaMalloc(&c->shell_out, sizeof(double) * 4 * nb), "shells"));
+    PMR_TRY(check_cuda(c, cudaMalloc(&c->shell_out, sizeof(double) * 7 * nb), "shells"));
     PMR_TRY(check_cuda(c, cudaMemcpy(c->shell_order, order.data(), sizeof(uint32_t) * order.size(),
                                      cudaMemcpyHostToDevice), "shells"));
     return check_cuda(c, cudaMemcpy(c->shell_off, cnt.data(), sizeof(uint32_t) * (nb + 1), cudaMemcpyHostToDevice),
@@ -87,7 +105,10 @@ void twopt_free(pmr_ctx* c) {
 
 using namespace pmr;
 
-extern "C" int pmr_power_spectra(pmr_ctx* c, const float* a, const float* b, double* out) {
+namespace {
+
+// spectra and statistics of Sec. 4.3 into c->shell_out [7][N/2], then `rows` rows to the host
+int two_point(pmr_ctx* c, const float* a, const float* b, double* out, int rows) {
     if (!c) return fail(nullptr, PMR_EINVAL, "context is NULL");
     if (!a || !b || !out) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(build_shells(c));
@@ -96,15 +117,20 @@ extern "C" int pmr_power_spectra(pmr_ctx* c, const float* a, const float* b, dou
     const int nb = c->N / 2;
     k_shell_reduce<<<nb, kT, 0, c->stream>>>(c->cA, c->cB, c->shell_order, c->shell_off, c->P, c->N, c->shell_out);
     PMR_TRY(check_launch(c, "shell_reduce"));
-    std::vector<double> h(4 * nb);
-    PMR_TRY(check_cuda(c, cudaMemcpyAsync(h.data(), c->shell_out, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost,
-                                          c->stream), "readback"));
-    PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
     const double norm = std::pow(c->cfg.L, 3) / std::pow((double)c->N, 6);
-    for (int i = 0; i < nb; ++i) {
-        const double n = h[i];
-        out[i] = n;
-        for (int q = 1; q < 4; ++q) out[q * nb + i] = n > 0 ? h[q * nb + i] / n * norm : 0.0;
-    }
-    return PMR_OK;
+    k_shell_stats<<<nblocks(nb, 128), 128, 0, c->stream>>>(c->shell_out, nb, norm);
+    PMR_TRY(check_launch(c, "shell_stats"));
+    PMR_TRY(check_cuda(c, cudaMemcpyAsync(out, c->shell_out, sizeof(double) * rows * nb, cudaMemcpyDeviceToHost,
+                                          c->stream), "readback"));
+    return check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
+}
+
+}  // namespace
+
+extern "C" int pmr_power_spectra(pmr_ctx* c, const float* a, const float* b, double* out) {
+    return two_point(c, a, b, out, 4);
+}
+
+extern "C" int pmr_two_point(pmr_ctx* c, const float* h, const float* m, double* out) {
+    return two_point(c, h, m, out, 7);
 }

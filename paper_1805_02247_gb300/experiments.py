@@ -29,14 +29,12 @@ from . import anneal, pmrecon, synth
 
 
 def _stats(ctx, a, b):
-    counts, Paa, Pbb, Pab = ctx.power_spectra(a, b)
+    """Sec. 4.3 statistics of field b (the model) against field a (the truth), per |k| shell."""
+    t = ctx.two_point(a, b)
     kf = 2 * math.pi / ctx.cfg.L
-    k = kf * (np.arange(len(counts)) + 1.0)  # shell i holds i <= |n| - 0.5 < i + 1
-    with np.errstate(divide="ignore", invalid="ignore"):
-        rc = (Pab / np.sqrt(Paa * Pbb)).numpy()
-        tf = np.sqrt(Pbb / Paa).numpy()
-    return {"k": k.tolist(), "modes": counts.numpy().tolist(), "r_c": rc.tolist(), "transfer": tf.tolist(),
-            "stochasticity": (1 - rc ** 2).tolist()}
+    k = kf * (np.arange(len(t["counts"])) + 1.0)  # shell i holds i <= |n| - 0.5 < i + 1
+    return {"k": k.tolist(), "modes": t["counts"].tolist(), "r_c": t["r_c"].tolist(), "transfer": t["TF"].tolist(),
+            "stochasticity": t["s"].tolist()}
 
 
 def stages_for(schedule: str, head: int, N: int, L: float, radii, M0: float):

@@ -76,7 +76,9 @@ _SIGS = {
     "pmr_growth": (ctypes.c_int, [_P, ctypes.c_double, _P, _P, _P]),
     "pmr_lbfgs_direction": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _I64, _P]),
     "pmr_power_spectra": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pmr_two_point": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmr_launch_count": (ctypes.c_int64, [_P]),
+    "pmr_forward_id": (ctypes.c_int64, [_P]),
     "pmr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmr_timing_report": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
 }
@@ -228,8 +230,21 @@ class Context:
         t = torch.tensor(list(out), dtype=torch.float64).view(4, nb)
         return t[0], t[1], t[2], t[3]
 
+    def two_point(self, h: torch.Tensor, m: torch.Tensor) -> dict:
+        """Per |k| shell (Sec. 4.3): counts, P_hh, P_mm, P_hm, r_c, stochasticity s, transfer function TF,
+        as float64 host tensors; h = the truth or data field, m = the model field."""
+        nb = self.N // 2
+        out = (ctypes.c_double * (7 * nb))()
+        self._check(self._lib.pmr_two_point(self._h, _ptr(h), _ptr(m), out))
+        t = torch.tensor(list(out), dtype=torch.float64).view(7, nb)
+        return dict(zip(("counts", "P_hh", "P_mm", "P_hm", "r_c", "s", "TF"), t))
+
     def launch_count(self) -> int:
         return int(self._lib.pmr_launch_count(self._h))
+
+    def forward_id(self) -> int:
+        """Identifier of the trajectory the next pm_adjoint differentiates (-1: none)."""
+        return int(self._lib.pmr_forward_id(self._h))
 
     def timing(self, enable: bool):
         self._check(self._lib.pmr_timing(self._h, int(enable)))
@@ -340,13 +355,26 @@ class ReconLoss(torch.autograd.Function):
 
 
 class PMForward(torch.autograd.Function):
-    """delta_final(s) of the PM model with the hand-written adjoint as its backward."""
+    """delta_final(s) of the PM model with the hand-written adjoint as its backward.
+
+    The context stores one trajectory (the per-step particle positions of its
+    last forward sweep). backward() differentiates the trajectory its own
+    forward() left; if any later call on the same context replaced it (another
+    PMForward, loss_and_grad, recon_step, ...), backward raises PMR_ESTATE
+    instead of returning the gradient of a different trajectory.
+    """
 
     @staticmethod
     def forward(ctx_, s: torch.Tensor, job: Context):
         ctx_.job = job
-        return job.pm_forward(s.detach().contiguous())
+        delta = job.pm_forward(s.detach().contiguous())
+        ctx_.fwd_id = job.forward_id()
+        return delta
 
     @staticmethod
     def backward(ctx_, grad_delta):
-        return ctx_.job.pm_adjoint(grad_delta.contiguous().to(torch.float32)), None
+        job = ctx_.job
+        if job.forward_id() != ctx_.fwd_id:
+            raise PMRError(-6, "PMForward.backward: the context's stored trajectory was replaced after this "
+                               "forward (run backward before the next forward on the same context)")
+        return job.pm_adjoint(grad_delta.contiguous().to(torch.float32)), None

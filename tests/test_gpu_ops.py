@@ -253,3 +253,25 @@ def test_lpt_order_one_is_zeldovich():
     d1, p1 = ctx.lpt_ics(to_dev(s))
     d0, p0 = ctx.za_ics(to_dev(s))
     assert torch.equal(d1, d0) and torch.equal(p1, p0)
+
+
+@pytest.mark.parametrize("N,L", [(32, 100.0), (64, 400.0)])
+def test_two_point_statistics_parity(N, L):
+    # r_c, stochasticity s = P_hh (1 - r_c^2) and TF = sqrt(P_mm / P_hh) of Sec. 4.3,
+    # formed on the device, against the oracle on the same meshes: data = signal +
+    # noise in quadrature with it (s = the noise power, r_c strictly inside (0, 1))
+    from oracle import twopt
+    ctx, _ = context(N=N, L=L)
+    a = synth.gaussian_vector((N, N, N), seed=63)
+    kx = np.fft.fftfreq(N, d=1.0 / N)[:, None, None] * np.ones((1, N, N // 2 + 1))
+    kx[N // 2] = 0.0
+    n = np.fft.irfftn(0.3j * kx * np.fft.rfftn(a.astype(np.float64)), s=(N, N, N), axes=(0, 1, 2))
+    h = (a + n).astype(np.float32)
+    got = ctx.two_point(to_dev(h), to_dev(a))
+    counts, P_hh, P_mm, P_hm = twopt.power_spectra(f32(h), f32(a), L)
+    rc, s, tf = twopt.statistics(P_hh, P_mm, P_hm)
+    assert np.array_equal(got["counts"].numpy(), counts)
+    for key, want in (("P_hh", P_hh), ("P_mm", P_mm), ("P_hm", P_hm), ("r_c", rc), ("s", s), ("TF", tf)):
+        assert rel_l2(got[key].numpy(), want) <= FIELD_TOL, key
+    _, P_nn, _, _ = twopt.power_spectra(f32(h) - f32(a), f32(h) - f32(a), L)
+    assert rel_l2(got["s"].numpy(), P_nn) <= 1e-4  # the stochasticity is the noise power

@@ -310,3 +310,24 @@ def test_graphs_need_a_stream():
     ctx, _ = context(N=8)  # default (legacy) stream
     with pytest.raises(PMRError, match="EINVAL"):
         ctx.use_graphs(True)
+
+
+def test_pm_forward_autograd_detects_a_replaced_trajectory():
+    # the context stores one trajectory: a backward whose forward was followed
+    # by another forward on the same context raises instead of differentiating
+    # the wrong trajectory; the newest forward's backward still works
+    from paper_1805_02247_gb300.pmrecon import PMForward, PMRError
+    N, L, nsteps = 16, 100.0, 2
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    setup, s = _problem(N, L, nsteps)
+    assert ctx.forward_id() == -1
+    s1 = to_dev(s).requires_grad_(True)
+    s2 = to_dev(0.5 * s).requires_grad_(True)
+    d1 = PMForward.apply(s1, ctx)
+    d2 = PMForward.apply(s2, ctx)
+    with pytest.raises(PMRError, match="ESTATE"):
+        d1.sum().backward()
+    g = synth.gaussian_vector((N, N, N), seed=25)
+    (d2 * to_dev(g)).sum().backward()
+    x_fin, cps, _ = opm.pm_forward(f32(0.5 * s), setup)
+    assert rel_l2(to_np(s2.grad), opm.final_density_T(cps, x_fin, f32(g), setup)) <= GRAD_TOL

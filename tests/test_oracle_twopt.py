@@ -66,3 +66,51 @@ def test_linear_field_recovers_the_input_power():
     ok = c > 500
     assert np.all(np.abs(p[ok] / want[ok] - 1.0) < 5.0 * np.sqrt(2.0 / c[ok]))
     assert k[0] == pytest.approx(2 * np.pi / L)
+
+
+def _orthogonal_pair(N, seed):
+    """A field a and a field n whose Fourier modes are in quadrature mode by mode
+    (n_k = i c(k) a_k with c real and odd: here a scaled x-derivative with its
+    Nyquist plane zeroed), so Re(a_k conj(n_k)) = 0 for every mode and every
+    shell sum of the cross term vanishes exactly, not only on average."""
+    a = synth.gaussian_vector((N, N, N), seed=seed).astype(np.float64)
+    A = np.fft.rfftn(a)
+    kx = np.fft.fftfreq(N, d=1.0 / N)[:, None, None] * np.ones((1, N, N // 2 + 1))
+    kx[N // 2] = 0.0
+    n = np.fft.irfftn(1j * 0.3 * kx * A, s=(N, N, N), axes=(0, 1, 2))
+    return a, n
+
+
+def test_stochasticity_is_the_noise_power_when_data_is_signal_plus_orthogonal_noise():
+    # h = a + n with n in quadrature with a: P_hm = P_mm = P_aa, P_hh = P_aa + P_nn
+    # per shell exactly, so r_c = sqrt(P_aa / P_hh), TF = sqrt(P_aa / P_hh) and
+    # the stochasticity s = P_hh (1 - r_c^2) = P_hh - P_aa is the noise power P_nn.
+    # The noise grows with |k|, so r_c falls strictly inside (0, 1) and a missing
+    # P_hh factor (s = 1 - r_c^2) or the wrong auto spectrum in front fails.
+    N, L = 16, 50.0
+    a, n = _orthogonal_pair(N, seed=8)
+    h = a + n
+    _, P_hh, P_mm, P_hm = twopt.power_spectra(h, a, L)
+    rc, s, tf = twopt.statistics(P_hh, P_mm, P_hm)
+    _, P_nn, _, _ = twopt.power_spectra(n, n, L)
+    _, P_aa, _, _ = twopt.power_spectra(a, a, L)
+    assert np.all((rc[1:] > 0.05) & (rc[1:] < 0.99))
+    assert np.allclose(s, P_nn, rtol=1e-10, atol=0)
+    assert np.allclose(rc, np.sqrt(P_aa / (P_aa + P_nn)), rtol=1e-10)
+    assert np.allclose(tf, np.sqrt(P_aa / (P_aa + P_nn)), rtol=1e-10)
+    # anti-correlated: the model is -a; r_c changes sign, s and TF do not
+    _, P_hh2, P_mm2, P_hm2 = twopt.power_spectra(h, -a, L)
+    rc2, s2, tf2 = twopt.statistics(P_hh2, P_mm2, P_hm2)
+    assert np.allclose(rc2, -rc, rtol=1e-10) and np.allclose(s2, s, rtol=1e-10) and np.allclose(tf2, tf, rtol=1e-10)
+
+
+def test_stochasticity_scales_with_the_data_amplitude():
+    # s carries the units of a power spectrum: scaling the data by 3 scales s by
+    # 9 and leaves r_c unchanged; TF = sqrt(P_mm / P_hh) drops by 3
+    N, L = 16, 50.0
+    a, n = _orthogonal_pair(N, seed=9)
+    st1 = twopt.statistics(*twopt.power_spectra(a + n, a, L)[1:])
+    st3 = twopt.statistics(*twopt.power_spectra(3.0 * (a + n), a, L)[1:])
+    assert np.allclose(st3[0], st1[0], rtol=1e-12)
+    assert np.allclose(st3[1], 9.0 * st1[1], rtol=1e-12)
+    assert np.allclose(st3[2], st1[2] / 3.0, rtol=1e-12)
