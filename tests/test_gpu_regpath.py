@@ -14,6 +14,24 @@ finishes in seconds to a minute:
 * 128^3, L = 400 Mpc/h, 5 PM steps, second-order LPT ICs (the annealed
   reconstruction workload's shape, Sec. 3 and 5.3).
 
+The network's ReLU units (Eq. relu) make the gradient discontinuous: a unit
+whose pre-activation lies within rounding of zero is switched on or off by
+the last bit, and switching it moves the input gradient of that voxel by an
+O(1) fraction. At 64^3 with Xavier weights and zero biases some of the
+5.2 million hidden units sit that close: changing s by one part in 10^6 moves
+the FP64 oracle's own gradient by 5e-4 (relative L2), almost all of it from
+the network's input gradient (1.3e-3) while its input fields move by 1.3e-6.
+A float32 path differs from the float64 one by about that much, so the 1e-4
+gradient bound cannot separate a correct adjoint from an incorrect one there.
+The bound is therefore applied to a network whose every ReLU decision has a
+margin: the same Xavier weights with biases chosen, from the oracle's own
+pre-activation ranges over every voxel of the fields evaluated, so that half
+of the units of each layer stay on and half stay off with a gap of half the
+range on either side of zero (`margin_network`). Every kernel, mask and
+product of the network still runs; only the ambiguous decisions are gone. The
+Xavier network with zero biases is compared too, with its bound stated from
+the oracle's measured sensitivity.
+
 M0 = 1e11: at 64^3 in a 400 Mpc/h box the R_M = 3 Mpc/h smoothing is below a
 cell, and the truncated Gaussian rings the smoothed data mass down to about
 -2.6e10, so the 1e8 of the small workload would put a negative number inside
@@ -27,45 +45,106 @@ import pytest
 import torch
 
 from oracle import loss as oloss
+from oracle import nn as onn
 from oracle import pm as opm
 from paper_1805_02247_gb300 import pmrecon, synth
 
-from gpu_util import context, f32, rel_l2, to_dev, to_np
+from gpu_util import f32, lib, rel_l2, to_dev, to_np
 
 pytestmark = pytest.mark.gpu
 
 FIELD_TOL = 1e-5
 GRAD_TOL = 1e-4
+# Xavier weights, zero biases: ReLU decisions within rounding of zero (see the
+# module docstring; the oracle moves by 5e-4 under a 1e-6 change of s)
+KINK_GRAD_TOL = 1e-3
 
 
-def _problem(N, L, nsteps, lpt_order):
+def _ranges(u):
+    return u.min(axis=1), u.max(axis=1)
+
+
+def margin_network(w, field_sets, gap=0.5):
+    """Xavier weights w with biases that keep every ReLU decision away from zero.
+
+    Layer by layer, over every voxel of the given feature fields: the
+    pre-activation range [lo, hi] of each unit without bias; even units get a
+    bias that puts the range at [gap, 1 + gap] x (hi - lo) (always on), odd
+    units at -[1 + gap, gap] x (hi - lo) (always off); the output bias centres
+    y on its range so the softplus stays in its curved part. Returns the weight
+    vector and the smallest |pre-activation| / range width over all units and
+    voxels (>= gap by construction)."""
+    W1, _, W2, _, w3, _ = onn.unpack(w)
+    on1 = np.arange(W1.shape[0]) % 2 == 0
+    on2 = np.arange(W2.shape[0]) % 2 == 0
+
+    def chunks():
+        for f in field_sets:
+            n = f.shape[1]
+            for idx in np.array_split(np.arange(n ** 3), max(1, n ** 3 // (1 << 17))):
+                yield onn.stencil_at(f, np.stack(np.unravel_index(idx, (n, n, n)), axis=1))
+
+    def bias_for(lo, hi, on):
+        width = hi - lo
+        return np.where(on, -lo + gap * width, -hi - gap * width), width
+
+    lo = np.full(W1.shape[0], np.inf); hi = -lo
+    for v in chunks():
+        a, b = _ranges(W1 @ v)
+        lo, hi = np.minimum(lo, a), np.maximum(hi, b)
+    b1, width1 = bias_for(lo, hi, on1)
+    lo = np.full(W2.shape[0], np.inf); hi = -lo
+    for v in chunks():
+        a, b = _ranges(W2 @ onn.relu(W1 @ v + b1[:, None]))
+        lo, hi = np.minimum(lo, a), np.maximum(hi, b)
+    b2, width2 = bias_for(lo, hi, on2)
+    ylo, yhi, margin = np.inf, -np.inf, np.inf
+    for v in chunks():
+        a1 = W1 @ v + b1[:, None]
+        a2 = W2 @ onn.relu(a1) + b2[:, None]
+        y = w3 @ onn.relu(a2)
+        ylo, yhi = min(ylo, y.min()), max(yhi, y.max())
+        margin = min(margin, (np.abs(a1) / width1[:, None]).min(), (np.abs(a2) / width2[:, None]).min())
+    b3 = -0.5 * (ylo + yhi)
+    out = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, [b3]]).astype(np.float32)
+    return out, margin
+
+
+def _job(N, L, nsteps, lpt_order, margin):
+    """Oracle problem (start s at 10% power, synthetic data from the truth) and a GPU context."""
     setup = opm.PMSetup(N=N, L=L, nsteps=nsteps, lpt_order=lpt_order)
+    ls = oloss.LossSetup()
     s = f32(np.sqrt(0.1) * opm.linear_field(f32(synth.white_noise(N, 0)), setup))
+    s_true = opm.linear_field(f32(synth.white_noise(N, 2)), setup)
+    delta_true = opm.final_density(s_true, setup)
     w = synth.xavier_weights(1)
-    data = f32(oloss.synthetic_data(f32(synth.white_noise(N, 2)), f32(synth.scatter_noise(N, 2)), w, setup,
-                                    oloss.LossSetup()))
-    return setup, s, w, data
+    if margin:
+        delta_s = opm.final_density(s, setup)
+        w, m = margin_network(w, [oloss.features(delta_true, setup, ls), oloss.features(delta_s, setup, ls)])
+        assert m >= 0.49
+    # Sec. 4.2 synthetic data: the model's mass field on the truth times log-normal scatter
+    data = f32(oloss.nn_halo_map(delta_true, w, setup, ls) * np.exp(0.3 * f32(synth.scatter_noise(N, 2))))
+    lib()
+    cfg = pmrecon.default_config(N=N, L=L, nsteps=nsteps, lpt_order=lpt_order)
+    ctx = pmrecon.Context(cfg, torch.from_numpy(np.asarray(w, np.float32)).cuda())
+    return dict(ctx=ctx, setup=setup, s=s, w=w, data=data, N=N)
 
 
 @pytest.fixture(scope="module")
 def za64():
-    N, L, nsteps = 64, 400.0, 10
-    setup, s, w, data = _problem(N, L, nsteps, 1)
-    ctx, _ = context(N=N, L=L, nsteps=nsteps)
-    yield dict(ctx=ctx, setup=setup, s=s, w=w, data=data, N=N)
-    ctx.close()
+    job = _job(64, 400.0, 10, 1, margin=True)
+    yield job
+    job["ctx"].close()
 
 
 @pytest.fixture(scope="module")
 def lpt128():
-    N, L, nsteps = 128, 400.0, 5
-    setup, s, w, data = _problem(N, L, nsteps, 2)
-    ctx, _ = context(N=N, L=L, nsteps=nsteps, lpt_order=2)
-    yield dict(ctx=ctx, setup=setup, s=s, w=w, data=data, N=N)
-    ctx.close()
+    job = _job(128, 400.0, 5, 2, margin=True)
+    yield job
+    job["ctx"].close()
 
 
-def _loss_and_grad_parity(job, R_sm, M0):
+def _loss_and_grad_parity(job, R_sm, M0, grad_tol=GRAD_TOL):
     ctx, setup, s, w, data = job["ctx"], job["setup"], job["s"], job["w"], job["data"]
     parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
     want, gwant = oloss.loss_and_grad(s, data, w, setup, oloss.LossSetup(), oloss.Anneal(R_sm=R_sm, M0=M0))
@@ -76,7 +155,10 @@ def _loss_and_grad_parity(job, R_sm, M0):
     # the residual's share of the gradient is not negligible next to the prior's
     gprior = oloss.prior_grad(s, opm.power_half(setup))
     assert np.linalg.norm(gwant - gprior) > 0.3 * np.linalg.norm(gwant)
-    assert rel_l2(to_np(g), gwant) <= GRAD_TOL
+    err = rel_l2(to_np(g), gwant)
+    print(f"gradient rel-L2 vs oracle: {err:.2e}")
+    assert err <= grad_tol
+    return want, gwant
 
 
 def test_loss_and_grad_parity_64cubed_10_steps(za64):
@@ -85,6 +167,14 @@ def test_loss_and_grad_parity_64cubed_10_steps(za64):
 
 def test_loss_and_grad_parity_128cubed_2lpt_5_steps(lpt128):
     _loss_and_grad_parity(lpt128, R_sm=2.0, M0=1e11)
+
+
+def test_loss_and_grad_64cubed_xavier_network_within_its_kink_sensitivity():
+    # the plain Xavier network (zero biases): the loss parts to 1e-5; the gradient
+    # to the bound set by ReLU units on their kink (module docstring)
+    job = _job(64, 400.0, 10, 1, margin=False)
+    _loss_and_grad_parity(job, R_sm=4.0, M0=1e11, grad_tol=KINK_GRAD_TOL)
+    job["ctx"].close()
 
 
 def test_pm_forward_and_adjoint_64cubed_10_steps(za64):
@@ -104,7 +194,9 @@ def test_lpt_ics_and_adjoint_64cubed(lpt_order):
     N, L = 64, 400.0
     setup = opm.PMSetup(N=N, L=L, nsteps=10, lpt_order=lpt_order)
     s = f32(opm.linear_field(f32(synth.white_noise(N, 0)), setup))
-    ctx, _ = context(N=N, L=L, nsteps=10, lpt_order=lpt_order)
+    lib()
+    ctx = pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=10, lpt_order=lpt_order),
+                          torch.from_numpy(synth.xavier_weights(1)).cuda())
     disp, mom = ctx.lpt_ics(to_dev(s))
     x_want, p_want = opm.lpt_ics(s, setup)
     assert rel_l2(to_np(disp), x_want - opm.lattice(N)) <= FIELD_TOL
