@@ -32,10 +32,11 @@ product of the network still runs; only the ambiguous decisions are gone. The
 Xavier network with zero biases is compared too, with its bound stated from
 the oracle's measured sensitivity.
 
-M0 = 1e11: at 64^3 in a 400 Mpc/h box the R_M = 3 Mpc/h smoothing is below a
-cell, and the truncated Gaussian rings the smoothed data mass down to about
--2.6e10, so the 1e8 of the small workload would put a negative number inside
-the log (the oracle returns NaN there too).
+M0 = 1e10 with the margin network (its smoothed data mass stays above 1e11);
+1e11 with the Xavier one: at 64^3 in a 400 Mpc/h box the R_M = 3 Mpc/h
+smoothing is below a cell, and the truncated Gaussian rings that smoothed data
+mass down to about -2.6e10, so the 1e8 of the small workload would put a
+negative number inside the log (the oracle returns NaN there too).
 
 Tolerances are the float32 path's: 1e-5 relative on fields and loss parts,
 1e-4 relative L2 on gradients.
@@ -56,24 +57,27 @@ pytestmark = pytest.mark.gpu
 FIELD_TOL = 1e-5
 GRAD_TOL = 1e-4
 # Xavier weights, zero biases: ReLU decisions within rounding of zero (see the
-# module docstring; the oracle moves by 5e-4 under a 1e-6 change of s)
-KINK_GRAD_TOL = 1e-3
+# module docstring; the oracle moves by 5e-4, its residual part by 7e-4, under a
+# 1e-6 change of s: four times that)
+KINK_GRAD_TOL = 2e-3
 
 
 def _ranges(u):
     return u.min(axis=1), u.max(axis=1)
 
 
-def margin_network(w, field_sets, gap=0.5):
+def margin_network(w, field_sets, gap=0.5, y_span=8.0):
     """Xavier weights w with biases that keep every ReLU decision away from zero.
 
     Layer by layer, over every voxel of the given feature fields: the
     pre-activation range [lo, hi] of each unit without bias; even units get a
     bias that puts the range at [gap, 1 + gap] x (hi - lo) (always on), odd
-    units at -[1 + gap, gap] x (hi - lo) (always off); the output bias centres
-    y on its range so the softplus stays in its curved part. Returns the weight
-    vector and the smallest |pre-activation| / range width over all units and
-    voxels (>= gap by construction)."""
+    units at -[1 + gap, gap] x (hi - lo) (always off); the output weights are
+    scaled and offset so that y spans [-y_span/2, y_span/2] (a mass range of
+    about 300 for the default 8; the unscaled output would span some 10^9 in
+    mass, and float32 smoothing errors of the largest masses would then land
+    on M0-sized values inside the log). Returns the weight vector and the smallest |pre-activation| /
+    range width over all units and voxels (>= gap by construction)."""
     W1, _, W2, _, w3, _ = onn.unpack(w)
     on1 = np.arange(W1.shape[0]) % 2 == 0
     on2 = np.arange(W2.shape[0]) % 2 == 0
@@ -105,8 +109,9 @@ def margin_network(w, field_sets, gap=0.5):
         y = w3 @ onn.relu(a2)
         ylo, yhi = min(ylo, y.min()), max(yhi, y.max())
         margin = min(margin, (np.abs(a1) / width1[:, None]).min(), (np.abs(a2) / width2[:, None]).min())
-    b3 = -0.5 * (ylo + yhi)
-    out = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, w3, [b3]]).astype(np.float32)
+    scale = y_span / (yhi - ylo)
+    b3 = -0.5 * (ylo + yhi) * scale
+    out = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, scale * w3, [b3]]).astype(np.float32)
     return out, margin
 
 
@@ -152,21 +157,25 @@ def _loss_and_grad_parity(job, R_sm, M0, grad_tol=GRAD_TOL):
     assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
     assert parts[1] == pytest.approx(want["prior"], rel=FIELD_TOL)
     assert parts[2] == pytest.approx(want["residual"], rel=FIELD_TOL)
-    # the residual's share of the gradient is not negligible next to the prior's
+    # the whole gradient, and its residual part (the network, PM and loss adjoint
+    # without the prior's w s / P~ term) on its own, so a small residual share
+    # cannot hide an error of the adjoint chain
     gprior = oloss.prior_grad(s, opm.power_half(setup))
-    assert np.linalg.norm(gwant - gprior) > 0.3 * np.linalg.norm(gwant)
-    err = rel_l2(to_np(g), gwant)
-    print(f"gradient rel-L2 vs oracle: {err:.2e}")
-    assert err <= grad_tol
+    share = np.linalg.norm(gwant - gprior) / np.linalg.norm(gwant)
+    assert share > 0.05
+    g = to_np(g)
+    err, err_res = rel_l2(g, gwant), rel_l2(g - gprior, gwant - gprior)
+    print(f"gradient rel-L2 vs oracle: {err:.2e}; residual part {err_res:.2e} (share {share:.2f})")
+    assert err <= grad_tol and err_res <= grad_tol
     return want, gwant
 
 
 def test_loss_and_grad_parity_64cubed_10_steps(za64):
-    _loss_and_grad_parity(za64, R_sm=4.0, M0=1e11)
+    _loss_and_grad_parity(za64, R_sm=4.0, M0=1e10)
 
 
 def test_loss_and_grad_parity_128cubed_2lpt_5_steps(lpt128):
-    _loss_and_grad_parity(lpt128, R_sm=2.0, M0=1e11)
+    _loss_and_grad_parity(lpt128, R_sm=2.0, M0=1e10)
 
 
 def test_loss_and_grad_64cubed_xavier_network_within_its_kink_sensitivity():
@@ -212,7 +221,7 @@ def test_recon_loss_autograd_function_64cubed(za64):
     # the differentiation pattern: L(s) behind torch.autograd.Function, its
     # backward the hand-written adjoint; compared with the oracle's gradient
     ctx, setup, s, w, data = za64["ctx"], za64["setup"], za64["s"], za64["w"], za64["data"]
-    R_sm, M0 = 4.0, 1e11
+    R_sm, M0 = 4.0, 1e10
     s_dev = to_dev(s).requires_grad_(True)
     loss = pmrecon.ReconLoss.apply(s_dev, to_dev(data), ctx, R_sm, M0)
     (2.0 * loss).backward()
