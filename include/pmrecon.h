@@ -47,6 +47,8 @@ extern "C" {
 #define PMR_ENAN (-4)        /* loss is not finite (e.g. M_R + M0 <= 0) */
 #define PMR_ELINESEARCH (-5) /* no Armijo step within 20 halvings */
 #define PMR_ESTATE (-6)      /* call order violated (e.g. adjoint before forward) */
+#define PMR_ETIMEOUT (-7)    /* a tensor-core kernel's bounded barrier wait ran out (its outputs are
+                                invalid; the kernel freed its tensor memory and the context stays usable) */
 
 /* Problem definition. pmr_default_config() fills the synthetic 32^3 workload. */
 typedef struct pmr_config {
@@ -154,8 +156,12 @@ int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, 
 
 /* Loss of Eq. (loss) at s(k) and its gradient (Sec. 5.1-5.2).
  * data_mass: float32 mesh of the observed halo mass M^data (unsmoothed).
- * loss_out: HOST double[3] = {total, prior, residual}; the call synchronises
- *   the stream to return it. May be NULL (then nothing is read back).
+ * loss_out: double[3] = {total, prior, residual}, or NULL (nothing returned).
+ *   A HOST pointer: the call synchronises the stream, returns PMR_ENAN for a
+ *   non-finite loss and PMR_ETIMEOUT for a timed-out tensor-core wait. A
+ *   DEVICE pointer: the values are written on the stream, the call does not
+ *   synchronise (a non-finite loss shows as NaN/Inf in loss_out; pmr_sync()
+ *   reports a timed-out wait).
  * grad_s_k: c64 half array, may alias nothing else. */
 int loss_and_grad(pmr_ctx* ctx, const void* s_k, const float* data_mass, const pmr_anneal* an,
                   double* loss_out, void* grad_s_k);
@@ -275,6 +281,20 @@ int pmr_power_spectra(pmr_ctx* ctx, const float* a, const float* b, double* out)
  * out: HOST double[7][N/2] = {mode counts, P_hh, P_mm, P_hm, r_c, s, TF}.
  * Synchronises. */
 int pmr_two_point(pmr_ctx* ctx, const float* h, const float* m, double* out);
+
+/* Synchronises the context's stream and reports what the asynchronous calls
+ * since the last report could not: PMR_ETIMEOUT if a tensor-core network
+ * kernel's bounded wait ran out (the flag is cleared), PMR_ECUDA for a failed
+ * kernel. */
+int pmr_sync(pmr_ctx* ctx);
+
+/* Failure-detection test hook (no counterpart in the paper). With enable != 0
+ * the tensor-core network kernels of this context issue no MMAs and bound their
+ * barrier waits at a short limit, so every wait for an accumulator runs out:
+ * each kernel records the timeout, waits for nothing in flight, frees its
+ * tensor memory and returns, and the next synchronising call reports
+ * PMR_ETIMEOUT. enable = 0 restores normal launches. PMR_EINVAL for nn_path 2. */
+int pmr_test_stall_mma(pmr_ctx* ctx, int enable);
 
 /* ------------------------------------------------------------- instrumentation */
 

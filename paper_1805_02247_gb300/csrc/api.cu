@@ -36,6 +36,18 @@ static void record_event(pmr_ctx* c, const char* what) {
     c->ev_used++;
 }
 
+int check_tc_timeout(pmr_ctx* c) {
+    if (!c->tc_err) return check_cuda(c, cudaStreamSynchronize(c->stream), "sync");
+    int flag = 0;
+    PMR_TRY(check_cuda(c, cudaMemcpyAsync(&flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "rb"));
+    PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
+    if (!flag) return PMR_OK;
+    PMR_TRY(check_cuda(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream), "clear flag"));
+    PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));
+    return fail(c, PMR_ETIMEOUT, "a tensor-core network kernel's barrier wait ran out; the kernel freed its tensor "
+                                 "memory and returned, its outputs are invalid");
+}
+
 int check_launch(pmr_ctx* c, const char* what) {
     int rc = check_cuda(c, cudaGetLastError(), what);
     if (rc == PMR_OK) {
@@ -155,10 +167,8 @@ int check_ctx(pmr_ctx* c) { return c ? PMR_OK : fail(nullptr, PMR_EINVAL, "conte
 // total, prior, residual into host[0..2]
 int finish_loss(pmr_ctx* c, double* host) {
     double v[2];
-    int tc_err = 0;
-    PMR_TRY(check_cuda(c, cudaMemcpyAsync(&tc_err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "rb"));
+    PMR_TRY(check_tc_timeout(c));
     PMR_TRY(check_finite(c, c->red_out, 2, v));
-    if (tc_err) return fail(c, PMR_ECUDA, "a tensor-core kernel timed out waiting for its MMAs");
     host[0] = v[0] + v[1];
     host[1] = v[0];
     host[2] = v[1];
@@ -439,7 +449,29 @@ int loss_and_grad(pmr_ctx* c, const void* s_k, const float* data_mass, const pmr
     PMR_TRY(check_ctx(c));
     if (!s_k || !data_mass || !an || !grad_s_k) return fail(c, PMR_EINVAL, "NULL argument");
     if (!(an->R_sm >= 0) || !std::isfinite(an->M0)) return fail(c, PMR_EINVAL, "anneal: R_sm >= 0, finite M0");
-    return evaluate(c, (const float2*)s_k, data_mass, an, loss_out, (float2*)grad_s_k);
+    bool dev_out = false;
+    if (loss_out) {
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, loss_out) != cudaSuccess) cudaGetLastError();  // plain host memory
+        else dev_out = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    }
+    if (!dev_out) return evaluate(c, (const float2*)s_k, data_mass, an, loss_out, (float2*)grad_s_k);
+    // device destination: enqueue the copy, no host read-back and no synchronisation
+    PMR_TRY(evaluate(c, (const float2*)s_k, data_mass, an, nullptr, (float2*)grad_s_k));
+    return loss_to_device(c, loss_out);
+}
+
+int pmr_sync(pmr_ctx* c) {
+    PMR_TRY(check_ctx(c));
+    return check_tc_timeout(c);
+}
+
+int pmr_test_stall_mma(pmr_ctx* c, int enable) {
+    PMR_TRY(check_ctx(c));
+    if (c->cfg.nn_path == 2) return fail(c, PMR_EINVAL, "the CUDA-core network (nn_path 2) has no tensor-core waits");
+    c->tc_stall = enable != 0;
+    if (c->g_exec) drop_graph(c);  // a captured graph holds the launch controls
+    return PMR_OK;
 }
 
 int pmr_lbfgs_reset(pmr_ctx* c) {

@@ -164,6 +164,7 @@ struct pmr_ctx {
     float* tc_img = nullptr;    // tensor-core operand images of the weights (TF32 head + tail)
     float* tc_img_bf = nullptr; // the same as bfloat16
     int* tc_err = nullptr;      // set by a tensor-core kernel whose barrier wait timed out
+    bool tc_stall = false;      // failure-detection test hook: tensor-core kernels issue no MMAs
     int num_sms = 0;
 
     // particle state: displacement from the lattice point, [3][N3]
@@ -326,6 +327,10 @@ int prior_value(pmr_ctx* c, const float2* s, double* out_dev);
 int prior_grad_add(pmr_ctx* c, const float2* s, float2* grad);
 int reduce_sum_sq(pmr_ctx* c, const float* v, int64_t n, double scale, double* out_dev);
 int check_finite(pmr_ctx* c, const double* v, int n, double* host);
+int loss_to_device(pmr_ctx* c, double* out_dev);
+// PMR_ETIMEOUT (and the flag cleared) if a tensor-core kernel's wait ran out
+// since the last check; synchronises the stream
+int check_tc_timeout(pmr_ctx* c);
 
 // L-BFGS (lbfgs.cu) -------------------------------------------------------------
 int lbfgs_alloc(pmr_ctx* c);

@@ -164,6 +164,22 @@ int residual_backward(pmr_ctx* c, const pmr_anneal* an, float* gM) {
     return smooth_into(c, c->gm, c->cfg.R_M, gM);
 }
 
+namespace {
+__global__ void k_loss_out(const double* __restrict__ red, double* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        out[0] = red[0] + red[1];
+        out[1] = red[0];
+        out[2] = red[1];
+    }
+}
+}  // namespace
+
+// {total, prior, residual} of the last evaluation into a device array, on the stream
+int loss_to_device(pmr_ctx* c, double* out_dev) {
+    k_loss_out<<<1, 32, 0, c->stream>>>(c->red_out, out_dev);
+    return check_launch(c, "loss_out");
+}
+
 int check_finite(pmr_ctx* c, const double* v, int n, double* host) {
     PMR_TRY(check_cuda(c, cudaMemcpyAsync(host, v, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "readback"));
     PMR_TRY(check_cuda(c, cudaStreamSynchronize(c->stream), "sync"));

@@ -29,7 +29,8 @@
 // tile's MMAs overlap the next tile's operand build.
 //
 // Every mbarrier wait is bounded; on timeout the block records an error flag,
-// waits (bounded) for its MMAs, frees its TMEM and returns.
+// waits (bounded) for its MMAs, frees its TMEM and returns. The host reports
+// the flag as PMR_ETIMEOUT and clears it.
 #include <algorithm>
 #include <cstring>
 
@@ -153,9 +154,21 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+// Launch controls of the tensor-core kernels: the bound of every mbarrier wait
+// (try_wait polls), and whether the issuing lane issues its MMAs. issue = 0 is
+// the failure-detection test hook (pmr_test_stall_mma): nothing is ever in
+// flight, every wait for an accumulator runs out, and the kernel takes its
+// timeout path (error flag, TMEM freed, return).
+struct TcCtl {
+    uint32_t wait_limit;
+    int issue;
+};
+constexpr uint32_t kWaitLimit = 1u << 22;      // normal launches
+constexpr uint32_t kTestWaitLimit = 1u << 12;  // the stall hook
+
 // bounded wait for the phase; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-    for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try(bar, phase)) return true;
     return false;
 }
@@ -300,7 +313,7 @@ struct LayF {
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
     k_mlp_tc_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
-              float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err) {
+              float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err, TcCtl ctl) {
     using L = Lay<BF>;
     using F = LayF<BF>;
     constexpr int K1 = L::K1;
@@ -358,16 +371,17 @@ __global__ void __launch_bounds__(NTW, 1)
             const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
             uint32_t pa1 = 0, pa2 = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                if (!mbar_wait(bars + 0, pa1)) {
+                if (!mbar_wait(bars + 0, pa1, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
                 pa1 ^= 1;
                 tc_fence_after();
+                if (!ctl.issue) continue;  // test hook: D1 never completes
                 issue_layer<BF>(tmem + COL_D1, sA1h, sA1l, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1),
                                 K1, N1, nsplit);
                 mma_commit(bars + 2);
-                if (!mbar_wait(bars + 1, pa2)) {
+                if (!mbar_wait(bars + 1, pa2, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 mma_commit(bars + 3);
             }
             mma_commit(bars + 4);  // completes once every MMA issued above has
-            mbar_wait(bars + 4, 0);
+            mbar_wait(bars + 4, 0, ctl.wait_limit);
         }
         __syncwarp();
     } else {
@@ -479,7 +493,7 @@ __global__ void __launch_bounds__(NTW, 1)
             const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
 
             // (1) layer 1 of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 2, ph1));
+            ok = nbar_and(NT, mbar_wait(bars + 2, ph1, ctl.wait_limit));
             ph1 ^= 1;
             if (!ok) break;
             tc_fence_after();
@@ -509,7 +523,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 load_halo(nxt + gridDim.x);
             }
             // (4) layer 2 of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 3, ph2));
+            ok = nbar_and(NT, mbar_wait(bars + 3, ph2, ctl.wait_limit));
             ph2 ^= 1;
             if (!ok) break;
             tc_fence_after();
@@ -590,7 +604,7 @@ template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
     k_mlp_tc_bwd(const float* __restrict__ feat, const float* __restrict__ gM, const float4* __restrict__ img,
               TileMap tm, int ntiles, int nsplit, float M_scale, float a, float* __restrict__ gbox, Saved sv,
-              int* __restrict__ err) {
+              int* __restrict__ err, TcCtl ctl) {
     using L = Lay<BF>;
     using B = LayB<BF>;
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -643,16 +657,17 @@ __global__ void __launch_bounds__(NTW, 1)
             const uint32_t sA3h = smem_u32(A3h), sA3l = smem_u32(A3l), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
             uint32_t pa3 = 0, pa4 = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                if (!mbar_wait(bars + 0, pa3)) {
+                if (!mbar_wait(bars + 0, pa3, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
                 pa3 ^= 1;
                 tc_fence_after();
+                if (!ctl.issue) continue;  // test hook: D3 never completes
                 issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3),
                                 K3, NB3, nsplit);
                 mma_commit(bars + 2);
-                if (!mbar_wait(bars + 1, pa4)) {
+                if (!mbar_wait(bars + 1, pa4, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
@@ -663,7 +678,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 mma_commit(bars + 3);
             }
             mma_commit(bars + 4);  // completes once every MMA issued above has
-            mbar_wait(bars + 4, 0);
+            mbar_wait(bars + 4, 0, ctl.wait_limit);
         }
         __syncwarp();
     } else {
@@ -754,7 +769,7 @@ __global__ void __launch_bounds__(NTW, 1)
             tile_origin(tile, x0, y0, z0);
 
             // (1) layer-2 input gradient of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 2, ph3));
+            ok = nbar_and(NT, mbar_wait(bars + 2, ph3, ctl.wait_limit));
             ph3 ^= 1;
             if (!ok) break;
             tc_fence_after();
@@ -778,7 +793,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 load_saved(nxt + gridDim.x);
             }
             // (4) layer-1 input gradient of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 3, ph4));
+            ok = nbar_and(NT, mbar_wait(bars + 3, ph4, ctl.wait_limit));
             ph4 ^= 1;
             if (!ok) break;
             tc_fence_after();
@@ -979,21 +994,22 @@ int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nspl
     const float4* img = reinterpret_cast<const float4*>(BF ? c->tc_img_bf : c->tc_img);
     const float Ms = (float)c->cfg.M_scale;
     const Saved sv{c->nn_y, c->nn_m1, c->nn_m2};  // written by the forward, read by the backward
+    const TcCtl ctl{c->tc_stall ? kTestWaitLimit : kWaitLimit, c->tc_stall ? 0 : 1};
     if (!BWD) {
         const uint32_t sf = LayF<BF>::SMEM;
         if (c->cfg.head == 1)
-            k_mlp_tc_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_tc_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err, ctl);
         else
-            k_mlp_tc_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err);
+            k_mlp_tc_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err, ctl);
         return check_launch(c, "mlp_tc_fwd");
     }
     const uint32_t sb = LayB<BF>::SMEM;
     if (c->cfg.head == 1)
         k_mlp_tc_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
-                                                          c->tc_err);
+                                                          c->tc_err, ctl);
     else
         k_mlp_tc_bwd<false, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,
-                                                           c->tc_err);
+                                                           c->tc_err, ctl);
     return check_launch(c, "mlp_tc_bwd");
 }
 

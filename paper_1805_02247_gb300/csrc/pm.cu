@@ -510,16 +510,20 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
         gy = gy < 0 ? gy + N : (gy >= N ? gy - N : gy);
         return ((int64_t)gx * N + gy) * N;
     };
-    // one particle's corner terms (oz = 1 only when ONLY1)
-    auto acc = [&](uint32_t j, float (&S)[2][2][2][NM], bool only1) {
-        const float dx = sfrac[j], dy = sf1[j], dz = sf2[j];
-        float mv[NM];
+    // particle j's fractional offsets and masses
+    auto load = [&](uint32_t j, float& dx, float& dy, float& dz, float (&mv)[NM]) {
+        dx = sfrac[j];
+        dy = sf1[j];
+        dz = sf2[j];
 #pragma unroll
         for (int m = 0; m < NM; ++m) mv[m] = 1.f;
         if (MMODE == 1) mv[0] = mass[perm[j]];
         if (MMODE == 2)
 #pragma unroll
             for (int m = 0; m < NM; ++m) mv[m] = mass[m * np + j];
+    };
+    // one particle's corner terms (oz = 1 only when ONLY1)
+    auto acc_v = [&](float dx, float dy, float dz, const float (&mv)[NM], float (&S)[2][2][2][NM], bool only1) {
         const float ux = 1.f - dx, uy = 1.f - dy, uz = 1.f - dz;
         const float a[2][2] = {{ux * uy, ux * dy}, {dx * uy, dx * dy}};
 #pragma unroll
@@ -533,6 +537,11 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
                     S[ox][oy][1][m] = fmaf(a[ox][oy], wz1, S[ox][oy][1][m]);
                 }
         }
+    };
+    auto acc = [&](uint32_t j, float (&S)[2][2][2][NM], bool only1) {
+        float dx, dy, dz, mv[NM];
+        load(j, dx, dy, dz, mv);
+        acc_v(dx, dy, dz, mv, S, only1);
     };
 
     // warp w walks the bins of x-row w along y; the next row's bin bounds are
@@ -561,16 +570,41 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
     }
     __syncwarp();
     float C[2][NM];   // T_(ox,1) of the previous row
+    const int last = min(31, N - 1 - z0);  // the row's last bin in this block's z range
     for (int by = 0; by < WT::RY; ++by) {
         const int r = bx * WT::RY + by;
-        const uint32_t s = s_n, e = e_n;
+        uint32_t s = s_n, e = e_n;
         if (by + 1 < WT::RY && zin) {
             const int64_t rb = row_base(r + 1);
             s_n = start[rb + z];
             e_n = start[rb + z + 1];
         }
+        // The row's bins hold one contiguous run [rs, re) of the sorted arrays.
+        // It is read in coalesced chunks of 32 particles (one per lane); each
+        // lane then takes its own bin's particles of the chunk from the lanes
+        // that loaded them, in sorted order, so no lane waits on a chain of
+        // dependent loads as long as its bin's count.
+        const uint32_t rs = __shfl_sync(0xffffffffu, s, 0), re = __shfl_sync(0xffffffffu, e, last);
+        if (!zin) s = e = re;
         float S[2][2][2][NM] = {};
-        for (uint32_t j = s; j < e; ++j) acc(j, S, false);
+        for (uint32_t c0 = rs; c0 < re; c0 += 32) {
+            float px = 0.f, py = 0.f, pz = 0.f, pm[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) pm[m] = 1.f;
+            if (c0 + lane < re) load(c0 + lane, px, py, pz, pm);
+            const int lo = (int)(max(s, c0) - c0);
+            const int cnt = max((int)min(e, c0 + 32) - (int)max(s, c0), 0);
+            const int mc = __reduce_max_sync(0xffffffffu, cnt);
+            for (int it = 0; it < mc; ++it) {
+                const int src = min(lo + it, 31);
+                float mv[NM];
+                const float dx = __shfl_sync(0xffffffffu, px, src), dy = __shfl_sync(0xffffffffu, py, src),
+                            dz = __shfl_sync(0xffffffffu, pz, src);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) mv[m] = MMODE ? __shfl_sync(0xffffffffu, pm[m], src) : 1.f;
+                if (it < cnt) acc_v(dx, dy, dz, mv, S, false);
+            }
+        }
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
 #pragma unroll
@@ -833,8 +867,8 @@ int launch_paint_wtile(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, 
                        int64_t np, float scale, float offset, float* const* rho) {
     using WT = WTile<NM>;
     // one mass fits the default 48 KB of dynamic shared memory, so the
-    // allocation-free paint (no context, possibly inside a graph capture) needs
-    // no attribute; pm_init raises the limit for three masses
+    // allocation-free paint (which has no context and so no set-up call)
+    // needs no attribute; pm_init raises the limit for three masses
     static_assert(WTile<1>::smem <= 48 * 1024, "one-mass paint within the default shared-memory limit");
     const int N = c->N;
     const dim3 grid((N + 31) / 32, (N + WT::Y - 1) / WT::Y, (N + WT::X - 1) / WT::X);

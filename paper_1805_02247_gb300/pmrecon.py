@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpmrecon.so")
 
 PMR_OK = 0
-ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENAN", -5: "ELINESEARCH", -6: "ESTATE"}
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENAN", -5: "ELINESEARCH", -6: "ESTATE", -7: "ETIMEOUT"}
 N_WEIGHTS = 5661  # trunk network; the two-network head adds the mass network's
 N_MASS_WEIGHTS = 301
 
@@ -79,6 +79,8 @@ _SIGS = {
     "pmr_two_point": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmr_launch_count": (ctypes.c_int64, [_P]),
     "pmr_forward_id": (ctypes.c_int64, [_P]),
+    "pmr_sync": (ctypes.c_int, [_P]),
+    "pmr_test_stall_mma": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmr_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmr_timing_report": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
 }
@@ -207,13 +209,29 @@ class Context:
         return g
 
     def loss_and_grad(self, s, data, R_sm: float, M0: float, out=None, readback: bool = True,
-                      a: float = 3.0):
+                      a: float = 3.0, loss_dev: torch.Tensor | None = None):
+        """Loss parts (total, prior, residual) and the gradient. readback: return the parts on
+        the host (synchronises); loss_dev: a float64 CUDA tensor of 3 to receive them on the
+        stream instead (no synchronisation)."""
         g = self.half() if out is None else out
         an = Anneal(R_sm, M0, a)
         host = (ctypes.c_double * 3)()
-        self._check(self._lib.loss_and_grad(self._h, _ptr(s), _ptr(data), ctypes.byref(an),
-                                            host if readback else None, _ptr(g)))
-        return (tuple(host) if readback else None), g
+        if loss_dev is not None:
+            if loss_dev.dtype != torch.float64 or loss_dev.numel() < 3:
+                raise ValueError("loss_dev must be a float64 CUDA tensor with 3 entries")
+            dst = _ptr(loss_dev)
+        else:
+            dst = host if readback else None
+        self._check(self._lib.loss_and_grad(self._h, _ptr(s), _ptr(data), ctypes.byref(an), dst, _ptr(g)))
+        return (tuple(host) if readback and loss_dev is None else None), g
+
+    def sync(self):
+        """Synchronise the stream; raises PMR_ETIMEOUT / PMR_ECUDA for failures of earlier async calls."""
+        self._check(self._lib.pmr_sync(self._h))
+
+    def test_stall_mma(self, enable: bool):
+        """Failure-detection test hook: tensor-core network kernels issue no MMAs, so their waits run out."""
+        self._check(self._lib.pmr_test_stall_mma(self._h, 1 if enable else 0))
 
     def recon_step(self, s, data, R_sm: float, M0: float, a: float = 3.0):
         an = Anneal(R_sm, M0, a)

@@ -331,3 +331,48 @@ def test_pm_forward_autograd_detects_a_replaced_trajectory():
     (d2 * to_dev(g)).sum().backward()
     x_fin, cps, _ = opm.pm_forward(f32(0.5 * s), setup)
     assert rel_l2(to_np(s2.grad), opm.final_density_T(cps, x_fin, f32(g), setup)) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("nn_path", [0, 3])
+def test_tensor_core_wait_timeout_is_reported_and_the_context_recovers(nn_path):
+    # failure detection without a GPU fault: the stall hook makes the tensor-core
+    # kernels issue no MMAs, so their bounded accumulator waits run out; each
+    # kernel records the timeout, frees its tensor memory and returns. The loss
+    # call reports PMR_ETIMEOUT, an asynchronous call's timeout surfaces at
+    # pmr_sync, and the same context then computes the oracle's loss and gradient.
+    from paper_1805_02247_gb300.pmrecon import PMRError
+    N, L, nsteps, R_sm, M0 = 16, 50.0, 2, 4.0, 1e8
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, nn_path=nn_path)
+    setup, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = _data(N, L, nsteps)
+    s_dev, d_dev = to_dev(s), to_dev(data)
+    ctx.test_stall_mma(True)
+    with pytest.raises(PMRError, match="ETIMEOUT"):
+        ctx.loss_and_grad(s_dev, d_dev, R_sm, M0)
+    ctx.nn_halo_map(to_dev(f32(synth.gaussian_vector((N, N, N), seed=71))))
+    with pytest.raises(PMRError, match="ETIMEOUT"):
+        ctx.sync()
+    ctx.sync()  # reported once, then cleared
+    ctx.test_stall_mma(False)
+    parts, g = ctx.loss_and_grad(s_dev, d_dev, R_sm, M0)
+    want, gwant = oloss.loss_and_grad(s, data, synth.xavier_weights(1), setup, oloss.LossSetup(),
+                                      oloss.Anneal(R_sm=R_sm, M0=M0))
+    tol = (FIELD_TOL, GRAD_TOL) if nn_path == 0 else (1e-2, 1e-1)
+    assert parts[0] == pytest.approx(want["loss"], rel=tol[0])
+    assert rel_l2(to_np(g), gwant) <= tol[1]
+
+
+def test_loss_into_a_device_buffer_without_a_host_read():
+    # loss_out may be a device pointer: the parts land on the stream with no
+    # synchronisation, equal to what the host read returns
+    N, L, nsteps, R_sm, M0 = 16, 50.0, 2, 4.0, 1e8
+    ctx, _ = context(N=N, L=L, nsteps=nsteps)
+    _, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    s_dev, d_dev = to_dev(s), to_dev(_data(N, L, nsteps))
+    loss_dev = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    none, g1 = ctx.loss_and_grad(s_dev, d_dev, R_sm, M0, loss_dev=loss_dev)
+    assert none is None
+    g1 = g1.clone()
+    parts, g2 = ctx.loss_and_grad(s_dev, d_dev, R_sm, M0)
+    assert tuple(loss_dev.cpu().tolist()) == parts
+    assert torch.equal(g1, g2)
