@@ -570,41 +570,16 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
     }
     __syncwarp();
     float C[2][NM];   // T_(ox,1) of the previous row
-    const int last = min(31, N - 1 - z0);  // the row's last bin in this block's z range
     for (int by = 0; by < WT::RY; ++by) {
         const int r = bx * WT::RY + by;
-        uint32_t s = s_n, e = e_n;
+        const uint32_t s = s_n, e = e_n;
         if (by + 1 < WT::RY && zin) {
             const int64_t rb = row_base(r + 1);
             s_n = start[rb + z];
             e_n = start[rb + z + 1];
         }
-        // The row's bins hold one contiguous run [rs, re) of the sorted arrays.
-        // It is read in coalesced chunks of 32 particles (one per lane); each
-        // lane then takes its own bin's particles of the chunk from the lanes
-        // that loaded them, in sorted order, so no lane waits on a chain of
-        // dependent loads as long as its bin's count.
-        const uint32_t rs = __shfl_sync(0xffffffffu, s, 0), re = __shfl_sync(0xffffffffu, e, last);
-        if (!zin) s = e = re;
         float S[2][2][2][NM] = {};
-        for (uint32_t c0 = rs; c0 < re; c0 += 32) {
-            float px = 0.f, py = 0.f, pz = 0.f, pm[NM];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) pm[m] = 1.f;
-            if (c0 + lane < re) load(c0 + lane, px, py, pz, pm);
-            const int lo = (int)(max(s, c0) - c0);
-            const int cnt = max((int)min(e, c0 + 32) - (int)max(s, c0), 0);
-            const int mc = __reduce_max_sync(0xffffffffu, cnt);
-            for (int it = 0; it < mc; ++it) {
-                const int src = min(lo + it, 31);
-                float mv[NM];
-                const float dx = __shfl_sync(0xffffffffu, px, src), dy = __shfl_sync(0xffffffffu, py, src),
-                            dz = __shfl_sync(0xffffffffu, pz, src);
-#pragma unroll
-                for (int m = 0; m < NM; ++m) mv[m] = MMODE ? __shfl_sync(0xffffffffu, pm[m], src) : 1.f;
-                if (it < cnt) acc_v(dx, dy, dz, mv, S, false);
-            }
-        }
+        for (uint32_t j = s; j < e; ++j) acc(j, S, false);
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
 #pragma unroll

@@ -60,6 +60,9 @@ GRAD_TOL = 1e-4
 # module docstring; the oracle moves by 5e-4, its residual part by 7e-4, under a
 # 1e-6 change of s: four times that)
 KINK_GRAD_TOL = 2e-3
+# relative accuracy of the float32 network's mass field (two-part TF32 products,
+# float32 accumulation) that the residual term's condition number multiplies
+NET_REL_ERR = 1e-6
 
 
 def _ranges(u):
@@ -149,14 +152,28 @@ def lpt128():
     job["ctx"].close()
 
 
-def _loss_and_grad_parity(job, R_sm, M0, grad_tol=GRAD_TOL):
+def residual_condition(s, data, w, setup, an):
+    """kappa = 2 sum|r_s| / sum r_s^2 for the smoothed residual r_s of Eq. (loss):
+    if every model mass changes by a relative amount of at most eps, the residual
+    term changes by a relative amount of at most about kappa eps (the log turns the
+    change into an additive one of at most eps, and the Gaussian smoothings, whose
+    kernels sum to one, keep that bound up to their truncation). With the synthetic
+    data's log-normal scatter exp(0.3 g) the smoothed residual sits near its mean
+    -0.045 with a small spread, and kappa is 20 to 50."""
+    ls = oloss.LossSetup()
+    M = oloss.nn_halo_map(opm.final_density(s, setup), w, setup, ls)
+    _, (_, r_s) = oloss.residual_terms(M, data, setup, ls, an)
+    return 2.0 * np.abs(r_s).sum() / (r_s ** 2).sum()
+
+
+def _loss_and_grad_parity(job, R_sm, M0, grad_tol=GRAD_TOL, residual_tol=FIELD_TOL):
     ctx, setup, s, w, data = job["ctx"], job["setup"], job["s"], job["w"], job["data"]
     parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
     want, gwant = oloss.loss_and_grad(s, data, w, setup, oloss.LossSetup(), oloss.Anneal(R_sm=R_sm, M0=M0))
     assert np.isfinite(want["loss"])
-    assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
     assert parts[1] == pytest.approx(want["prior"], rel=FIELD_TOL)
-    assert parts[2] == pytest.approx(want["residual"], rel=FIELD_TOL)
+    assert parts[2] == pytest.approx(want["residual"], rel=residual_tol)
+    assert parts[0] == pytest.approx(want["loss"], rel=max(FIELD_TOL, residual_tol * want["residual"] / want["loss"]))
     # the whole gradient, and its residual part (the network, PM and loss adjoint
     # without the prior's w s / P~ term) on its own, so a small residual share
     # cannot hide an error of the adjoint chain
@@ -170,12 +187,28 @@ def _loss_and_grad_parity(job, R_sm, M0, grad_tol=GRAD_TOL):
     return want, gwant
 
 
+def _margin_residual_tol(job, R_sm, M0):
+    # the margin network's output is a difference of larger sums (its always-on
+    # units carry their offsets), so its float32 mass field carries a relative
+    # error of about 1e-6 (measured: 1.1e-6 rel-L2, mean 8e-7, at 64^3 and 128^3);
+    # the residual term is held to kappa times that
+    kappa = residual_condition(job["s"], job["data"], job["w"], job["setup"], oloss.Anneal(R_sm=R_sm, M0=M0))
+    return max(FIELD_TOL, NET_REL_ERR * kappa)
+
+
 def test_loss_and_grad_parity_64cubed_10_steps(za64):
-    _loss_and_grad_parity(za64, R_sm=4.0, M0=1e10)
+    _loss_and_grad_parity(za64, R_sm=4.0, M0=1e10, residual_tol=_margin_residual_tol(za64, 4.0, 1e10))
 
 
 def test_loss_and_grad_parity_128cubed_2lpt_5_steps(lpt128):
-    _loss_and_grad_parity(lpt128, R_sm=2.0, M0=1e10)
+    _loss_and_grad_parity(lpt128, R_sm=2.0, M0=1e10, residual_tol=_margin_residual_tol(lpt128, 2.0, 1e10))
+
+
+def test_loss_and_grad_128cubed_2lpt_xavier_network_within_its_kink_sensitivity():
+    # the plain Xavier network at the annealed-reconstruction shape: loss parts to 1e-5
+    job = _job(128, 400.0, 5, 2, margin=False)
+    _loss_and_grad_parity(job, R_sm=2.0, M0=1e11, grad_tol=KINK_GRAD_TOL)
+    job["ctx"].close()
 
 
 def test_loss_and_grad_64cubed_xavier_network_within_its_kink_sensitivity():
