@@ -44,13 +44,15 @@ def smoothing_schedule(radii_mpc, M0: float) -> list[Stage]:
     return [Stage(float(r), M0) for r in radii_mpc]
 
 
-def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=None, min_iter: int = 1):
+def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=None, min_iter: int = 1,
+                stage_end=None):
     """Runs the stages on s (complex64 half array, updated in place).
 
     Returns a list of per-iteration records {stage, iter, loss, prior, residual,
     converged, seconds}. A stage ends when recon_step reports convergence (from
     its min_iter-th iteration on) or after max_iter iterations; a line-search
-    failure ends the stage.
+    failure ends the stage. stage_end(index, stage), if given, runs after each
+    stage (per-stage dumps).
     """
     history = []
     for si, st in enumerate(stages):
@@ -70,4 +72,6 @@ def reconstruct(ctx: Context, s, data, stages, max_iter: int = 100, callback=Non
                 callback(rec)
             if conv and it + 1 >= min_iter:
                 break
+        if stage_end:
+            stage_end(si, st)
     return history

@@ -69,7 +69,15 @@ def full_reconstruction(N=128, L=400.0, nsteps=5, lpt_order=2, nbar=1e-3, radii=
     before = {"linear": _stats(ctx, lin_true, ctx.irfft(s)), "final": _stats(ctx, d_true, ctx.pm_forward(s))}
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    hist = anneal.reconstruct(ctx, s, data, stages, max_iter=iters, callback=progress, min_iter=min_iter)
+    dumps = []
+
+    def stage_end(si, st):
+        # the reconstructed linear field against the truth after each stage (the
+        # per-stage panels of the paper's reconstruction figure, Sec. 5.3)
+        dumps.append(_stats(ctx, lin_true, ctx.irfft(s)))
+
+    hist = anneal.reconstruct(ctx, s, data, stages, max_iter=iters, callback=progress, min_iter=min_iter,
+                              stage_end=stage_end)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     after = {"linear": _stats(ctx, lin_true, ctx.irfft(s)), "final": _stats(ctx, d_true, ctx.pm_forward(s))}
@@ -79,7 +87,9 @@ def full_reconstruction(N=128, L=400.0, nsteps=5, lpt_order=2, nbar=1e-3, radii=
         per_stage.append({"R_sm": st.R_sm, "M0": st.M0, "a": st.a, "iterations": len(rec),
                           "loss_first": rec[0]["loss"] if rec else None, "loss_last": rec[-1]["loss"] if rec else None,
                           "converged": bool(rec and rec[-1]["converged"]),
-                          "seconds": sum(h["seconds"] for h in rec)})
+                          "seconds": sum(h["seconds"] for h in rec),
+                          "losses": [h["loss"] for h in rec],
+                          "linear_after": dumps[si]})
     out = {"config": {"N": N, "L": L, "nsteps": nsteps, "lpt_order": lpt_order, "nbar": nbar, "kept_voxels": keep,
                       "schedule": schedule, "radii": list(radii), "M0": M0, "max_iter": iters, "min_iter": min_iter,
                       "nn_path": nn_path, "head": head},
@@ -95,11 +105,14 @@ def _rel(a, b):
     return float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
 
 
-def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cuda"):
+def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cuda", schedule=None):
     """The bf16 tensor-core network (nn_path 3) against the float32-accurate one
     (nn_path 0, itself within 1e-5 / 1e-4 of the FP64 oracle in the tests): the
-    error of each stage on the same inputs, and the loss each path reaches after
-    `iters` L-BFGS iterations from the same start on the same data."""
+    error of each stage on the same inputs, and the loss each path reaches from
+    the same start on the same data: after `iters` L-BFGS iterations at (R_sm,
+    M0), or, with schedule="paper", at the end of the annealing procedure of
+    Sec. 5.3 run to its stop rule (a stage ends when an iteration lowers the loss
+    by less than 0.1%; at most `iters` iterations per stage)."""
     dev = torch.device(device)
     w = torch.from_numpy(synth.xavier_weights(1)).to(dev)
     ctx = {p: pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=p), w) for p in (0, 3)}
@@ -112,9 +125,33 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
     M = {p: ctx[p].nn_halo_map(delta).clone() for p in (0, 3)}
     gd = {p: ctx[p].nn_halo_map_adjoint(delta, gM).clone() for p in (0, 3)}
     lg = {p: ctx[p].loss_and_grad(s0, data, R_sm, M0) for p in (0, 3)}
-    stages = {"network_output_M": _rel(M[3], M[0]), "network_adjoint_grad_delta": _rel(gd[3], gd[0]),
-              "loss": abs(lg[3][0][0] / lg[0][0][0] - 1), "loss_gradient": _rel(lg[3][1], lg[0][1])}
+    stages_err = {"network_output_M": _rel(M[3], M[0]), "network_adjoint_grad_delta": _rel(gd[3], gd[0]),
+                  "loss": abs(lg[3][0][0] / lg[0][0][0] - 1), "loss_gradient": _rel(lg[3][1], lg[0][1])}
     runs = {}
+    if schedule == "paper":
+        stages = anneal.paper_schedule(L / N)
+        for p in (0, 3):
+            s = s0.clone()
+            t = time.perf_counter()
+            hist = anneal.reconstruct(ctx[p], s, data, stages, max_iter=iters)
+            torch.cuda.synchronize()
+            per = []
+            for si, st in enumerate(stages):
+                rec = [h for h in hist if h["stage"] == si]
+                per.append({"R_sm": st.R_sm, "M0": st.M0, "iterations": len(rec),
+                            "final_loss": rec[-1]["loss"] if rec else None,
+                            "converged": bool(rec and rec[-1]["converged"])})
+            runs[p] = {"iterations": len(hist), "final_loss": hist[-1]["loss"], "stages": per,
+                       "seconds": time.perf_counter() - t}
+        for c in ctx.values():
+            c.close()
+        gaps = [abs(b["final_loss"] / a["final_loss"] - 1) if a["final_loss"] and b["final_loss"] else None
+                for a, b in zip(runs[0]["stages"], runs[3]["stages"])]
+        return {"config": {"N": N, "L": L, "nsteps": nsteps, "schedule": "paper (Sec. 5.3)",
+                           "max_iter_per_stage": iters, "stop": "0.1% decrease per iteration"},
+                "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
+                "stage_final_loss_rel_gap": gaps,
+                "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1)}
     for p in (0, 3):
         s = s0.clone()
         ctx[p].lbfgs_reset()
@@ -134,7 +171,7 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
     for c in ctx.values():
         c.close()
     return {"config": {"N": N, "L": L, "nsteps": nsteps, "R_sm": R_sm, "M0": M0, "iters": iters},
-            "stage_rel_err_bf16_vs_fp32": stages, "fp32_path": runs[0], "bf16_path": runs[3],
+            "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
             "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1)}
 
 
@@ -152,7 +189,8 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     if args.run == "precision":
-        res = precision(N=args.N or 256, L=args.L, nsteps=args.nsteps, iters=args.iters or 200)
+        res = precision(N=args.N or 256, L=args.L, nsteps=args.nsteps, iters=args.iters or 200,
+                        schedule="paper" if args.schedule == "paper" else None)
         if args.out:
             with open(args.out, "w") as f:
                 f.write(json.dumps(res))

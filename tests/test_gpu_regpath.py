@@ -273,3 +273,33 @@ def test_pm_forward_autograd_function_64cubed(za64):
     x_fin, cps, _ = opm.pm_forward(s, setup)
     assert rel_l2(to_np(delta.detach()), opm.density(x_fin, N)) <= FIELD_TOL
     assert rel_l2(to_np(s_dev.grad), opm.final_density_T(cps, x_fin, gd, setup, s)) <= GRAD_TOL
+
+
+def test_bf16_network_error_of_each_stage_against_the_oracle_64cubed():
+    # the precision pattern: the bf16 tensor-core network (bfloat16 operands,
+    # float32 accumulation; PM, FFT float32; loss, prior float64) against the FP64
+    # oracle at 64^3 / 10 steps with the Xavier network, stage by stage. Reported
+    # (printed), and bounded at the level 8-bit mantissas allow: 2^-9 per operand
+    # on the mass field, ReLU masks flipping on near-zero units for the gradients.
+    N, L, nsteps, R_sm, M0 = 64, 400.0, 10, 4.0, 1e11
+    job = _job(N, L, nsteps, 1, margin=False)
+    job["ctx"].close()
+    setup, s, w, data = job["setup"], job["s"], job["w"], job["data"]
+    ls = oloss.LossSetup()
+    ctx = pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=3),
+                          torch.from_numpy(np.asarray(w, np.float32)).cuda())
+    delta = opm.final_density(s, setup)
+    gM = f32(synth.gaussian_vector((N, N, N), seed=26))
+    err = {
+        "mass_field_M": rel_l2(to_np(ctx.nn_halo_map(to_dev(delta))), oloss.nn_halo_map(delta, w, setup, ls)),
+        "network_input_gradient": rel_l2(to_np(ctx.nn_halo_map_adjoint(to_dev(delta), to_dev(gM))),
+                                         oloss.nn_halo_map_T(gM, delta, w, setup, ls)),
+    }
+    parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0)
+    want, gwant = oloss.loss_and_grad(s, data, w, setup, ls, oloss.Anneal(R_sm=R_sm, M0=M0))
+    err["loss"] = abs(parts[0] / want["loss"] - 1)
+    err["loss_gradient"] = rel_l2(to_np(g), gwant)
+    ctx.close()
+    print("bf16 network vs FP64 oracle, 64^3 / 10 steps:", {k: f"{v:.2e}" for k, v in err.items()})
+    assert err["mass_field_M"] <= 1e-2 and err["loss"] <= 1e-2
+    assert err["network_input_gradient"] <= 1e-1 and err["loss_gradient"] <= 1e-1
