@@ -44,7 +44,7 @@ constexpr int OFF_B1 = H1 * NI, OFF_W2 = OFF_B1 + H1, OFF_B2 = OFF_W2 + H2 * H1,
               OFF_B3 = OFF_W3 + H2;
 
 constexpr int TM = 128;           // voxels per tile = MMA M = TMEM lanes
-constexpr int N1 = 64;            // layer 1 (81 -> 50, padded; K1 per precision below)
+constexpr int N1 = 64;            // layer 1 (81 -> 50, padded)
 constexpr int K2 = 64, N2 = 32;   // layer 2 (50 -> 30, padded)
 constexpr int K3 = 32, NB3 = 64;  // backward layer 2: g_a2 -> g_a1 (B = W2)
 constexpr int K4 = 64, NB4 = 96;  // backward layer 1: g_a1 -> g_v  (B = W1)
@@ -59,7 +59,20 @@ constexpr uint32_t COL_D1 = 0, COL_D2 = 64, COL_D3 = 96, COL_D4 = 160;
 
 constexpr uint32_t VEC_MASS = 160;  // float offset of the mass-network weights in the vector block
 constexpr uint32_t SZ_VEC = 1920;    // b1[64], b2[32], w3[32], b3[4], mass network[301]: 4 * 461 rounded to 128 B
-constexpr int HALO_PER = (HALO + NT - 1) / NT;  // halo values each thread loads
+
+// Layer 1 of the forward runs on z-line tiles: 128 voxels (x, y, z0 .. z0+127)
+// of one line along z. Its operand image holds, for rows i = 0 .. ZR-1 (the
+// voxel at z0 + i - 1, periodic), the K1Z = 32 columns k = c*9 + (ox+1)*3 +
+// (oy+1) (27 used): the three fields on the 3x3 (x, y) neighbourhood of the
+// line. A 16-byte K chunk is a column of ZR rows 16 bytes apart (8-row groups
+// SBO = 128 B apart) and chunks sit ZLBO bytes apart, so every row sits 16
+// bytes after the previous one and the operand for the neighbour offset oz is
+// the same image read from row oz + 1: a descriptor that starts 16 (oz + 1)
+// bytes in. Each input value is stored once, not once per stencil copy, and
+// the 3x3x3 stencil becomes three K1Z-wide MMA groups, one per oz.
+constexpr int ZR = TM + 2;             // image rows
+constexpr uint32_t ZLBO = ZR * 16;     // K-chunk stride of the z-line image
+constexpr int K1Z = 32;                // layer-1 K per z offset (27 used)
 
 // Operand precision. BF = false: float32 split into TF32 head and tail parts
 // (kind::tf32, K = 8 per instruction); BF = true: one bfloat16 part
@@ -77,13 +90,12 @@ struct Lay {
     static constexpr int KS = 32 / ES;       // K per instruction
     static constexpr int EC = 16 / ES;       // elements per 16-byte core-matrix row
     static constexpr int NP = BF ? 1 : 2;    // parts per operand (head, tail)
-    static constexpr int K1 = BF ? 96 : 88;  // layer-1 K (81 inputs) padded to whole k-steps
     __host__ __device__ static constexpr uint32_t off(int R, int r, int k) {
         return (uint32_t)((k / KS) * (R * 32) + (r >> 3) * 256 + ((k / EC) & 1) * 128 + (r & 7) * 16 + (k % EC) * ES);
     }
     static constexpr uint32_t bytes(int R, int K) { return (uint32_t)(R * K * ES); }
     // shared-memory map (bytes); weight images first, in the order of the global image
-    static constexpr uint32_t SZ_B1 = bytes(N1, K1), SZ_B2 = bytes(N2, K2), SZ_B3 = bytes(NB3, K3),
+    static constexpr uint32_t SZ_B1 = 3 * bytes(N1, K1Z), SZ_B2 = bytes(N2, K2), SZ_B3 = bytes(NB3, K3),
                               SZ_B4 = bytes(NB4, K4);
     static constexpr uint32_t S_B1 = 0;
     static constexpr uint32_t S_B2 = S_B1 + NP * SZ_B1;
@@ -107,6 +119,13 @@ __device__ __forceinline__ float tf32_hi(float x) {
 // descriptor version 1 (bits 46-47), no swizzle, base offset 0.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// The same for the z-line image of layer 1: LBO = ZLBO (K chunks), SBO = 128 B
+// (8-row groups), so rows are uniformly 16 bytes apart.
+__device__ __forceinline__ uint64_t zdesc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(ZLBO >> 4) << 16) | ((uint64_t)(128u >> 4) << 32) |
            ((uint64_t)1 << 46);
 }
 
@@ -283,49 +302,58 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 constexpr int NTW = NT + 32;  // 16 compute warps + the warp whose lane 0 issues the MMAs
 
-// Forward only, warp-specialised and software-pipelined over the CTA's tiles.
-// Warps 0-15 build operands and read accumulators; lane 0 of warp 16 issues
-// the MMAs. Operand buffers are per layer, so the compute warps build the next
-// tile's A1 while this tile's layer 2 runs, and read this tile's layer 2 while
-// the next tile's layer 1 runs. Handshakes (mbarriers):
+// Forward only, warp-specialised and software-pipelined over the CTA's z-line
+// tiles. Warps 0-15 build operands and read accumulators; lane 0 of warp 16
+// issues the MMAs. Operand buffers are per layer, so the compute warps build
+// the next tile's A1 while this tile's layer 2 runs, and read this tile's
+// layer 2 while the next tile's layer 1 runs. Handshakes (mbarriers):
 //   A1 full / A2 full: 512 compute-thread arrivals, each after its operand
 //     stores (async-proxy fence) and after its own reads of the accumulator
 //     the next MMA overwrites;
 //   D1 full / D2 full: tcgen05.commit after MMA1 / MMA2.
 // Per tile t (t' = the CTA's next tile), compute warps:
-//   wait D1(t); D1 -> A2, arrive A2; halo(t') -> A1, arrive A1; wait D2(t); D2 -> y, M
+//   wait D1(t); D1 -> A2, arrive A2; lines(t') -> A1, arrive A1; wait D2(t); D2 -> y, M
 // and the issuing lane: wait A1(t), MMA1(t) -> D1; wait A2(t), MMA2(t) -> D2.
 
 template <bool BF>
 struct LayF {
     using L = Lay<BF>;
-    static constexpr uint32_t SZ_A1 = L::bytes(TM, L::K1), SZ_A2 = L::bytes(TM, K2);
+    static constexpr int CH = K1Z / L::EC;            // 16-byte K chunks per image row
+    static constexpr int CH_USED = (27 + L::EC - 1) / L::EC;  // chunks holding inputs
+    static constexpr int TASKS = ZR * CH_USED;        // (row, chunk) stores per tile
+    static constexpr int TPT = (TASKS + NT - 1) / NT;  // per compute thread
+    static constexpr int KST = K1Z / L::KS;           // k-steps per z offset
+    static constexpr uint32_t SZ_A1 = CH * ZLBO, SZ_A2 = L::bytes(TM, K2);
     static constexpr uint32_t S_A1 = L::IMG_FWD;
     static constexpr uint32_t S_A2 = S_A1 + L::NP * SZ_A1;
     static constexpr uint32_t S_TAIL = S_A2 + L::NP * SZ_A2;
-    // halo, partial sums [4][TM], stencil offsets [K1], 5 barriers + TMEM slot
-    static constexpr uint32_t SMEM = S_TAIL + 4 * HALO + 4 * 4 * TM + 4 * L::K1 + 64;
+    // partial sums [4][TM], 5 barriers + TMEM slot
+    static constexpr uint32_t SMEM = S_TAIL + 4 * 4 * TM + 64;
     static_assert(SMEM <= 232448, "shared memory budget");
-    static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0, "aligned regions");
-    static_assert((4 * HALO + 4 * 4 * TM + 4 * L::K1) % 8 == 0, "aligned barriers");
+    static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0 && SZ_A1 % 128 == 0, "aligned regions");
+    static_assert(CH % 2 == 0 && KST * 2 == CH, "a k-step is two 16-byte chunks");
+};
+
+// z-line tiles: tile = (x * N + y) * nzt + zt, voxels z0 = 128 zt .. min(z0 + 128, N) - 1
+struct ZMap {
+    FastDiv nzt, n;
+    int N;
+    int64_t N3;
 };
 
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
-    k_mlp_tc_fwd(const float* __restrict__ feat, const float4* __restrict__ img, TileMap tm, int ntiles, int nsplit,
+    k_mlp_tc_fwd(const float* __restrict__ feat, const float4* __restrict__ img, ZMap zm, int ntiles, int nsplit,
               float M_scale, float a, float* __restrict__ M_out, Saved sv, int* __restrict__ err, TcCtl ctl) {
     using L = Lay<BF>;
     using F = LayF<BF>;
-    constexpr int K1 = L::K1;
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A1h = sm + F::S_A1;
     unsigned char* A1l = A1h + (L::NP - 1) * F::SZ_A1;  // == A1h with one part
     unsigned char* A2h = sm + F::S_A2;
     unsigned char* A2l = A2h + (L::NP - 1) * F::SZ_A2;
-    float* halo = reinterpret_cast<float*>(sm + F::S_TAIL);
-    float* part = halo + HALO;  // [4][TM]
-    int* koff = reinterpret_cast<int*>(part + 4 * TM);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(koff + K1);  // A1 full, A2 full, D1 full, D2 full, drain
+    float* part = reinterpret_cast<float*>(sm + F::S_TAIL);  // [4][TM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(part + 4 * TM);  // A1 full, A2 full, D1 full, D2 full, drain
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
     const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
     const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
@@ -334,13 +362,18 @@ __global__ void __launch_bounds__(NTW, 1)
     const int quad = warp & 3, cb = warp >> 2;
     const int row = quad * 32 + lane;
     constexpr uint32_t ncols = 128;
-    const int N = tm.N;
-    const int64_t N3 = tm.N3;
+    const int N = zm.N;
+    const int64_t N3 = zm.N3;
 
     {
         const uint32_t n16 = L::IMG_FWD / 16;
         float4* dst = reinterpret_cast<float4*>(sm);
         for (uint32_t i = tid; i < n16; i += NTW) dst[i] = img[i];
+        // the padding chunks of A1 (columns past the 27 inputs) stay zero
+        for (uint32_t i = tid; i < (uint32_t)(F::CH - F::CH_USED) * ZR; i += NTW)
+            for (int p = 0; p < L::NP; ++p)
+                *reinterpret_cast<float4*>(sm + F::S_A1 + p * F::SZ_A1 + (F::CH_USED + i / ZR) * ZLBO +
+                                           (i % ZR) * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (tid == 0) {
         const uint32_t cnt[5] = {(uint32_t)NT, (uint32_t)NT, 1u, 1u, 1u};
@@ -355,11 +388,7 @@ __global__ void __launch_bounds__(NTW, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (tid < K1) {
-        const int k = tid;
-        const int c = k / 27, o = k % 27, ox = o / 9, oy = (o / 3) % 3, oz = o % 3;
-        koff[k] = k < NI ? ((c * HX + ox) * HY + oy) * HZ + oz : -1;
-    }
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -369,6 +398,8 @@ __global__ void __launch_bounds__(NTW, 1)
         // ---- MMA issue (one lane)
         if (lane == 0) {
             const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
+            const uint32_t sB1 = smem_u32(sm + L::S_B1);
+            constexpr uint32_t SZ_B1OZ = L::bytes(N1, K1Z);
             uint32_t pa1 = 0, pa2 = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
                 if (!mbar_wait(bars + 0, pa1, ctl.wait_limit)) {
@@ -378,8 +409,23 @@ __global__ void __launch_bounds__(NTW, 1)
                 pa1 ^= 1;
                 tc_fence_after();
                 if (!ctl.issue) continue;  // test hook: D1 never completes
-                issue_layer<BF>(tmem + COL_D1, sA1h, sA1l, smem_u32(sm + L::S_B1), smem_u32(sm + L::S_B1 + L::SZ_B1),
-                                K1, N1, nsplit);
+                // layer 1: the three z offsets of the stencil, each a shifted view of A1
+                for (int oz = 0; oz < 3; ++oz)
+                    for (int ks = 0; ks < F::KST; ++ks) {
+                        const uint32_t ao = (uint32_t)ks * 2 * ZLBO + (uint32_t)oz * 16;
+                        const uint32_t bo = (uint32_t)oz * SZ_B1OZ + (uint32_t)ks * (N1 * 32);
+                        const uint32_t acc = (oz | ks) ? 1u : 0u;
+                        if constexpr (BF) {
+                            mma_bf16(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_bf16(TM, N1), acc);
+                        } else {
+                            mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), acc);
+                            if (nsplit > 1) {
+                                mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + L::SZ_B1 + bo),
+                                         idesc_tf32(TM, N1), 1u);
+                                mma_tf32(tmem + COL_D1, zdesc(sA1l + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), 1u);
+                            }
+                        }
+                    }
                 mma_commit(bars + 2);
                 if (!mbar_wait(bars + 1, pa2, ctl.wait_limit)) {
                     atomicExch(err, 1);
@@ -400,77 +446,54 @@ __global__ void __launch_bounds__(NTW, 1)
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         uint32_t ph1 = 0, ph2 = 0;
         bool ok = true;
-        // halo offsets of this thread's A1 entries (row tid / 4, k-steps tid % 4 + 4 i); -1: padding
-        constexpr int KS_PER = (K1 / 8 + 3) / 4;
-        int hoff[KS_PER][8];
-        {
-            const int r = tid >> 2, p = tid & 3;
-            const int base = ((r >> 6) * HY + ((r >> 4) & 3)) * HZ + (r & 15);
-#pragma unroll
-            for (int i = 0; i < KS_PER; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int ks = p + 4 * i, ko = ks < K1 / 8 ? koff[ks * 8 + j] : -1;
-                    hoff[i][j] = ko >= 0 ? ko + base : -1;
-                }
-        }
-        auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
-            const uint32_t t2 = tm.ntz.div((uint32_t)tile);
-            const int tz = tile - (int)(t2 * tm.ntz.d);
-            const int tx = (int)tm.nty.div(t2);
-            const int ty = (int)t2 - tx * (int)tm.nty.d;
-            x0 = tx * TX;
-            y0 = ty * TY;
-            z0 = tz * TZ;
+        auto tile_origin = [&](int tile, int& x, int& y, int& z0) {
+            const uint32_t line = zm.nzt.div((uint32_t)tile);
+            z0 = (tile - (int)(line * zm.nzt.d)) * TM;
+            x = (int)zm.n.div(line);
+            y = (int)line - x * N;
         };
-        float hv[HALO_PER];
-        // this thread's halo entries t = tid + q NT as (field, hx, hy, hz), 8 bits each (-1: none)
-        int hq[HALO_PER];
-#pragma unroll
-        for (int q = 0; q < HALO_PER; ++q) {
-            const int t = tid + q * NT;
-            const int c = t / (HX * HY * HZ), r = t % (HX * HY * HZ);
-            hq[q] = t < HALO ? (c << 24) | ((r / (HY * HZ)) << 16) | (((r / HZ) % HY) << 8) | (r % HZ) : -1;
-        }
-        auto load_halo = [&](int tile) {
+        // this thread's build tasks u = tid + NT m: image row i = u % ZR, chunk q = u / ZR,
+        // EC input columns k = q EC + e (k >= 27: padding, zero)
+        constexpr int EC = L::EC;
+        float hv[F::TPT][EC];
+        auto load_lines = [&](int tile) {
             if (tile >= ntiles) return;
-            int x0, y0, z0;
-            tile_origin(tile, x0, y0, z0);
+            int x, y, z0;
+            tile_origin(tile, x, y, z0);
 #pragma unroll
-            for (int q = 0; q < HALO_PER; ++q) {
-                if (hq[q] >= 0) {
-                    const int c = hq[q] >> 24, hx = (hq[q] >> 16) & 255, hy = (hq[q] >> 8) & 255, hz = hq[q] & 255;
-                    const int gx = wrapi(x0 + hx - 1, N), gy = wrapi(y0 + hy - 1, N), gz = wrapi(z0 + hz - 1, N);
-                    hv[q] = feat[c * N3 + ((int64_t)gx * N + gy) * N + gz];
+            for (int m = 0; m < F::TPT; ++m) {
+                const int u = tid + NT * m;
+                if (u >= F::TASKS) continue;
+                const int q = u / ZR, i = u - q * ZR;
+                const int z = (int)(((int64_t)z0 + i - 1 + N) % N);
+#pragma unroll
+                for (int e = 0; e < EC; ++e) {
+                    const int k = q * EC + e;
+                    float v = 0.f;
+                    if (k < 27) {
+                        const int c = k / 9, ox = (k / 3) % 3 - 1, oy = k % 3 - 1;
+                        const int gx = wrapi(x + ox, N), gy = wrapi(y + oy, N);
+                        v = feat[c * N3 + ((int64_t)gx * N + gy) * N + z];
+                    }
+                    hv[m][e] = v;
                 }
             }
         };
-        // halo registers -> shared memory -> A1 (4 threads per row), then arrive on "A1 full";
-        // the voxel's own three values (two-network head) of rows tid < TM into f
-        auto build_A1 = [&](float (&f)[3]) {
+        // prefetched lines -> A1, then arrive on "A1 full"
+        auto build_A1 = [&]() {
 #pragma unroll
-            for (int q = 0; q < HALO_PER; ++q) {
-                const int t = tid + q * NT;
-                if (t < HALO) halo[t] = hv[q];
-            }
-            nbar_sync(NT);
-            {
-                const int r = tid >> 2, p = tid & 3;
-#pragma unroll
-                for (int i = 0; i < KS_PER; ++i) {
-                    const int ks = p + 4 * i;
-                    if (ks < K1 / 8) {
-                        float v[8];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) v[j] = hoff[i][j] >= 0 ? halo[hoff[i][j]] : 0.f;
-                        put8<BF>(A1h, A1l, r, ks * 8, v);
-                    }
+            for (int m = 0; m < F::TPT; ++m) {
+                const int u = tid + NT * m;
+                if (u >= F::TASKS) continue;
+                const int q = u / ZR, i = u - q * ZR;
+                const uint32_t off = (uint32_t)q * ZLBO + (uint32_t)i * 16;
+                if constexpr (BF) {
+                    *reinterpret_cast<uint4*>(A1h + off) =
+                        make_uint4(pack_bf16x2(hv[m][0], hv[m][1]), pack_bf16x2(hv[m][2], hv[m][3]),
+                                   pack_bf16x2(hv[m][4], hv[m][5]), pack_bf16x2(hv[m][6], hv[m][7]));
+                } else {
+                    put4(A1h, A1l, off, hv[m][0], hv[m][1], hv[m][2], hv[m][3]);
                 }
-            }
-            if (TWO_NET && tid < TM) {
-                const int lx = tid >> 6, ly = (tid >> 4) & 3, lz = tid & 15;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) f[c] = halo[((c * HX + lx + 1) * HY + ly + 1) * HZ + lz + 1];
             }
             fence_async_smem();
             tc_fence_before();
@@ -478,20 +501,18 @@ __global__ void __launch_bounds__(NTW, 1)
         };
 
         int tile = blockIdx.x;
-        float fc[3] = {0.f, 0.f, 0.f};  // the current tile's centre values (two-network head)
-        load_halo(tile);
+        load_lines(tile);
         if (tile < ntiles) {
-            build_A1(fc);
-            load_halo(tile + gridDim.x);
+            build_A1();
+            load_lines(tile + gridDim.x);
         }
         for (; tile < ntiles; tile += gridDim.x) {
             const int nxt = tile + gridDim.x;
-            int x0, y0, z0;
-            tile_origin(tile, x0, y0, z0);
-            const int row_gx = x0 + (row >> 6), row_gy = y0 + ((row >> 4) & 3), row_gz = z0 + (row & 15);
-            const bool row_in = row_gx < N && row_gy < N && row_gz < N;
-            const int64_t row_vox = ((int64_t)row_gx * N + row_gy) * N + row_gz;
-
+            int x, y, z0;
+            tile_origin(tile, x, y, z0);
+            const int64_t line_vox = ((int64_t)x * N + y) * N + z0;
+            const bool row_in = z0 + row < N;
+            const int64_t row_vox = line_vox + row;
             // (1) layer 1 of this tile
             ok = nbar_and(NT, mbar_wait(bars + 2, ph1, ctl.wait_limit));
             ph1 ^= 1;
@@ -517,10 +538,9 @@ __global__ void __launch_bounds__(NTW, 1)
             tc_fence_before();
             mbar_arrive(bars + 1);
             // (3) the next tile's A1 while layer 2 runs
-            float fn[3] = {0.f, 0.f, 0.f};
             if (nxt < ntiles) {
-                build_A1(fn);
-                load_halo(nxt + gridDim.x);
+                build_A1();
+                load_lines(nxt + gridDim.x);
             }
             // (4) layer 2 of this tile
             ok = nbar_and(NT, mbar_wait(bars + 3, ph2, ctl.wait_limit));
@@ -544,24 +564,20 @@ __global__ void __launch_bounds__(NTW, 1)
             }
             tc_fence_before();
             nbar_sync(NT);
-            if (tid < TM) {
-                const int r = tid;
-                const int gx = x0 + (r >> 6), gy = y0 + ((r >> 4) & 3), gz = z0 + (r & 15);
-                const bool in = gx < N && gy < N && gz < N;
-                const int64_t vox = ((int64_t)gx * N + gy) * N + gz;
-                const float y = b3[0] + ((part[r] + part[TM + r]) + (part[2 * TM + r] + part[3 * TM + r]));
-                if (sv.y && in) sv.y[vox] = y;
+            if (tid < TM && z0 + tid < N) {
+                const int64_t vox = line_vox + tid;
+                const float y = b3[0] + ((part[tid] + part[TM + tid]) + (part[2 * TM + tid] + part[3 * TM + tid]));
+                if (sv.y) sv.y[vox] = y;
                 if (TWO_NET) {
                     const float pl = sigmoidf(a * y);
                     float u0, u1, u2;
-                    if (in)
-                        M_out[vox] = M_scale * pl * mass_net<false>(vec + VEC_MASS, fc[0], fc[1], fc[2], 0.f, u0, u1, u2);
+                    M_out[vox] = M_scale * pl *
+                                 mass_net<false>(vec + VEC_MASS, feat[vox], feat[N3 + vox], feat[2 * N3 + vox], 0.f,
+                                                 u0, u1, u2);
                 } else {
-                    if (in) M_out[vox] = M_scale * softplusf(y);
+                    M_out[vox] = M_scale * softplusf(y);
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) fc[c] = fn[c];
             nbar_sync(NT);  // part is rewritten by the next tile
         }
         if (!ok && tid == 0) atomicExch(err, 1);
@@ -874,10 +890,12 @@ uint16_t bf16_bits(float x) {
     return (uint16_t)(u >> 16);
 }
 
-// B operand (R rows, K columns) into the image: TF32 head and tail parts, or one bf16 part
+// B operand (R rows, K columns) into the image: TF32 head and tail parts (the
+// tail lo_delta bytes after the head; 0 means right after it), or one bf16 part
 template <bool BF>
 void put_operand(std::vector<unsigned char>& img, uint32_t base, int R, int K, float (*get)(const float*, int, int),
-                 const float* W) {
+                 const float* W, uint32_t lo_delta = 0) {
+    if (lo_delta == 0) lo_delta = Lay<BF>::bytes(R, K);
     using L = Lay<BF>;
     for (int r = 0; r < R; ++r)
         for (int k = 0; k < K; ++k) {
@@ -889,12 +907,18 @@ void put_operand(std::vector<unsigned char>& img, uint32_t base, int R, int K, f
             } else {
                 const float hi = tf32_round(v), lo = v - hi;
                 std::memcpy(&img[o], &hi, 4);
-                std::memcpy(&img[o + L::bytes(R, K)], &lo, 4);
+                std::memcpy(&img[o + lo_delta], &lo, 4);
             }
         }
 }
 
-float get_B1(const float* W, int h, int k) { return (h < H1 && k < NI) ? W[h * NI + k] : 0.f; }
+// layer-1 weights of z offset oz (0..2 for -1..1) on the z-line columns k = c*9 + (ox+1)*3 + (oy+1)
+template <int OZ>
+float get_B1z(const float* W, int h, int k) {
+    if (h >= H1 || k >= 27) return 0.f;
+    const int c = k / 9, oxy = k % 9;  // (ox+1)*3 + (oy+1)
+    return W[h * NI + c * 27 + oxy * 3 + OZ];
+}
 float get_B2(const float* W, int h2, int h1) { return (h2 < H2 && h1 < H1) ? W[OFF_W2 + h2 * H1 + h1] : 0.f; }
 float get_B3(const float* W, int h1, int h2) { return (h2 < H2 && h1 < H1) ? W[OFF_W2 + h2 * H1 + h1] : 0.f; }
 float get_B4(const float* W, int k, int h1) { return (h1 < H1 && k < NI) ? W[h1 * NI + k] : 0.f; }
@@ -960,7 +984,10 @@ template <bool BF>
 std::vector<unsigned char> build_image(const float* W) {
     using L = Lay<BF>;
     std::vector<unsigned char> img(L::IMG_ALL, 0);
-    put_operand<BF>(img, L::S_B1, N1, L::K1, get_B1, W);
+    // layer 1: the three z-offset sub-images, all heads first, then all tails
+    put_operand<BF>(img, L::S_B1, N1, K1Z, get_B1z<0>, W, L::SZ_B1);
+    put_operand<BF>(img, L::S_B1 + L::bytes(N1, K1Z), N1, K1Z, get_B1z<1>, W, L::SZ_B1);
+    put_operand<BF>(img, L::S_B1 + 2 * L::bytes(N1, K1Z), N1, K1Z, get_B1z<2>, W, L::SZ_B1);
     put_operand<BF>(img, L::S_B2, N2, K2, get_B2, W);
     put_operand<BF>(img, L::S_B3, NB3, K3, get_B3, W);
     put_operand<BF>(img, L::S_B4, NB4, K4, get_B4, W);
@@ -990,19 +1017,30 @@ template <bool BWD, bool BF>
 int launch_tc(pmr_ctx* c, const float* feat, const float* gM, float* M, int nsplit, float a) {
     int ntiles = 0;
     TileMap m = tile_map(c, &ntiles);
-    const int grid = std::min(ntiles, c->num_sms);
     const float4* img = reinterpret_cast<const float4*>(BF ? c->tc_img_bf : c->tc_img);
     const float Ms = (float)c->cfg.M_scale;
     const Saved sv{c->nn_y, c->nn_m1, c->nn_m2};  // written by the forward, read by the backward
     const TcCtl ctl{c->tc_stall ? kTestWaitLimit : kWaitLimit, c->tc_stall ? 0 : 1};
     if (!BWD) {
+        // z-line tiles: N^2 lines of ceil(N / 128) segments
+        const int nzt = (c->N + TM - 1) / TM;
+        ZMap zm;
+        zm.nzt = FastDiv((uint32_t)nzt);
+        zm.n = FastDiv((uint32_t)c->N);
+        zm.N = c->N;
+        zm.N3 = c->N3;
+        const int nz_tiles = c->N * c->N * nzt;
+        const int gz = std::min(nz_tiles, c->num_sms);
         const uint32_t sf = LayF<BF>::SMEM;
         if (c->cfg.head == 1)
-            k_mlp_tc_fwd<true, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err, ctl);
+            k_mlp_tc_fwd<true, BF><<<gz, NTW, sf, c->stream>>>(feat, img, zm, nz_tiles, nsplit, Ms, a, M, sv,
+                                                               c->tc_err, ctl);
         else
-            k_mlp_tc_fwd<false, BF><<<grid, NTW, sf, c->stream>>>(feat, img, m, ntiles, nsplit, Ms, a, M, sv, c->tc_err, ctl);
+            k_mlp_tc_fwd<false, BF><<<gz, NTW, sf, c->stream>>>(feat, img, zm, nz_tiles, nsplit, Ms, a, M, sv,
+                                                                c->tc_err, ctl);
         return check_launch(c, "mlp_tc_fwd");
     }
+    const int grid = std::min(ntiles, c->num_sms);
     const uint32_t sb = LayB<BF>::SMEM;
     if (c->cfg.head == 1)
         k_mlp_tc_bwd<true, BF><<<grid, NTW, sb, c->stream>>>(feat, gM, img, m, ntiles, nsplit, Ms, a, c->gbox, sv,

@@ -105,17 +105,24 @@ def _rel(a, b):
     return float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
 
 
-def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cuda", schedule=None):
+def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cuda", schedule=None, min_iter=10,
+              tol=1e-7):
     """The bf16 tensor-core network (nn_path 3) against the float32-accurate one
     (nn_path 0, itself within 1e-5 / 1e-4 of the FP64 oracle in the tests): the
     error of each stage on the same inputs, and the loss each path reaches from
     the same start on the same data: after `iters` L-BFGS iterations at (R_sm,
-    M0), or, with schedule="paper", at the end of the annealing procedure of
+    M0); with schedule="paper", at the end of the annealing procedure of
     Sec. 5.3 run to its stop rule (a stage ends when an iteration lowers the loss
-    by less than 0.1%; at most `iters` iterations per stage)."""
+    by less than 0.1%, from its min_iter-th iteration on; at most `iters` per
+    stage); with schedule="converged", at (R_sm, M0) until an iteration lowers
+    the loss by less than tol (relative) or after `iters` iterations. Each path's
+    final point is also evaluated with the float32-accurate loss, so the two
+    solutions are compared on one yardstick."""
     dev = torch.device(device)
     w = torch.from_numpy(synth.xavier_weights(1)).to(dev)
-    ctx = {p: pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=p), w) for p in (0, 3)}
+    ltol = tol if schedule == "converged" else 1e-3
+    ctx = {p: pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=p, lbfgs_tol=ltol), w)
+           for p in (0, 3)}
     s_true = ctx[0].linear_field(torch.from_numpy(synth.white_noise(N, 2)).to(dev), 1.0)
     delta = ctx[0].pm_forward(s_true).clone()
     data = (ctx[0].nn_halo_map(delta) * torch.exp(0.3 * torch.from_numpy(synth.scatter_noise(N, 2)).to(dev)))
@@ -128,13 +135,21 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
     stages_err = {"network_output_M": _rel(M[3], M[0]), "network_adjoint_grad_delta": _rel(gd[3], gd[0]),
                   "loss": abs(lg[3][0][0] / lg[0][0][0] - 1), "loss_gradient": _rel(lg[3][1], lg[0][1])}
     runs = {}
-    if schedule == "paper":
-        stages = anneal.paper_schedule(L / N)
+    finals = {}
+
+    def fp32_loss_at(s_final, st):
+        parts, _ = ctx[0].loss_and_grad(s_final, data, st.R_sm, st.M0)
+        return parts[0]
+
+    if schedule in ("paper", "converged"):
+        stages = anneal.paper_schedule(L / N) if schedule == "paper" else [anneal.Stage(R_sm, M0)]
+        mi = min_iter if schedule == "paper" else 1
         for p in (0, 3):
             s = s0.clone()
             t = time.perf_counter()
-            hist = anneal.reconstruct(ctx[p], s, data, stages, max_iter=iters)
+            hist = anneal.reconstruct(ctx[p], s, data, stages, max_iter=iters, min_iter=mi)
             torch.cuda.synchronize()
+            finals[p] = s
             per = []
             for si, st in enumerate(stages):
                 rec = [h for h in hist if h["stage"] == si]
@@ -143,15 +158,21 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
                             "converged": bool(rec and rec[-1]["converged"])})
             runs[p] = {"iterations": len(hist), "final_loss": hist[-1]["loss"], "stages": per,
                        "seconds": time.perf_counter() - t}
+        last = stages[-1]
+        yard = {p: fp32_loss_at(finals[p], last) for p in (0, 3)}
         for c in ctx.values():
             c.close()
         gaps = [abs(b["final_loss"] / a["final_loss"] - 1) if a["final_loss"] and b["final_loss"] else None
                 for a, b in zip(runs[0]["stages"], runs[3]["stages"])]
-        return {"config": {"N": N, "L": L, "nsteps": nsteps, "schedule": "paper (Sec. 5.3)",
-                           "max_iter_per_stage": iters, "stop": "0.1% decrease per iteration"},
+        return {"config": {"N": N, "L": L, "nsteps": nsteps, "schedule": schedule, "max_iter_per_stage": iters,
+                           "stop": (f"decrease below 0.1% per iteration from iteration {mi} of a stage"
+                                    if schedule == "paper" else f"decrease below {tol:g} per iteration"),
+                           "stages": [(st.R_sm, st.M0) for st in stages]},
                 "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
                 "stage_final_loss_rel_gap": gaps,
-                "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1)}
+                "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1),
+                "final_points_on_the_fp32_loss": {"fp32_path": yard[0], "bf16_path": yard[3],
+                                                  "rel_diff": abs(yard[3] / yard[0] - 1)}}
     for p in (0, 3):
         s = s0.clone()
         ctx[p].lbfgs_reset()
@@ -168,11 +189,15 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
         torch.cuda.synchronize()
         runs[p] = {"iterations": len(losses), "final_loss": losses[-1], "first_loss": losses[0],
                    "seconds": time.perf_counter() - t}
+        finals[p] = s
+    yard = {p: fp32_loss_at(finals[p], anneal.Stage(R_sm, M0)) for p in (0, 3)}
     for c in ctx.values():
         c.close()
     return {"config": {"N": N, "L": L, "nsteps": nsteps, "R_sm": R_sm, "M0": M0, "iters": iters},
             "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
-            "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1)}
+            "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1),
+            "final_points_on_the_fp32_loss": {"fp32_path": yard[0], "bf16_path": yard[3],
+                                              "rel_diff": abs(yard[3] / yard[0] - 1)}}
 
 
 def main(argv=None):
@@ -184,13 +209,17 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--nn-path", type=int, default=0)
     ap.add_argument("--head", type=int, default=0)
-    ap.add_argument("--schedule", choices=["radii", "paper"], default="radii",
-                    help="radii: R_sm = 4, 2, 1, 0.5 Mpc/h at M0 = 1e12; paper: the procedure of Sec. 5.3")
+    ap.add_argument("--schedule", choices=["radii", "paper", "converged"], default="radii",
+                    help="recon: radii (R_sm = 4, 2, 1, 0.5 Mpc/h at M0 = 1e12) or paper (the procedure of Sec. 5.3); "
+                         "precision: paper, or converged (one stage to a 1e-7 relative decrease)")
+    ap.add_argument("--R-sm", type=float, default=4.0, help="precision: residual smoothing, Mpc/h")
+    ap.add_argument("--M0", type=float, default=1e8, help="precision: M0")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     if args.run == "precision":
         res = precision(N=args.N or 256, L=args.L, nsteps=args.nsteps, iters=args.iters or 200,
-                        schedule="paper" if args.schedule == "paper" else None)
+                        schedule=args.schedule if args.schedule in ("paper", "converged") else None,
+                        R_sm=args.R_sm, M0=args.M0)
         if args.out:
             with open(args.out, "w") as f:
                 f.write(json.dumps(res))
