@@ -121,17 +121,25 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
     dev = torch.device(device)
     w = torch.from_numpy(synth.xavier_weights(1)).to(dev)
     ltol = tol if schedule == "converged" else 1e-3
-    ctx = {p: pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=p, lbfgs_tol=ltol), w)
-           for p in (0, 3)}
+    # path 0: float32-accurate network; 3: bf16 network; "c": the float32 path again
+    # from the start perturbed by one part in 10^6 (the control: how far two float32
+    # trajectories drift apart from rounding-sized differences alone)
+    ctx = {p: pmrecon.Context(pmrecon.default_config(N=N, L=L, nsteps=nsteps, nn_path=0 if p == "c" else p,
+                                                     lbfgs_tol=ltol), w)
+           for p in (0, 3, "c")}
     s_true = ctx[0].linear_field(torch.from_numpy(synth.white_noise(N, 2)).to(dev), 1.0)
     delta = ctx[0].pm_forward(s_true).clone()
     data = (ctx[0].nn_halo_map(delta) * torch.exp(0.3 * torch.from_numpy(synth.scatter_noise(N, 2)).to(dev)))
     data = data.contiguous()
     s0 = ctx[0].linear_field(torch.from_numpy(synth.white_noise(N, 0)).to(dev), math.sqrt(0.1))
+    eps = torch.from_numpy(synth.gaussian_vector(tuple(s0.shape) + (2,), seed=6)).to(dev)
+    s0c = (s0 * (1 + 1e-6 * torch.view_as_complex(eps))).contiguous()
+    starts = {0: s0, 3: s0, "c": s0c}
     gM = torch.from_numpy(synth.gaussian_vector((N, N, N), seed=5)).to(dev)
     M = {p: ctx[p].nn_halo_map(delta).clone() for p in (0, 3)}
     gd = {p: ctx[p].nn_halo_map_adjoint(delta, gM).clone() for p in (0, 3)}
     lg = {p: ctx[p].loss_and_grad(s0, data, R_sm, M0) for p in (0, 3)}
+    paths = (0, 3, "c")
     stages_err = {"network_output_M": _rel(M[3], M[0]), "network_adjoint_grad_delta": _rel(gd[3], gd[0]),
                   "loss": abs(lg[3][0][0] / lg[0][0][0] - 1), "loss_gradient": _rel(lg[3][1], lg[0][1])}
     runs = {}
@@ -144,8 +152,8 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
     if schedule in ("paper", "converged"):
         stages = anneal.paper_schedule(L / N) if schedule == "paper" else [anneal.Stage(R_sm, M0)]
         mi = min_iter if schedule == "paper" else 1
-        for p in (0, 3):
-            s = s0.clone()
+        for p in paths:
+            s = starts[p].clone()
             t = time.perf_counter()
             hist = anneal.reconstruct(ctx[p], s, data, stages, max_iter=iters, min_iter=mi)
             torch.cuda.synchronize()
@@ -159,22 +167,27 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
             runs[p] = {"iterations": len(hist), "final_loss": hist[-1]["loss"], "stages": per,
                        "seconds": time.perf_counter() - t}
         last = stages[-1]
-        yard = {p: fp32_loss_at(finals[p], last) for p in (0, 3)}
+        yard = {p: fp32_loss_at(finals[p], last) for p in paths}
         for c in ctx.values():
             c.close()
         gaps = [abs(b["final_loss"] / a["final_loss"] - 1) if a["final_loss"] and b["final_loss"] else None
                 for a, b in zip(runs[0]["stages"], runs[3]["stages"])]
+        gaps_c = [abs(b["final_loss"] / a["final_loss"] - 1) if a["final_loss"] and b["final_loss"] else None
+                  for a, b in zip(runs[0]["stages"], runs["c"]["stages"])]
         return {"config": {"N": N, "L": L, "nsteps": nsteps, "schedule": schedule, "max_iter_per_stage": iters,
                            "stop": (f"decrease below 0.1% per iteration from iteration {mi} of a stage"
                                     if schedule == "paper" else f"decrease below {tol:g} per iteration"),
                            "stages": [(st.R_sm, st.M0) for st in stages]},
                 "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
-                "stage_final_loss_rel_gap": gaps,
+                "stage_final_loss_rel_gap": gaps, "stage_final_loss_rel_gap_fp32_control": gaps_c,
                 "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1),
                 "final_points_on_the_fp32_loss": {"fp32_path": yard[0], "bf16_path": yard[3],
-                                                  "rel_diff": abs(yard[3] / yard[0] - 1)}}
-    for p in (0, 3):
-        s = s0.clone()
+                                                  "rel_diff": abs(yard[3] / yard[0] - 1),
+                                                  "fp32_control_from_start_x(1+1e-6)": yard["c"],
+                                                  "control_rel_diff": abs(yard["c"] / yard[0] - 1)},
+                "fp32_control_path": runs["c"]}
+    for p in paths:
+        s = starts[p].clone()
         ctx[p].lbfgs_reset()
         t = time.perf_counter()
         losses = []
@@ -190,14 +203,17 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
         runs[p] = {"iterations": len(losses), "final_loss": losses[-1], "first_loss": losses[0],
                    "seconds": time.perf_counter() - t}
         finals[p] = s
-    yard = {p: fp32_loss_at(finals[p], anneal.Stage(R_sm, M0)) for p in (0, 3)}
+    yard = {p: fp32_loss_at(finals[p], anneal.Stage(R_sm, M0)) for p in paths}
     for c in ctx.values():
         c.close()
     return {"config": {"N": N, "L": L, "nsteps": nsteps, "R_sm": R_sm, "M0": M0, "iters": iters},
             "stage_rel_err_bf16_vs_fp32": stages_err, "fp32_path": runs[0], "bf16_path": runs[3],
+            "fp32_control_path": runs["c"],
             "final_loss_rel_diff": abs(runs[3]["final_loss"] / runs[0]["final_loss"] - 1),
             "final_points_on_the_fp32_loss": {"fp32_path": yard[0], "bf16_path": yard[3],
-                                              "rel_diff": abs(yard[3] / yard[0] - 1)}}
+                                              "rel_diff": abs(yard[3] / yard[0] - 1),
+                                              "fp32_control_from_start_x(1+1e-6)": yard["c"],
+                                              "control_rel_diff": abs(yard["c"] / yard[0] - 1)}}
 
 
 def main(argv=None):
