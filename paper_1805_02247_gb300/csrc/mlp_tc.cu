@@ -55,15 +55,7 @@ constexpr int TX = 2, TY = 4, TZ = 16, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HALO = 3 * HX * HY * HZ;
 
 // TMEM columns
-// TMEM columns. With the two-part TF32 operands the three products hi*hi,
-// hi*lo and lo*hi of a layer accumulate into three separate accumulators
-// (COL + 0, + stride, + 2 stride) that the epilogue adds: three independent MMA
-// chains instead of one chain of three times the length, whose K = 8 steps
-// would each wait for the previous one. Forward: D1 (64 wide), D2 (32 wide);
-// backward: D3 (64 wide), D4 (96 wide). 512 columns per CTA (one CTA per SM).
-constexpr uint32_t COL_D1 = 0, ST_D1 = 64, COL_D2 = 192, ST_D2 = 32;
-constexpr uint32_t COL_D3 = 0, ST_D3 = 64, COL_D4 = 192, ST_D4 = 96;
-constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t COL_D1 = 0, COL_D2 = 64, COL_D3 = 96, COL_D4 = 160;
 
 constexpr uint32_t VEC_MASS = 160;  // float offset of the mass-network weights in the vector block
 constexpr uint32_t SZ_VEC = 1920;    // b1[64], b2[32], w3[32], b3[4], mass network[301]: 4 * 461 rounded to 128 B
@@ -258,47 +250,22 @@ __device__ __forceinline__ float sigmoidf(float y) {
     return y >= 0.f ? 1.f / (1.f + expf(-y)) : expf(y) / (1.f + expf(y));
 }
 
-// issue the MMAs of one layer: D = A x B^T over K; TF32: hi*hi (+ hi*lo into
-// D + dstride, lo*hi into D + 2 dstride), BF16: one product
+// issue the MMAs of one layer: D (+)= A x B^T over K; TF32: hi*hi (+ hi*lo + lo*hi), BF16: one product
 template <bool BF>
 __device__ __forceinline__ void issue_layer(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
-                                            int K, int Rb, int nsplit, uint32_t dstride) {
+                                            int K, int Rb, int nsplit) {
     const int ksteps = K / Lay<BF>::KS;
     for (int ks = 0; ks < ksteps; ++ks) {
         const uint32_t ao = (uint32_t)ks * (TM * 32), bo = (uint32_t)ks * (Rb * 32);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
         if constexpr (BF) {
-            mma_bf16(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_bf16(TM, Rb), acc);
+            mma_bf16(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_bf16(TM, Rb), ks > 0 ? 1u : 0u);
         } else {
-            mma_tf32(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), acc);
+            mma_tf32(d, sdesc(a_hi + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), ks > 0 ? 1u : 0u);
             if (nsplit > 1) {
-                mma_tf32(d + dstride, sdesc(a_hi + ao), sdesc(b_lo + bo), idesc_tf32(TM, Rb), acc);
-                mma_tf32(d + 2 * dstride, sdesc(a_lo + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), acc);
+                mma_tf32(d, sdesc(a_hi + ao), sdesc(b_lo + bo), idesc_tf32(TM, Rb), 1u);
+                mma_tf32(d, sdesc(a_lo + ao), sdesc(b_hi + bo), idesc_tf32(TM, Rb), 1u);
             }
         }
-    }
-}
-
-// an accumulator's 16 (8) columns of this thread's row; with split products
-// the sum hi*hi + (hi*lo + lo*hi) of the three accumulators
-__device__ __forceinline__ void tmem_ld16_sum(uint32_t taddr, uint32_t stride, bool split, float* v) {
-    tmem_ld16(taddr, v);
-    if (split) {
-        float b[16], c[16];
-        tmem_ld16(taddr + stride, b);
-        tmem_ld16(taddr + 2 * stride, c);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += b[i] + c[i];
-    }
-}
-__device__ __forceinline__ void tmem_ld8_sum(uint32_t taddr, uint32_t stride, bool split, float* v) {
-    tmem_ld8(taddr, v);
-    if (split) {
-        float b[8], c[8];
-        tmem_ld8(taddr + stride, b);
-        tmem_ld8(taddr + 2 * stride, c);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] += b[i] + c[i];
     }
 }
 
@@ -394,8 +361,7 @@ __global__ void __launch_bounds__(NTW, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cb = warp >> 2;
     const int row = quad * 32 + lane;
-    constexpr uint32_t ncols = TMEM_COLS;
-    const bool split = !BF && nsplit > 1;
+    constexpr uint32_t ncols = 128;
     const int N = zm.N;
     const int64_t N3 = zm.N3;
 
@@ -453,11 +419,10 @@ __global__ void __launch_bounds__(NTW, 1)
                             mma_bf16(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_bf16(TM, N1), acc);
                         } else {
                             mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), acc);
-                            if (split) {
-                                mma_tf32(tmem + COL_D1 + ST_D1, zdesc(sA1h + ao), sdesc(sB1 + L::SZ_B1 + bo),
-                                         idesc_tf32(TM, N1), acc);
-                                mma_tf32(tmem + COL_D1 + 2 * ST_D1, zdesc(sA1l + ao), sdesc(sB1 + bo),
-                                         idesc_tf32(TM, N1), acc);
+                            if (nsplit > 1) {
+                                mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + L::SZ_B1 + bo),
+                                         idesc_tf32(TM, N1), 1u);
+                                mma_tf32(tmem + COL_D1, zdesc(sA1l + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), 1u);
                             }
                         }
                     }
@@ -469,7 +434,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 pa2 ^= 1;
                 tc_fence_after();
                 issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2),
-                                K2, N2, nsplit, ST_D2);
+                                K2, N2, nsplit);
                 mma_commit(bars + 3);
             }
             mma_commit(bars + 4);  // completes once every MMA issued above has
@@ -556,7 +521,7 @@ __global__ void __launch_bounds__(NTW, 1)
             // (2) relu(D1 + b1) -> A2 and the layer-1 mask
             {
                 float av[16];
-                tmem_ld16_sum(lane_base + COL_D1 + 16 * cb, ST_D1, split, av);
+                tmem_ld16(lane_base + COL_D1 + 16 * cb, av);
                 uint32_t mask1 = 0;
                 float z[16];
 #pragma unroll
@@ -585,7 +550,7 @@ __global__ void __launch_bounds__(NTW, 1)
             // (5) y = b3 + w3 . relu(D2 + b2) and the head
             {
                 float av[8];
-                tmem_ld8_sum(lane_base + COL_D2 + 8 * cb, ST_D2, split, av);
+                tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
                 uint32_t mask2 = 0;
                 float sacc = 0.f;
 #pragma unroll
@@ -674,8 +639,7 @@ __global__ void __launch_bounds__(NTW, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cb = warp >> 2;
     const int row = quad * 32 + lane;
-    constexpr uint32_t ncols = TMEM_COLS;
-    const bool split = !BF && nsplit > 1;
+    constexpr uint32_t ncols = 256;
     const int N = tm.N;
     const int64_t N3 = tm.N3;
 
@@ -717,7 +681,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 tc_fence_after();
                 if (!ctl.issue) continue;  // test hook: D3 never completes
                 issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3),
-                                K3, NB3, nsplit, ST_D3);
+                                K3, NB3, nsplit);
                 mma_commit(bars + 2);
                 if (!mbar_wait(bars + 1, pa4, ctl.wait_limit)) {
                     atomicExch(err, 1);
@@ -726,7 +690,7 @@ __global__ void __launch_bounds__(NTW, 1)
                 pa4 ^= 1;
                 tc_fence_after();
                 issue_layer<BF>(tmem + COL_D4, sA4h, sA4l, smem_u32(sm + B::S_B4), smem_u32(sm + B::S_B4 + L::SZ_B4),
-                                K4, NB4, nsplit, ST_D4);
+                                K4, NB4, nsplit);
                 mma_commit(bars + 3);
             }
             mma_commit(bars + 4);  // completes once every MMA issued above has
@@ -828,7 +792,7 @@ __global__ void __launch_bounds__(NTW, 1)
             // (2) A4 = g_a1 [a1 > 0]
             {
                 float av[16];
-                tmem_ld16_sum(lane_base + COL_D3 + 16 * cb, ST_D3, split, av);
+                tmem_ld16(lane_base + COL_D3 + 16 * cb, av);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) av[j] = ((m1_cur >> j) & 1u) ? av[j] : 0.f;
                 put8<BF>(A4h, A4l, row, 16 * cb, av);
@@ -856,7 +820,7 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
                     float av[8];
-                    tmem_ld8_sum(lane_base + COL_D4 + 24 * cb + 8 * h, ST_D4, split, av);
+                    tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, av);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int k = 24 * cb + 8 * h + j;
