@@ -483,6 +483,10 @@ struct Reg {
     // twiddles + transpose buffer (plain pass); + kept k-space tile (fused pass)
     static constexpr size_t smem_col() { return sizeof(float2) * (size_t)(N + N * kRC); }
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(N + 2 * N * kRC); }
+    // resident blocks of the fused x-pass: as many as 80 registers a thread and the
+    // shared memory of the kept k-space tile allow (3 at N = 256)
+    static constexpr int XB0 = 65536 / (T * 80), XB1 = (int)(232448 / smem());
+    static constexpr int XB = XB0 < XB1 ? (XB0 > 0 ? XB0 : 1) : (XB1 > 0 ? XB1 : 1);
 };
 
 // S[k1][n2][c]
@@ -604,7 +608,7 @@ __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out
 // x-pass with multipliers, same contract as k_x_fused. MODE 0: one input,
 // one output; 1: one input, several outputs; 2: several inputs, one output.
 template <class RG, int MODE>
-__global__ void __launch_bounds__(RG::T, 65536 / (RG::T * 128)) k_x_reg(XFused p, ColGeom geo,
+__global__ void __launch_bounds__(RG::T, RG::XB) k_x_reg(XFused p, ColGeom geo,
                                                                       const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int N = RG::N;
