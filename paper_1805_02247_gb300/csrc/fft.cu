@@ -267,6 +267,7 @@ struct ColGeom {
     int ncols;           // P
     int64_t es;          // element stride along the transform axis
     int64_t os;          // stride of the outer (tile row) index
+    int rev;             // register passes: visit the outer index from the last to the first
 };
 
 // Plain column pass (y-pass, or an x-pass without multipliers).
@@ -483,10 +484,14 @@ struct Reg {
     // twiddles + transpose buffer (plain pass); + kept k-space tile (fused pass)
     static constexpr size_t smem_col() { return sizeof(float2) * (size_t)(N + N * kRC); }
     static constexpr size_t smem() { return sizeof(float2) * (size_t)(N + 2 * N * kRC); }
-    // resident blocks of the fused x-pass: as many as 80 registers a thread and the
-    // shared memory of the kept k-space tile allow (3 at N = 256)
-    static constexpr int XB0 = 65536 / (T * 80), XB1 = (int)(232448 / smem());
-    static constexpr int XB = XB0 < XB1 ? (XB0 > 0 ? XB0 : 1) : (XB1 > 0 ? XB1 : 1);
+    // resident blocks of the fused x-pass: as many as 80 registers a thread (128 for
+    // the several-inputs variant, which spills at 80) and the shared memory of the
+    // kept k-space tile allow (3 and 2 at N = 256)
+    static constexpr int XB1 = (int)(232448 / smem());
+    static constexpr int xb(int regs) {
+        const int r = 65536 / (T * regs);
+        return (r < XB1 ? r : XB1) > 0 ? (r < XB1 ? r : XB1) : 1;
+    }
 };
 
 // S[k1][n2][c]
@@ -592,7 +597,8 @@ __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out
     const int c = threadIdx.x % kRC, g = threadIdx.x / kRC;
     const int c0 = blockIdx.x * kRC;
     const bool ok = c0 + c < geo.ncols;
-    const int64_t base = (int64_t)blockIdx.y * geo.os + c0 + c;
+    const int ob = geo.rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    const int64_t base = (int64_t)ob * geo.os + c0 + c;
     float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
     load_n2<RG>(v1, in, base, geo.es, ok, g);
     __syncthreads();  // twiddles
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out
 // x-pass with multipliers, same contract as k_x_fused. MODE 0: one input,
 // one output; 1: one input, several outputs; 2: several inputs, one output.
 template <class RG, int MODE>
-__global__ void __launch_bounds__(RG::T, RG::XB) k_x_reg(XFused p, ColGeom geo,
+__global__ void __launch_bounds__(RG::T, RG::xb(MODE == 2 ? 128 : 80)) k_x_reg(XFused p, ColGeom geo,
                                                                       const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int N = RG::N;
@@ -918,7 +924,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
 template <class RG>
 __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restrict__ in, float* __restrict__ out,
                                                              int64_t nrows, float scale, const float2* __restrict__ twM,
-                                                             const float2* __restrict__ twN) {
+                                                             const float2* __restrict__ twN, int rev) {
     using Z = ZReg<RG>;
     constexpr int M = Z::M, N = 2 * M, P = M + 1;
     extern __shared__ float2 sm[];
@@ -926,7 +932,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     float2* s_twN = s_twM + M;
     float2* A = s_twN + N;                    // [R][PITCH]: the P inputs, then z
     const int tid = threadIdx.x;
-    const int64_t row0 = (int64_t)blockIdx.x * Z::R;
+    const int64_t row0 = (int64_t)(rev ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x) * Z::R;
     const int rows = (int)min((int64_t)Z::R, nrows - row0);
     for (int t = tid; t < M; t += Z::T) s_twM[t] = twM[t];
     for (int t = tid; t < N; t += Z::T) s_twN[t] = twN[t];
@@ -1036,7 +1042,7 @@ int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
     bool done = with_zreg(c->N, [&](auto rg) {
         using Z = ZReg<decltype(rg)>;
         k_z_c2r_reg<decltype(rg)><<<nblocks(nrows, Z::R), Z::T, Z::smem(), c->stream>>>(in, out, nrows, scale,
-                                                                                       c->plan.twM, c->plan.twN);
+                                                                                       c->plan.twM, c->plan.twN, 1);
     });
     if (!done)
         k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
@@ -1045,6 +1051,11 @@ int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
 }
 
 int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
+    // The y-pass after a z r2c pass visits the x-planes last-written first (they
+    // are the ones still in L2), and so does the z c2r pass after an inverse
+    // y-pass (which runs in plane order); the passes are in place or row-local,
+    // so the order changes only which reads hit L2.
+    g.rev = (!inv && g.os == (int64_t)c->N * c->P) ? 1 : 0;
     bool done = with_reg(c->N, [&](auto rg) {
         using RG = decltype(rg);
         dim3 grid(nblocks(g.ncols, kRC), c->N);
