@@ -267,7 +267,6 @@ struct ColGeom {
     int ncols;           // P
     int64_t es;          // element stride along the transform axis
     int64_t os;          // stride of the outer (tile row) index
-    int rev;             // register passes: visit the outer index from the last to the first
 };
 
 // Plain column pass (y-pass, or an x-pass without multipliers).
@@ -597,8 +596,7 @@ __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out
     const int c = threadIdx.x % kRC, g = threadIdx.x / kRC;
     const int c0 = blockIdx.x * kRC;
     const bool ok = c0 + c < geo.ncols;
-    const int ob = geo.rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
-    const int64_t base = (int64_t)ob * geo.os + c0 + c;
+    const int64_t base = (int64_t)blockIdx.y * geo.os + c0 + c;
     float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
     load_n2<RG>(v1, in, base, geo.es, ok, g);
     __syncthreads();  // twiddles
@@ -924,7 +922,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
 template <class RG>
 __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restrict__ in, float* __restrict__ out,
                                                              int64_t nrows, float scale, const float2* __restrict__ twM,
-                                                             const float2* __restrict__ twN, int rev) {
+                                                             const float2* __restrict__ twN) {
     using Z = ZReg<RG>;
     constexpr int M = Z::M, N = 2 * M, P = M + 1;
     extern __shared__ float2 sm[];
@@ -932,7 +930,7 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
     float2* s_twN = s_twM + M;
     float2* A = s_twN + N;                    // [R][PITCH]: the P inputs, then z
     const int tid = threadIdx.x;
-    const int64_t row0 = (int64_t)(rev ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x) * Z::R;
+    const int64_t row0 = (int64_t)blockIdx.x * Z::R;
     const int rows = (int)min((int64_t)Z::R, nrows - row0);
     for (int t = tid; t < M; t += Z::T) s_twM[t] = twM[t];
     for (int t = tid; t < N; t += Z::T) s_twN[t] = twN[t];
@@ -1042,7 +1040,7 @@ int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
     bool done = with_zreg(c->N, [&](auto rg) {
         using Z = ZReg<decltype(rg)>;
         k_z_c2r_reg<decltype(rg)><<<nblocks(nrows, Z::R), Z::T, Z::smem(), c->stream>>>(in, out, nrows, scale,
-                                                                                       c->plan.twM, c->plan.twN, 1);
+                                                                                       c->plan.twM, c->plan.twN);
     });
     if (!done)
         k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
@@ -1051,11 +1049,6 @@ int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
 }
 
 int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
-    // The y-pass after a z r2c pass visits the x-planes last-written first (they
-    // are the ones still in L2), and so does the z c2r pass after an inverse
-    // y-pass (which runs in plane order); the passes are in place or row-local,
-    // so the order changes only which reads hit L2.
-    g.rev = (!inv && g.os == (int64_t)c->N * c->P) ? 1 : 0;
     bool done = with_reg(c->N, [&](auto rg) {
         using RG = decltype(rg);
         dim3 grid(nblocks(g.ncols, kRC), c->N);
