@@ -305,9 +305,6 @@ struct XFused {
     // all multipliers are MUL_ODD with j = their index and one scale and
     // weighting: the shared factor scale/k^2 is applied once per element
     int odd3;
-    // with odd3 and one input: write i k_x g X to out[0] and g X to out[1] only;
-    // the y and z components' i k_y, i k_z are applied by the y and z passes
-    int yz_defer;
 };
 
 __device__ __forceinline__ float2 apply_mul(const Mul& m, float2 v, int nx, int ny, int kz, int N,
@@ -588,10 +585,8 @@ __device__ __forceinline__ void load_k1(float2 (&v2)[RG::A2][RG::N2], const floa
 
 __device__ __forceinline__ void put(float2* d, float2 v, bool acc) { *d = acc ? cadd(*d, v) : v; }
 
-// Plain y- or x-pass; in-place safe (the tile is read before any write).
-// MULY: multiply the input by i k_y first (an inverse y-pass of the y component
-// of a deferred force; k_y = 2 pi n_y / N, zero at the Nyquist frequency).
-template <class RG, bool INV, bool MULY = false>
+// Plain y- or x-pass (no multiplier); in-place safe (the tile is read before any write).
+template <class RG, bool INV>
 __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out, ColGeom geo,
                                                      const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
@@ -604,15 +599,6 @@ __global__ void __launch_bounds__(RG::T) k_col_reg(const float2* in, float2* out
     const int64_t base = (int64_t)blockIdx.y * geo.os + c0 + c;
     float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
     load_n2<RG>(v1, in, base, geo.es, ok, g);
-    if constexpr (MULY)
-#pragma unroll
-        for (int a = 0; a < RG::A1; ++a)
-#pragma unroll
-            for (int n1 = 0; n1 < RG::N1; ++n1) {
-                const int n = RG::N2 * n1 + g + RG::G * a;  // frequency index of the element
-                const float ky = odd_k(1, 0, (2 * n <= RG::N) ? n : n - RG::N, 0, RG::N);
-                v1[a][n1] = make_float2(-ky * v1[a][n1].y, ky * v1[a][n1].x);
-            }
     __syncthreads();  // twiddles
     four_step_fwd<RG, INV>(v1, v2, S, s_tw, c, g);
     if (ok)
@@ -747,8 +733,7 @@ __global__ void __launch_bounds__(RG::T, RG::xb(MODE == 2 ? 128 : 80)) k_x_reg(X
                 for (int a = 0; a < RG::A2; ++a)
 #pragma unroll
                     for (int k2 = 0; k2 < RG::N2; ++k2) X[a][k2] = Kb[(a * RG::N2 + k2) * RG::T + threadIdx.x];
-                if (p.yz_defer) emit(X, p.out[1]);
-                else emit2(X, p.out[1], odd_k(1, 0, ny, kz, N), p.out[2], odd_k(2, 0, ny, kz, N));
+                emit2(X, p.out[1], odd_k(1, 0, ny, kz, N), p.out[2], odd_k(2, 0, ny, kz, N));
             } else {
 #pragma unroll 1
                 for (int o = 0; o < p.nout; ++o) {
@@ -934,12 +919,10 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
     }
 }
 
-// zodd: multiply the half-complex input row by i k_z first (k_z = 2 pi kz / N,
-// zero at kz = N/2), the z component of a deferred force
 template <class RG>
 __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restrict__ in, float* __restrict__ out,
                                                              int64_t nrows, float scale, const float2* __restrict__ twM,
-                                                             const float2* __restrict__ twN, int zodd) {
+                                                             const float2* __restrict__ twN) {
     using Z = ZReg<RG>;
     constexpr int M = Z::M, N = 2 * M, P = M + 1;
     extern __shared__ float2 sm[];
@@ -963,10 +946,6 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_c2r_reg(const float2* __restr
 #pragma unroll
         for (int q = 0; q < LD; ++q) {
             const int t = tid + q * Z::T, r = t / P, k = t - r * P;
-            if (zodd) {
-                const float kz = odd_k(2, 0, 0, k, N);
-                v[q] = make_float2(-kz * v[q].y, kz * v[q].x);
-            }
             if (t < Z::R * P) A[r * Z::PITCH + k] = v[q];
         }
     }
@@ -1055,16 +1034,14 @@ int launch_z_r2c(pmr_ctx* c, const float* in, float2* out) {
     return check_launch(c, "z_r2c");
 }
 
-// zodd (register path only): multiply by i k_z before the inverse
-int launch_z_c2r(pmr_ctx* c, const float2* in, float* out, int zodd = 0) {
+int launch_z_c2r(pmr_ctx* c, const float2* in, float* out) {
     int64_t nrows = (int64_t)c->N * c->N;
     float scale = (float)(1.0 / ((double)c->N * c->N));
     bool done = with_zreg(c->N, [&](auto rg) {
         using Z = ZReg<decltype(rg)>;
         k_z_c2r_reg<decltype(rg)><<<nblocks(nrows, Z::R), Z::T, Z::smem(), c->stream>>>(in, out, nrows, scale,
-                                                                                       c->plan.twM, c->plan.twN, zodd);
+                                                                                       c->plan.twM, c->plan.twN);
     });
-    if (!done && zodd) return fail(c, PMR_EINVAL, "z pass with i k_z: register path only");
     if (!done)
         k_z_c2r<<<nblocks(nrows, kRows), kThreads, smem_z(c->N, true), c->stream>>>(in, out, nrows, c->N, scale,
                                                                                    c->plan.rM, c->plan.twM, c->plan.twN);
@@ -1083,18 +1060,6 @@ int launch_col(pmr_ctx* c, const float2* in, float2* out, ColGeom g, bool inv) {
         if (inv) k_col<true><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
         else k_col<false><<<grid, kThreads, smem_col(c->N, 2), c->stream>>>(in, out, g, c->plan.rN, c->plan.twN);
     }
-    return check_launch(c, "col_pass");
-}
-
-// inverse y-pass with i k_y applied to its input (register path only)
-int launch_col_iky(pmr_ctx* c, const float2* in, float2* out) {
-    const ColGeom g = geom_y(c);
-    bool done = with_reg(c->N, [&](auto rg) {
-        using RG = decltype(rg);
-        dim3 grid(nblocks(g.ncols, kRC), c->N);
-        k_col_reg<RG, true, true><<<grid, RG::T, RG::smem_col(), c->stream>>>(in, out, g, c->plan.twN);
-    });
-    if (!done) return fail(c, PMR_EINVAL, "y pass with i k_y: register path only");
     return check_launch(c, "col_pass");
 }
 
@@ -1191,8 +1156,7 @@ int fft_init(pmr_ctx* c) {
     with_reg(N, [&](auto rg) {
         using RG = decltype(rg);
         for (const void* fn : {(const void*)k_col_reg<RG, true>, (const void*)k_col_reg<RG, false>,
-                               (const void*)k_col_reg<RG, true, true>, (const void*)k_x_reg<RG, 0>,
-                               (const void*)k_x_reg<RG, 1>, (const void*)k_x_reg<RG, 2>})
+                               (const void*)k_x_reg<RG, 0>, (const void*)k_x_reg<RG, 1>, (const void*)k_x_reg<RG, 2>})
             if (rc == PMR_OK) rc = raise_smem_limit(c, fn, RG::smem());
     });
     PMR_TRY(rc);
@@ -1217,43 +1181,12 @@ int fft_c2r(pmr_ctx* c, const float2* in, float* out, float2* work) {
     return launch_z_c2r(c, work, out);
 }
 
-namespace {
-// the three inverse transforms of a gradient (force-like) multiplier set
-// i k_j g in k space, after an x-pass that wrote i k_x g X to outs[0] and the
-// shared g X to outs[1]: F_y = y^-1(i k_y g X) then z^-1; F_z = y^-1(g X) then
-// z^-1 of i k_z times it (the z pass applies it); F_x as usual. The two y
-// passes read one array (the second mostly from L2) instead of two.
-int odd3_inverse(pmr_ctx* c, float2* const* outs, float* const* out) {
-    PMR_TRY(launch_col_iky(c, outs[1], outs[2]));
-    PMR_TRY(launch_col(c, outs[1], outs[1], geom_y(c), true));
-    PMR_TRY(launch_z_c2r(c, outs[1], out[2], 1));
-    PMR_TRY(launch_z_c2r(c, outs[2], out[1]));
-    PMR_TRY(launch_col(c, outs[0], outs[0], geom_y(c), true));
-    return launch_z_c2r(c, outs[0], out[0]);
-}
-
-bool deferrable(const pmr_ctx* c, const Mul* mul, int nout) {
-    if (nout != 3 || !with_reg(c->N, [](auto) {}) || !with_zreg(c->N, [](auto) {})) return false;
-    for (int o = 0; o < 3; ++o)
-        if (mul[o].type != MUL_ODD || mul[o].j != o || mul[o].scale != mul[0].scale ||
-            mul[o].weighted != mul[0].weighted)
-            return false;
-    return true;
-}
-}  // namespace
-
 int conv_1toN(pmr_ctx* c, const float* in, float* const* out, const Mul* mul, int nout) {
     float2* outs[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
     PMR_TRY(launch_z_r2c(c, in, c->cA));
     PMR_TRY(launch_col(c, c->cA, c->cA, geom_y(c), false));
     const float2* ins[1] = {c->cA};
-    XFused p = make_x(ins, 1, outs, nout, mul, nout, true, true, c);
-    if (deferrable(c, mul, nout)) {
-        p.yz_defer = 1;
-        PMR_TRY(launch_x_fused(c, p));
-        return odd3_inverse(c, outs, out);
-    }
-    PMR_TRY(launch_x_fused(c, p));
+    PMR_TRY(launch_x_fused(c, make_x(ins, 1, outs, nout, mul, nout, true, true, c)));
     // last-written output first: more of it is still in L2
     for (int j = nout - 1; j >= 0; --j) {
         PMR_TRY(launch_col(c, outs[j], outs[j], geom_y(c), true));
@@ -1279,13 +1212,7 @@ int conv_Nto1(pmr_ctx* c, const float* const* in, const Mul* mul, int nin, float
 int k_to_real(pmr_ctx* c, const float2* in, float* const* out, const Mul* mul, int nout) {
     float2* outs[3] = {c->c3, c->c3 + c->NH, c->c3 + 2 * c->NH};
     const float2* ins[1] = {in};
-    XFused p = make_x(ins, 1, outs, nout, mul, nout, false, true, c);
-    if (deferrable(c, mul, nout)) {
-        p.yz_defer = 1;
-        PMR_TRY(launch_x_fused(c, p));
-        return odd3_inverse(c, outs, out);
-    }
-    PMR_TRY(launch_x_fused(c, p));
+    PMR_TRY(launch_x_fused(c, make_x(ins, 1, outs, nout, mul, nout, false, true, c)));
     for (int j = 0; j < nout; ++j) {
         PMR_TRY(launch_col(c, outs[j], outs[j], geom_y(c), true));
         PMR_TRY(launch_z_c2r(c, outs[j], out[j]));
