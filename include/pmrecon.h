@@ -59,7 +59,12 @@ typedef struct pmr_config {
     double omega_m;     /* Sec. 3: 0.3175 (flat LCDM) */
     double sigma8;      /* linear amplitude of the BBKS spectrum */
     double gamma_bbks;  /* BBKS shape parameter */
-    double R_feat[3];   /* Gaussian scales of the three network input fields, Mpc/h (Sec. 2.2) */
+    double R_feat[3];   /* Gaussian scales of the three smoothed density fields, Mpc/h (Sec. 2.2);
+                           0 = the unsmoothed density */
+    float feat_mix[9];  /* row-major 3x3 C: the network's input fields are f_i = sum_j C_ij delta_Rj
+                           (Sec. 2.2 uses delta_0, delta_R1, delta_R1 - delta_R2: R_feat = {0, R1, R2},
+                           C = {1,0,0, 0,1,0, 0,1,-1}); identity by default. pmr_create folds C into the
+                           first-layer weights (and the mass network's, head == 1), so it costs nothing */
     double R_M;         /* smoothing of model and data mass inside the log, Mpc/h (Sec. 4.2: 3) */
     double sigma_N2;    /* noise variance of Eq. (loss) (Sec. 5.3: 0.25) */
     double mu_N;        /* offset of Eq. (loss) */
@@ -92,7 +97,7 @@ typedef struct pmr_anneal {
 typedef struct pmr_ctx pmr_ctx;
 
 /* Fills *cfg with the defaults: N=32, L=100, nsteps=3, a0=0.1, omega_m=0.3175,
- * sigma8=0.8, Gamma=0.21, R_feat={1,2,4}, R_M=3, sigma_N2=0.25, mu_N=0,
+ * sigma8=0.8, Gamma=0.21, R_feat={1,2,4}, feat_mix=identity, R_M=3, sigma_N2=0.25, mu_N=0,
  * f_eff=1, M_scale=1e12, lbfgs_m=10, lbfgs_tol=1e-3, nn_path=0, head=0,
  * lpt_order=1. */
 void pmr_default_config(pmr_config* cfg);
@@ -144,15 +149,18 @@ int pm_forward(pmr_ctx* ctx, const void* s_k, float* delta_out);
  * recomputed from the stored positions. Returns PMR_ESTATE without a forward. */
 int pm_adjoint(pmr_ctx* ctx, const float* grad_delta, void* grad_s_k);
 
-/* Network halo-mass map (Sec. 2): delta -> three Gaussian-smoothed fields ->
- * per-voxel 81-50-30-1 ReLU network on the 3x3x3 neighbourhood -> M_scale *
- * softplus(y), or with head == 1 M_scale * logistic(y, a) * NNm (Sec. 2.1).
- * an: only a_logistic is read (NULL means a = 3). delta, mass_out: float32 meshes. */
-int nn_halo_map(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, float* mass_out);
+/* Network halo-mass map (Sec. 2): delta -> three Gaussian-smoothed fields,
+ * mixed by feat_mix -> per-voxel 81-50-30-1 ReLU network on the 3x3x3
+ * neighbourhood -> M_scale * softplus(y), or with head == 1 M_scale *
+ * logistic(y, a) * NNm (Sec. 2.1). delta, mass_out: float32 meshes.
+ * an: only a_logistic is read (NULL means a = 3). */
+int nn_halo_map(pmr_ctx* ctx, const float* delta, float* mass_out, const pmr_anneal* an);
 
-/* Adjoint of nn_halo_map at delta: grad_delta = (dM/d delta)^T grad_mass. */
-int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const pmr_anneal* an, const float* grad_mass,
-                        float* grad_delta);
+/* Adjoint of nn_halo_map at delta: grad_delta = (dM/d delta)^T grad_mass.
+ * The network's gradient depends on where it is taken, so delta is an
+ * argument (the call recomputes the forward at delta first). */
+int nn_halo_map_adjoint(pmr_ctx* ctx, const float* delta, const float* grad_mass, float* grad_delta,
+                        const pmr_anneal* an);
 
 /* Loss of Eq. (loss) at s(k) and its gradient (Sec. 5.1-5.2).
  * data_mass: float32 mesh of the observed halo mass M^data (unsmoothed).

@@ -14,7 +14,10 @@ Readings (the paper is silent or ambiguous on these):
 * mu_N defaults to 0 (the mass-dependent offsets of Fig. noise are not printed).
 * The three network input fields are the final overdensity smoothed with
   Gaussians of R_feat = (1, 2, 4) Mpc/h (Sec. 2.2 uses multi-scale smoothed
-  density; the scales are those of the synthetic workload).
+  density; the scales are those of the synthetic workload), optionally mixed
+  by a 3x3 matrix C, f_i = sum_j C_ij delta_Rj: the paper's own set delta_0,
+  delta_R1, delta_R1 - delta_R2 is R_feat = (0, R1, R2) with C rows (1, 0, 0),
+  (0, 1, 0), (0, 1, -1).
 * The prior is 1/2 sum over the half array of w_k |s_k|^2 / P~(k), k != 0 (pm.py).
 """
 from __future__ import annotations
@@ -28,7 +31,8 @@ from . import nn, pm
 
 @dataclass(frozen=True)
 class LossSetup:
-    R_feat: tuple = (1.0, 2.0, 4.0)  # Mpc/h
+    R_feat: tuple = (1.0, 2.0, 4.0)  # Mpc/h; 0 = unsmoothed
+    feat_mix: tuple | None = None  # row-major 3x3 C, f_i = sum_j C_ij delta_Rj; None = identity
     R_M: float = 3.0  # Mpc/h
     sigma_N2: float = 0.25
     mu_N: float = 0.0
@@ -62,11 +66,18 @@ def _head_backward(gM, f, weights, ls: LossSetup, a: float):
 
 def features(delta: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarray:
     cell = pms.L / pms.N
-    return np.stack([pm.smooth(delta, R / cell) for R in ls.R_feat])
+    smoothed = np.stack([pm.smooth(delta, R / cell) for R in ls.R_feat])
+    if ls.feat_mix is None:
+        return smoothed
+    C = np.asarray(ls.feat_mix, np.float64).reshape(3, 3)
+    return np.einsum("ij,jxyz->ixyz", C, smoothed)
 
 
 def features_T(g_fields: np.ndarray, pms: pm.PMSetup, ls: LossSetup) -> np.ndarray:
     cell = pms.L / pms.N
+    if ls.feat_mix is not None:
+        C = np.asarray(ls.feat_mix, np.float64).reshape(3, 3)
+        g_fields = np.einsum("ij,ixyz->jxyz", C, g_fields)  # transpose of the mix
     return sum(pm.smooth(g_fields[c], R / cell) for c, R in enumerate(ls.R_feat))
 
 

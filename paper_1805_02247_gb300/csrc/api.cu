@@ -67,6 +67,36 @@ int n_weights(const pmr_config* cfg) { return 5661 + (cfg->head == 1 ? kMassWeig
 
 float logistic_a(const pmr_anneal* an) { return an ? (float)an->a_logistic : 3.0f; }
 
+// The network sees f_i = sum_j C_ij delta_Rj (Sec. 2.2's mixed features) but
+// the kernels read the three smoothed fields delta_Rj: W1'[h][j*27 + o] =
+// sum_i W1[h][i*27 + o] C_ij, and the mass network's (head 1, on the voxel's
+// own three features) Wm1'[k][j] = sum_i Wm1[k][i] C_ij. Products in double.
+void fold_feature_mix(const pmr_config* cfg, float* W) {
+    const float* C = cfg->feat_mix;
+    bool ident = true;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) ident &= C[3 * i + j] == (i == j ? 1.0f : 0.0f);
+    if (ident) return;
+    for (int h = 0; h < 50; ++h)
+        for (int o = 0; o < 27; ++o) {
+            double src[3], dst[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < 3; ++i) src[i] = W[h * 81 + i * 27 + o];
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) dst[j] += src[i] * (double)C[3 * i + j];
+            for (int j = 0; j < 3; ++j) W[h * 81 + j * 27 + o] = (float)dst[j];
+        }
+    if (cfg->head == 1) {
+        float* Wm1 = W + 5661;
+        for (int k = 0; k < 20; ++k) {
+            double src[3], dst[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < 3; ++i) src[i] = Wm1[3 * k + i];
+            for (int j = 0; j < 3; ++j)
+                for (int i = 0; i < 3; ++i) dst[j] += src[i] * (double)C[3 * i + j];
+            for (int j = 0; j < 3; ++j) Wm1[3 * k + j] = (float)dst[j];
+        }
+    }
+}
+
 const char* validate(const pmr_config* cfg) {
     if (!cfg) return "config is NULL";
     const int N = cfg->N;
@@ -78,6 +108,8 @@ const char* validate(const pmr_config* cfg) {
     if (!(cfg->sigma8 > 0) || !(cfg->gamma_bbks > 0)) return "sigma8 and gamma_bbks must be > 0";
     for (int j = 0; j < 3; ++j)
         if (!(cfg->R_feat[j] >= 0)) return "R_feat must be >= 0";
+    for (int j = 0; j < 9; ++j)
+        if (!std::isfinite(cfg->feat_mix[j])) return "feat_mix must be finite";
     if (!(cfg->R_M >= 0)) return "R_M must be >= 0";
     if (!(cfg->sigma_N2 > 0)) return "sigma_N2 must be > 0";
     if (!(cfg->M_scale > 0)) return "M_scale must be > 0";
@@ -226,6 +258,7 @@ void pmr_default_config(pmr_config* cfg) {
     cfg->R_feat[0] = 1.0;
     cfg->R_feat[1] = 2.0;
     cfg->R_feat[2] = 4.0;
+    for (int j = 0; j < 9; ++j) cfg->feat_mix[j] = (j % 4 == 0) ? 1.0f : 0.0f;
     cfg->R_M = 3.0;
     cfg->sigma_N2 = 0.25;
     cfg->mu_N = 0.0;
@@ -310,12 +343,13 @@ int pmr_create(const pmr_config* cfg, const float* nn_weights_dev, void* stream,
     if (rc == PMR_OK) {
         const int nw = n_weights(cfg);
         c->W_host.assign(kNW, 0.0f);
-        rc = check_cuda(c, cudaMemset(c->W, 0, sizeof(float) * kNW), "weights");
-        if (rc == PMR_OK)
-            rc = check_cuda(c, cudaMemcpy(c->W, nn_weights_dev, sizeof(float) * nw, cudaMemcpyDeviceToDevice), "weights");
-        if (rc == PMR_OK)
-            rc = check_cuda(c, cudaMemcpy(c->W_host.data(), nn_weights_dev, sizeof(float) * nw, cudaMemcpyDeviceToHost),
+        rc = check_cuda(c, cudaMemcpy(c->W_host.data(), nn_weights_dev, sizeof(float) * nw, cudaMemcpyDeviceToHost),
+                        "weights");
+        if (rc == PMR_OK) {
+            fold_feature_mix(cfg, c->W_host.data());
+            rc = check_cuda(c, cudaMemcpy(c->W, c->W_host.data(), sizeof(float) * kNW, cudaMemcpyHostToDevice),
                             "weights");
+        }
         if (rc == PMR_OK) rc = mlp_tc_init(c);
     }
     if (rc != PMR_OK) {
@@ -370,15 +404,15 @@ int pm_adjoint(pmr_ctx* c, const float* grad_delta, void* grad_s_k) {
     return pm_adjoint_impl(c, grad_delta, (float2*)grad_s_k);
 }
 
-int nn_halo_map(pmr_ctx* c, const float* delta, const pmr_anneal* an, float* mass_out) {
+int nn_halo_map(pmr_ctx* c, const float* delta, float* mass_out, const pmr_anneal* an) {
     PMR_TRY(check_ctx(c));
     if (!delta || !mass_out) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(nn_features(c, delta));
     return mlp_forward(c, c->feat, mass_out, logistic_a(an));
 }
 
-int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const pmr_anneal* an, const float* grad_mass,
-                        float* grad_delta) {
+int nn_halo_map_adjoint(pmr_ctx* c, const float* delta, const float* grad_mass, float* grad_delta,
+                        const pmr_anneal* an) {
     PMR_TRY(check_ctx(c));
     if (!delta || !grad_mass || !grad_delta) return fail(c, PMR_EINVAL, "NULL argument");
     PMR_TRY(nn_features(c, delta));

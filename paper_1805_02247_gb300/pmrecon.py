@@ -30,7 +30,7 @@ class Config(ctypes.Structure):
     _fields_ = [
         ("N", ctypes.c_int), ("L", ctypes.c_double), ("nsteps", ctypes.c_int), ("a0", ctypes.c_double),
         ("omega_m", ctypes.c_double), ("sigma8", ctypes.c_double), ("gamma_bbks", ctypes.c_double),
-        ("R_feat", ctypes.c_double * 3), ("R_M", ctypes.c_double), ("sigma_N2", ctypes.c_double),
+        ("R_feat", ctypes.c_double * 3), ("feat_mix", ctypes.c_float * 9), ("R_M", ctypes.c_double), ("sigma_N2", ctypes.c_double),
         ("mu_N", ctypes.c_double), ("f_eff", ctypes.c_double), ("M_scale", ctypes.c_double),
         ("lbfgs_m", ctypes.c_int), ("lbfgs_tol", ctypes.c_double), ("nn_path", ctypes.c_int), ("head", ctypes.c_int),
         ("lpt_order", ctypes.c_int),
@@ -109,6 +109,8 @@ def default_config(**overrides) -> Config:
     for k, v in overrides.items():
         if k == "R_feat":
             cfg.R_feat = (ctypes.c_double * 3)(*v)
+        elif k == "feat_mix":
+            cfg.feat_mix = (ctypes.c_float * 9)(*[float(x) for x in v])
         else:
             setattr(cfg, k, v)
     return cfg
@@ -197,15 +199,15 @@ class Context:
         """Halo-mass map of the final density; a = logistic sharpness (two-network head only)."""
         m = self.mesh() if out is None else out
         an = Anneal(0.0, 0.0, a)
-        self._check(self._lib.nn_halo_map(self._h, _ptr(delta), ctypes.byref(an), _ptr(m)))
+        self._check(self._lib.nn_halo_map(self._h, _ptr(delta), _ptr(m), ctypes.byref(an)))
         return m
 
     def nn_halo_map_adjoint(self, delta: torch.Tensor, grad_mass: torch.Tensor, a: float = 3.0,
                             out=None) -> torch.Tensor:
         g = self.mesh() if out is None else out
         an = Anneal(0.0, 0.0, a)
-        self._check(self._lib.nn_halo_map_adjoint(self._h, _ptr(delta), ctypes.byref(an),
-                                                  _ptr(grad_mass), _ptr(g)))
+        self._check(self._lib.nn_halo_map_adjoint(self._h, _ptr(delta), _ptr(grad_mass), _ptr(g),
+                                                  ctypes.byref(an)))
         return g
 
     def loss_and_grad(self, s, data, R_sm: float, M0: float, out=None, readback: bool = True,

@@ -376,3 +376,30 @@ def test_loss_into_a_device_buffer_without_a_host_read():
     parts, g2 = ctx.loss_and_grad(s_dev, d_dev, R_sm, M0)
     assert tuple(loss_dev.cpu().tolist()) == parts
     assert torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("head", [0, 1])
+def test_paper_feature_set_through_feat_mix(head):
+    # Sec. 2.2's input fields delta_0, delta_R1, delta_R1 - delta_R2 as
+    # R_feat = (0, R1, R2) and feat_mix C: folded into the first-layer weights by
+    # pmr_create, against the oracle forming the mixed fields explicitly
+    mix = (1, 0, 0, 0, 1, 0, 0, 1, -1)
+    N, L, nsteps, R_sm, M0 = 16, 50.0, 2, 4.0, 1e11
+    two = head == 1
+    ctx, _ = context(N=N, L=L, nsteps=nsteps, head=head, R_feat=(0.0, 3.0, 6.0), feat_mix=mix)
+    setup = opm.PMSetup(N=N, L=L, nsteps=nsteps)
+    ls = oloss.LossSetup(R_feat=(0.0, 3.0, 6.0), feat_mix=mix, head="two_net" if two else "softplus")
+    w = synth.two_net_weights(1) if two else synth.xavier_weights(1)
+    delta = f32(2.0 * synth.gaussian_vector((N, N, N), seed=81))
+    M = to_np(ctx.nn_halo_map(to_dev(delta), 2.0))
+    assert rel_l2(M, oloss.nn_halo_map(delta, w, setup, ls, 2.0)) <= FIELD_TOL
+    gM = f32(synth.gaussian_vector((N, N, N), seed=82))
+    gd = to_np(ctx.nn_halo_map_adjoint(to_dev(delta), to_dev(gM), 2.0))
+    assert rel_l2(gd, oloss.nn_halo_map_T(gM, delta, w, setup, ls, 2.0)) <= GRAD_TOL
+    _, s = _problem(N, L, nsteps, amp=np.sqrt(0.1))
+    data = f32(oloss.synthetic_data(f32(synth.white_noise(N, 2)), f32(synth.scatter_noise(N, 2)), w, setup, ls,
+                                    a=2.0))
+    parts, g = ctx.loss_and_grad(to_dev(s), to_dev(data), R_sm, M0, a=2.0)
+    want, gwant = oloss.loss_and_grad(s, data, w, setup, ls, oloss.Anneal(R_sm=R_sm, M0=M0, a=2.0))
+    assert parts[0] == pytest.approx(want["loss"], rel=FIELD_TOL)
+    assert rel_l2(to_np(g), gwant) <= GRAD_TOL

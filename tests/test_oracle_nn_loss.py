@@ -308,3 +308,36 @@ def test_sampled_network_equals_full_network_at_those_voxels():
     np.add.at(gM, (vox[:, 0], vox[:, 1], vox[:, 2]), vals)
     dense = nn.mlp_backward(gM, f, w, 1e12)
     assert np.allclose(nn.mlp_backward_at(vals, vox, f, w, 1e12), dense, rtol=1e-12, atol=1e-12 * np.abs(dense).max())
+
+
+PAPER_MIX = (1, 0, 0, 0, 1, 0, 0, 1, -1)  # delta_0, delta_R1, delta_R1 - delta_R2 (Sec. 2.2)
+
+
+def test_paper_feature_set_by_explicit_smoothing():
+    # the mixed features with R_feat = (0, R1, R2): the unsmoothed density, its
+    # R1 smoothing, and the difference of the R1 and R2 smoothings, each formed here
+    # straight from a Gaussian filter written out in this test
+    N, L, R1, R2 = 16, 50.0, 3.0, 6.0
+    setup = pm.PMSetup(N=N, L=L, nsteps=1)
+    ls = loss.LossSetup(R_feat=(0.0, R1, R2), feat_mix=PAPER_MIX)
+    delta = synth.gaussian_vector((N, N, N), seed=9).astype(np.float64)
+    kf = 2 * np.pi * np.fft.fftfreq(N) * N / L   # h/Mpc per mode along each axis
+    kz = 2 * np.pi * np.arange(N // 2 + 1) / L
+    k2 = kf[:, None, None] ** 2 + kf[None, :, None] ** 2 + kz[None, None, :] ** 2
+    D = np.fft.rfftn(delta)
+    sm = lambda R: np.fft.irfftn(D * np.exp(-0.5 * k2 * R * R), s=(N, N, N), axes=(0, 1, 2))
+    f = loss.features(delta, setup, ls)
+    assert np.allclose(f[0], delta, atol=1e-12)
+    assert np.allclose(f[1], sm(R1), atol=1e-12)
+    assert np.allclose(f[2], sm(R1) - sm(R2), atol=1e-12)
+
+
+def test_mixed_features_adjoint_by_dot_product():
+    N, L = 16, 50.0
+    setup = pm.PMSetup(N=N, L=L, nsteps=1)
+    ls = loss.LossSetup(R_feat=(0.0, 3.0, 6.0), feat_mix=(0.5, -1.0, 2.0, 0.0, 1.5, 0.25, 1.0, 1.0, -3.0))
+    x = synth.gaussian_vector((N, N, N), seed=10).astype(np.float64)
+    y = synth.gaussian_vector((3, N, N, N), seed=11).astype(np.float64)
+    lhs = float(np.sum(loss.features(x, setup, ls) * y))
+    rhs = float(np.sum(x * loss.features_T(y, setup, ls)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
