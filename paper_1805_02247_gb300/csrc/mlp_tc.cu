@@ -813,10 +813,19 @@ __global__ void __launch_bounds__(NTW, 1)
             ph4 ^= 1;
             if (!ok) break;
             tc_fence_after();
-            // (5) g_v: 24 columns per thread -> gvs[k][row] (k < 81; rows outside the mesh stay 0)
+            // (5) g_v, folded over the z offset in registers: a thread holds 24
+            //     columns = 8 whole (c, ox, oy) triples over oz (k = 3 q + oz + 1), and
+            //     the voxels z - 1, z + 1 of its row are the neighbouring lanes of its
+            //     16-lane group, so T_q(hz) = g_v[q, oz=-1](hz) + g_v[q, 0](hz - 1) +
+            //     g_v[q, 1](hz - 2) (box z index hz = lz + 1; lane 0 also gives hz = 0,
+            //     lane 15 hz = 17) needs two shuffles per triple. T goes to shared
+            //     memory as Ts[q][lx][ly][hz] (27 x 2 x 4 x 18; rows outside the mesh give 0).
             {
                 const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
                 const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
+                float* Ts = gvs;
+                const int cell = (lx * TY + ly) * HZ;
+                float trip[8][3];  // [triple][oz + 1]
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
                     float av[8];
@@ -824,16 +833,34 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int k = 24 * cb + 8 * h + j;
-                        float v = av[j];
-                        if (TWO_NET && k < NI && k % 27 == 13) v += gcen[(slot * 3 + k / 27) * TM + row];
-                        if (k < NI) gvs[k * TM + row] = in ? v : 0.f;
+                        float v = in ? av[j] : 0.f;
+                        if (TWO_NET && k < NI && k % 27 == 13 && in) v += gcen[(slot * 3 + k / 27) * TM + row];
+                        av[j] = v;
+                    }
+                    // a load of 8 columns is not a whole number of triples: regroup
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) trip[(8 * h + j) / 3][(8 * h + j) % 3] = av[j];
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int q = 8 * cb + t;  // triple: c * 9 + (ox + 1) * 3 + (oy + 1)
+                    const float gm1 = trip[t][0], g0 = trip[t][1], gp1 = trip[t][2];
+                    float from_up = __shfl_down_sync(0xffffffffu, gm1, 1, 16);  // g_v[-1](lz + 1)
+                    float from_dn = __shfl_up_sync(0xffffffffu, gp1, 1, 16);    // g_v[+1](lz - 1)
+                    if (lz == 15) from_up = 0.f;
+                    if (lz == 0) from_dn = 0.f;
+                    if (q < 27) {
+                        float* Tq = Ts + q * (TX * TY * HZ) + cell;
+                        Tq[lz + 1] = from_up + g0 + from_dn;
+                        if (lz == 0) Tq[0] = gm1;
+                        if (lz == 15) Tq[17] = gp1;
                     }
                 }
             }
             tc_fence_before();
             nbar_sync(NT);
-            // (6) box sums: field c at box cell (hx, hy, hz) collects g_v[c, o] of the
-            //     tile voxel at box cell - 1 - o, offsets o in a fixed order
+            // (6) box sums: field c at box cell (hx, hy, hz) collects T of the triples
+            //     (c, ox, oy) at tile (lx, ly) = (hx - 1 - ox, hy - 1 - oy), in a fixed order
             for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
                 const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
                 const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
@@ -846,13 +873,8 @@ __global__ void __launch_bounds__(NTW, 1)
                     for (int oy = -1; oy <= 1; ++oy) {
                         const int ly = hy - 1 - oy;
                         if (ly < 0 || ly >= TY) continue;
-#pragma unroll
-                        for (int oz = -1; oz <= 1; ++oz) {
-                            const int lz = hz - 1 - oz;
-                            if (lz < 0 || lz >= TZ) continue;
-                            const int k = c * 27 + (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
-                            acc += gvs[k * TM + (lx * TY + ly) * TZ + lz];
-                        }
+                        const int q = c * 9 + (ox + 1) * 3 + (oy + 1);
+                        acc += gvs[q * (TX * TY * HZ) + (lx * TY + ly) * HZ + hz];
                     }
                 }
                 gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
