@@ -32,6 +32,7 @@
 // waits (bounded) for its MMAs, frees its TMEM and returns. The host reports
 // the flag as PMR_ETIMEOUT and clears it.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 #include "common.cuh"
@@ -453,27 +454,57 @@ __global__ void __launch_bounds__(NTW, 1)
             y = (int)line - x * N;
         };
         // this thread's build tasks u = tid + NT m: image row i = u % ZR, chunk q = u / ZR,
-        // EC input columns k = q EC + e (k >= 27: padding, zero)
+        // EC input columns k = q EC + e (k >= 27: padding, zero). Fixed over the tiles:
+        // zoff = i - 1 (kNoTask: no task) and, per column, the input's offset from the
+        // line's centre element, c N^3 + ox N^2 + oy N (kNoTask: padding). Indices fit in
+        // 32 bits (3 N^3 < 2^31 for N <= 512). The bf16 image's 8 columns a chunk would
+        // not fit in registers: there the offsets are formed per tile.
         constexpr int EC = L::EC;
+        constexpr int kNoTask = INT_MIN;
+        constexpr bool KEEP = !BF;
+        auto col_off = [&](int m, int e) {
+            const int k = ((tid + NT * m) / ZR) * EC + e;
+            return k < 27 ? (k / 9) * (int)N3 + ((k / 3) % 3 - 1) * N * N + (k % 3 - 1) * N : kNoTask;
+        };
+        int zoff[F::TPT], koff[F::TPT][KEEP ? EC : 1];
+#pragma unroll
+        for (int m = 0; m < F::TPT; ++m) {
+            const int u = tid + NT * m;
+            zoff[m] = u < F::TASKS ? u % ZR - 1 : kNoTask;
+            if constexpr (KEEP)
+#pragma unroll
+                for (int e = 0; e < EC; ++e) koff[m][e] = col_off(m, e);
+        }
         float hv[F::TPT][EC];
         auto load_lines = [&](int tile) {
             if (tile >= ntiles) return;
             int x, y, z0;
             tile_origin(tile, x, y, z0);
+            // lines off the mesh's x and y borders need no wrap in x or y
+            const bool inner = x > 0 && x < N - 1 && y > 0 && y < N - 1;
+            const int centre = (x * N + y) * N;
 #pragma unroll
             for (int m = 0; m < F::TPT; ++m) {
-                const int u = tid + NT * m;
-                if (u >= F::TASKS) continue;
-                const int q = u / ZR, i = u - q * ZR;
-                const int z = (int)(((int64_t)z0 + i - 1 + N) % N);
+                if (zoff[m] == kNoTask) continue;
+                int z = z0 + zoff[m];
+                z = z < 0 ? z + N : z;
+                if (z >= N) z = z >= 2 * N ? z % N : z - N;  // several wraps only when N < 129
 #pragma unroll
                 for (int e = 0; e < EC; ++e) {
-                    const int k = q * EC + e;
                     float v = 0.f;
-                    if (k < 27) {
-                        const int c = k / 9, ox = (k / 3) % 3 - 1, oy = k % 3 - 1;
-                        const int gx = wrapi(x + ox, N), gy = wrapi(y + oy, N);
-                        v = feat[c * N3 + ((int64_t)gx * N + gy) * N + z];
+                    int ko;
+                    if constexpr (KEEP)
+                        ko = koff[m][e];
+                    else
+                        ko = col_off(m, e);
+                    if (ko != kNoTask) {
+                        if (inner) {
+                            v = feat[(uint32_t)(centre + z + ko)];
+                        } else {
+                            const int k = ((tid + NT * m) / ZR) * EC + e;
+                            const int c = k / 9, gx = wrapi(x + (k / 3) % 3 - 1, N), gy = wrapi(y + k % 3 - 1, N);
+                            v = feat[(uint32_t)(c * (int)N3 + (gx * N + gy) * N + z)];
+                        }
                     }
                     hv[m][e] = v;
                 }
