@@ -801,6 +801,29 @@ __global__ void __launch_bounds__(NTW, 1)
             mbar_arrive(bars + 0);
         };
 
+        // box cells e = tid + NT j of this thread (fixed over the tiles): field c, cell
+        // (hx, hy, hz); the term of (ox, oy) sits at gvs[box_base + ((ox + 1) 3 + oy + 1) *
+        // TX TY HZ - (ox TY + oy) HZ], present when bit (ox + 1) 3 + oy + 1 of the cell's
+        // 9 mask bits is set (its tile cell lies inside the tile)
+        constexpr int NBOX = 3 * HX * HY * HZ, BOX_PER_THREAD = (NBOX + NT - 1) / NT;
+        static_assert(BOX_PER_THREAD * 9 <= 32, "mask bits of a thread's box cells in one word");
+        int box_base[BOX_PER_THREAD];
+        uint32_t box_mask = 0;
+#pragma unroll
+        for (int j = 0; j < BOX_PER_THREAD; ++j) {
+            const int e = tid + NT * j;
+            const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
+            const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
+            box_base[j] = c * 9 * (TX * TY * HZ) + ((hx - 1) * TY + (hy - 1)) * HZ + hz;
+            uint32_t msk = 0;
+            for (int ox = -1; ox <= 1; ++ox)
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int lx = hx - 1 - ox, ly = hy - 1 - oy;
+                    if (e < NBOX && lx >= 0 && lx < TX && ly >= 0 && ly < TY) msk |= 1u << ((ox + 1) * 3 + (oy + 1));
+                }
+            box_mask |= msk << (9 * j);
+        }
+
         int tile = blockIdx.x;
         uint32_t m1_cur = 0;
         load_saved(tile);
@@ -892,23 +915,19 @@ __global__ void __launch_bounds__(NTW, 1)
             nbar_sync(NT);
             // (6) box sums: field c at box cell (hx, hy, hz) collects T of the triples
             //     (c, ox, oy) at tile (lx, ly) = (hx - 1 - ox, hy - 1 - oy), in a fixed order
-            for (int e = tid; e < 3 * HX * HY * HZ; e += NT) {
-                const int c = e / (HX * HY * HZ), rem = e - c * (HX * HY * HZ);
-                const int hx = rem / (HY * HZ), hy = (rem / HZ) % HY, hz = rem % HZ;
+#pragma unroll
+            for (int j = 0; j < BOX_PER_THREAD; ++j) {
+                const int e = tid + NT * j;
+                if (e >= NBOX) break;
+                const uint32_t msk = box_mask >> (9 * j);
                 float acc = 0.f;
 #pragma unroll
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int lx = hx - 1 - ox;
-                    if (lx < 0 || lx >= TX) continue;
+                for (int ox = -1; ox <= 1; ++ox)
 #pragma unroll
-                    for (int oy = -1; oy <= 1; ++oy) {
-                        const int ly = hy - 1 - oy;
-                        if (ly < 0 || ly >= TY) continue;
-                        const int q = c * 9 + (ox + 1) * 3 + (oy + 1);
-                        acc += gvs[q * (TX * TY * HZ) + (lx * TY + ly) * HZ + hz];
-                    }
-                }
-                gbox[(int64_t)tile * (3 * HX * HY * HZ) + e] = acc;
+                    for (int oy = -1; oy <= 1; ++oy)
+                        if (msk & (1u << ((ox + 1) * 3 + (oy + 1))))
+                            acc += gvs[box_base[j] + ((ox + 1) * 3 + (oy + 1)) * (TX * TY * HZ) - (ox * TY + oy) * HZ];
+                gbox[(int64_t)tile * NBOX + e] = acc;
             }
             m1_cur = m1_nxt;
             nbar_sync(NT);  // gvs is rewritten by the next tile
