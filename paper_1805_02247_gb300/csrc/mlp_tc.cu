@@ -55,8 +55,9 @@ constexpr int NT = 512;           // threads per block (16 warps; 4 per TMEM lan
 constexpr int TX = 2, TY = 4, TZ = 16, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HALO = 3 * HX * HY * HZ;
 
-// TMEM columns
-constexpr uint32_t COL_D1 = 0, COL_D2 = 64, COL_D3 = 96, COL_D4 = 160;
+// TMEM columns. Forward: D1 buffers at COL_D1 and COL_D1 + 64, D2 at COL_D2.
+// Backward: D3 at COL_D3, D4 at COL_D4.
+constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_D3 = 96, COL_D4 = 160;
 
 constexpr uint32_t VEC_MASS = 160;  // float offset of the mass-network weights in the vector block
 constexpr uint32_t SZ_VEC = 1920;    // b1[64], b2[32], w3[32], b3[4], mass network[301]: 4 * 461 rounded to 128 B
@@ -305,16 +306,21 @@ constexpr int NTW = NT + 32;  // 16 compute warps + the warp whose lane 0 issues
 
 // Forward only, warp-specialised and software-pipelined over the CTA's z-line
 // tiles. Warps 0-15 build operands and read accumulators; lane 0 of warp 16
-// issues the MMAs. Operand buffers are per layer, so the compute warps build
-// the next tile's A1 while this tile's layer 2 runs, and read this tile's
-// layer 2 while the next tile's layer 1 runs. Handshakes (mbarriers):
-//   A1 full / A2 full: 512 compute-thread arrivals, each after its operand
-//     stores (async-proxy fence) and after its own reads of the accumulator
-//     the next MMA overwrites;
-//   D1 full / D2 full: tcgen05.commit after MMA1 / MMA2.
-// Per tile t (t' = the CTA's next tile), compute warps:
-//   wait D1(t); D1 -> A2, arrive A2; lines(t') -> A1, arrive A1; wait D2(t); D2 -> y, M
-// and the issuing lane: wait A1(t), MMA1(t) -> D1; wait A2(t), MMA2(t) -> D2.
+// issues the MMAs. The layer-1 operand A1 and accumulator D1 are double-
+// buffered (buffer b = the CTA's tile count mod 2), so layer 1 of the next tile
+// runs on the tensor cores while the compute warps read this tile's D1; A2 and
+// D2 are single. Per tile t of the CTA (t-1, t+1 its neighbours in the CTA's
+// sequence), the issuing lane runs
+//   wait A1(t+1), MMA1(t+1) -> D1[b^1]; wait A2(t), MMA2(t) -> D2
+// and the compute warps
+//   lines(t+1) -> A1[b^1], arrive A1(t+1); wait D2(t-1), D2 -> y, M of t-1;
+//   wait D1(t), relu(D1[b] + b1) -> A2, arrive A2(t).
+// Handshakes (mbarriers): "A1 full" [2] and "A2 full" take 512 compute-thread
+// arrivals, each after its operand stores (async-proxy fence) and after its
+// own reads of the accumulator the next MMA into that buffer overwrites;
+// "D1 full" [2] and "D2 full" take tcgen05.commit. One barrier per buffer keeps
+// every waiter within one phase of its barrier: a parity wait never sees two
+// completed phases.
 
 template <bool BF>
 struct LayF {
@@ -325,10 +331,11 @@ struct LayF {
     static constexpr int TPT = (TASKS + NT - 1) / NT;  // per compute thread
     static constexpr int KST = K1Z / L::KS;           // k-steps per z offset
     static constexpr uint32_t SZ_A1 = CH * ZLBO, SZ_A2 = L::bytes(TM, K2);
+    static constexpr uint32_t A1_BUF = L::NP * SZ_A1;  // one A1 buffer (head and tail parts)
     static constexpr uint32_t S_A1 = L::IMG_FWD;
-    static constexpr uint32_t S_A2 = S_A1 + L::NP * SZ_A1;
+    static constexpr uint32_t S_A2 = S_A1 + 2 * A1_BUF;
     static constexpr uint32_t S_TAIL = S_A2 + L::NP * SZ_A2;
-    // partial sums [4][TM], 5 barriers + TMEM slot
+    // partial sums [4][TM], 7 barriers + TMEM slot
     static constexpr uint32_t SMEM = S_TAIL + 4 * 4 * TM + 64;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0 && SZ_A1 % 128 == 0, "aligned regions");
@@ -342,6 +349,9 @@ struct ZMap {
     int64_t N3;
 };
 
+// mbarriers of the forward
+enum : int { FB_A1 = 0, FB_A2 = 2, FB_D1 = 3, FB_D2 = 5, FB_DRAIN = 6, FB_COUNT = 7 };
+
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
     k_mlp_tc_fwd(const float* __restrict__ feat, const float4* __restrict__ img, ZMap zm, int ntiles, int nsplit,
@@ -349,20 +359,18 @@ __global__ void __launch_bounds__(NTW, 1)
     using L = Lay<BF>;
     using F = LayF<BF>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* A1h = sm + F::S_A1;
-    unsigned char* A1l = A1h + (L::NP - 1) * F::SZ_A1;  // == A1h with one part
     unsigned char* A2h = sm + F::S_A2;
     unsigned char* A2l = A2h + (L::NP - 1) * F::SZ_A2;
     float* part = reinterpret_cast<float*>(sm + F::S_TAIL);  // [4][TM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(part + 4 * TM);  // A1 full, A2 full, D1 full, D2 full, drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(part + 4 * TM);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + FB_COUNT);
     const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
     const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cb = warp >> 2;
     const int row = quad * 32 + lane;
-    constexpr uint32_t ncols = 128;
+    constexpr uint32_t ncols = 256;  // D1 [2] x 64 + D2 32
     const int N = zm.N;
     const int64_t N3 = zm.N3;
 
@@ -370,17 +378,18 @@ __global__ void __launch_bounds__(NTW, 1)
         const uint32_t n16 = L::IMG_FWD / 16;
         float4* dst = reinterpret_cast<float4*>(sm);
         for (uint32_t i = tid; i < n16; i += NTW) dst[i] = img[i];
-        // the padding chunks of A1 (columns past the 27 inputs) stay zero
+        // the padding chunks of both A1 buffers (columns past the 27 inputs) stay zero
         for (uint32_t i = tid; i < (uint32_t)(F::CH - F::CH_USED) * ZR; i += NTW)
-            for (int p = 0; p < L::NP; ++p)
+            for (int p = 0; p < 2 * L::NP; ++p)
                 *reinterpret_cast<float4*>(sm + F::S_A1 + p * F::SZ_A1 + (F::CH_USED + i / ZR) * ZLBO +
                                            (i % ZR) * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (tid == 0) {
-        const uint32_t cnt[5] = {(uint32_t)NT, (uint32_t)NT, 1u, 1u, 1u};
 #pragma unroll
-        for (int b = 0; b < 5; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt[b]) : "memory");
+        for (int b = 0; b < FB_COUNT; ++b) {
+            const uint32_t cnt = b < FB_D1 ? (uint32_t)NT : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -398,54 +407,74 @@ __global__ void __launch_bounds__(NTW, 1)
     if (warp == NT / 32) {
         // ---- MMA issue (one lane)
         if (lane == 0) {
-            const uint32_t sA1h = smem_u32(A1h), sA1l = smem_u32(A1l), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
+            const uint32_t sA1 = smem_u32(sm + F::S_A1), sA2h = smem_u32(A2h), sA2l = smem_u32(A2l);
             const uint32_t sB1 = smem_u32(sm + L::S_B1);
             constexpr uint32_t SZ_B1OZ = L::bytes(N1, K1Z);
-            uint32_t pa1 = 0, pa2 = 0;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                if (!mbar_wait(bars + 0, pa1, ctl.wait_limit)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                pa1 ^= 1;
-                tc_fence_after();
-                if (!ctl.issue) continue;  // test hook: D1 never completes
-                // layer 1: the three z offsets of the stencil, each a shifted view of A1
+            // layer 1 of the tile in A1 buffer b, into D1 buffer b: the three z offsets
+            // of the stencil, each a shifted view of A1
+            auto mma1 = [&](int b) {
+                const uint32_t hi = sA1 + (uint32_t)b * F::A1_BUF, lo = hi + (L::NP - 1) * F::SZ_A1;
+                const uint32_t d = tmem + COL_D1 + (uint32_t)b * N1;
                 for (int oz = 0; oz < 3; ++oz)
                     for (int ks = 0; ks < F::KST; ++ks) {
                         const uint32_t ao = (uint32_t)ks * 2 * ZLBO + (uint32_t)oz * 16;
                         const uint32_t bo = (uint32_t)oz * SZ_B1OZ + (uint32_t)ks * (N1 * 32);
                         const uint32_t acc = (oz | ks) ? 1u : 0u;
                         if constexpr (BF) {
-                            mma_bf16(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_bf16(TM, N1), acc);
+                            mma_bf16(d, zdesc(hi + ao), sdesc(sB1 + bo), idesc_bf16(TM, N1), acc);
                         } else {
-                            mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), acc);
+                            mma_tf32(d, zdesc(hi + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), acc);
                             if (nsplit > 1) {
-                                mma_tf32(tmem + COL_D1, zdesc(sA1h + ao), sdesc(sB1 + L::SZ_B1 + bo),
-                                         idesc_tf32(TM, N1), 1u);
-                                mma_tf32(tmem + COL_D1, zdesc(sA1l + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), 1u);
+                                mma_tf32(d, zdesc(hi + ao), sdesc(sB1 + L::SZ_B1 + bo), idesc_tf32(TM, N1), 1u);
+                                mma_tf32(d, zdesc(lo + ao), sdesc(sB1 + bo), idesc_tf32(TM, N1), 1u);
                             }
                         }
                     }
-                mma_commit(bars + 2);
-                if (!mbar_wait(bars + 1, pa2, ctl.wait_limit)) {
+                mma_commit(bars + FB_D1 + b);
+            };
+            uint32_t pa1 = 0, pa2 = 0;  // phase bits: A1 full (bit b), A2 full
+            auto wait_a1 = [&](int b) {
+                if (!mbar_wait(bars + FB_A1 + b, (pa1 >> b) & 1u, ctl.wait_limit)) return false;
+                pa1 ^= 1u << b;
+                tc_fence_after();
+                return true;
+            };
+            int tile = blockIdx.x;
+            bool run = tile < ntiles;
+            if (run) {
+                run = wait_a1(0);
+                if (!run) atomicExch(err, 1);
+                else if (ctl.issue) mma1(0);  // ctl.issue = 0, the test hook: no D1 ever completes
+            }
+            for (int it = 0; run && tile < ntiles; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                if (tile + (int)gridDim.x < ntiles) {
+                    if (!wait_a1(b ^ 1)) {
+                        atomicExch(err, 1);
+                        break;
+                    }
+                    if (ctl.issue) mma1(b ^ 1);
+                }
+                if (!mbar_wait(bars + FB_A2, pa2, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
                 pa2 ^= 1;
                 tc_fence_after();
-                issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2), smem_u32(sm + L::S_B2 + L::SZ_B2),
-                                K2, N2, nsplit);
-                mma_commit(bars + 3);
+                if (ctl.issue) {
+                    issue_layer<BF>(tmem + COL_D2, sA2h, sA2l, smem_u32(sm + L::S_B2),
+                                    smem_u32(sm + L::S_B2 + L::SZ_B2), K2, N2, nsplit);
+                    mma_commit(bars + FB_D2);
+                }
             }
-            mma_commit(bars + 4);  // completes once every MMA issued above has
-            mbar_wait(bars + 4, 0, ctl.wait_limit);
+            mma_commit(bars + FB_DRAIN);  // completes once every MMA issued above has
+            mbar_wait(bars + FB_DRAIN, 0, ctl.wait_limit);
         }
         __syncwarp();
     } else {
         // ---- compute warps
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-        uint32_t ph1 = 0, ph2 = 0;
+        uint32_t ph1 = 0, ph2 = 0;  // phase bits: D1 full (bit b), D2 full
         bool ok = true;
         auto tile_origin = [&](int tile, int& x, int& y, int& z0) {
             const uint32_t line = zm.nzt.div((uint32_t)tile);
@@ -510,8 +539,10 @@ __global__ void __launch_bounds__(NTW, 1)
                 }
             }
         };
-        // prefetched lines -> A1, then arrive on "A1 full"
-        auto build_A1 = [&]() {
+        // prefetched lines -> A1 buffer b, then arrive on its "A1 full"
+        auto build_A1 = [&](int b) {
+            unsigned char* A1h = sm + F::S_A1 + (uint32_t)b * F::A1_BUF;
+            unsigned char* A1l = A1h + (L::NP - 1) * F::SZ_A1;  // == A1h with one part
 #pragma unroll
             for (int m = 0; m < F::TPT; ++m) {
                 const int u = tid + NT * m;
@@ -528,57 +559,42 @@ __global__ void __launch_bounds__(NTW, 1)
             }
             fence_async_smem();
             tc_fence_before();
-            mbar_arrive(bars + 0);
+            mbar_arrive(bars + FB_A1 + b);
         };
-
-        int tile = blockIdx.x;
-        load_lines(tile);
-        if (tile < ntiles) {
-            build_A1();
-            load_lines(tile + gridDim.x);
-        }
-        for (; tile < ntiles; tile += gridDim.x) {
-            const int nxt = tile + gridDim.x;
+        // bounded wait on a commit barrier, agreed by all compute threads
+        auto wait_commit = [&](int bar, uint32_t& ph, int bit) {
+            const bool got = nbar_and(NT, mbar_wait(bars + bar, (ph >> bit) & 1u, ctl.wait_limit));
+            ph ^= 1u << bit;
+            if (got) tc_fence_after();
+            return got;
+        };
+        // relu(D1[b] + b1) of a tile -> A2 and the layer-1 mask, then arrive on "A2 full"
+        auto epilogue1 = [&](int tile, int b) {
+            int x, y, z0;
+            tile_origin(tile, x, y, z0);
+            const int64_t row_vox = ((int64_t)x * N + y) * N + z0 + row;
+            float av[16];
+            tmem_ld16(lane_base + COL_D1 + (uint32_t)b * N1 + 16 * cb, av);
+            uint32_t mask1 = 0;
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float pre = av[j] + b1[16 * cb + j];
+                mask1 |= (pre > 0.f ? 1u : 0u) << j;
+                z[j] = fmaxf(pre, 0.f);
+            }
+            if (sv.m1 && z0 + row < N) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
+            put8<BF>(A2h, A2l, row, 16 * cb, z);
+            put8<BF>(A2h, A2l, row, 16 * cb + 8, z + 8);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + FB_A2);
+        };
+        // y = b3 + w3 . relu(D2 + b2) of a tile, the layer-2 mask and the head
+        auto epilogue2 = [&](int tile) {
             int x, y, z0;
             tile_origin(tile, x, y, z0);
             const int64_t line_vox = ((int64_t)x * N + y) * N + z0;
-            const bool row_in = z0 + row < N;
-            const int64_t row_vox = line_vox + row;
-            // (1) layer 1 of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 2, ph1, ctl.wait_limit));
-            ph1 ^= 1;
-            if (!ok) break;
-            tc_fence_after();
-            // (2) relu(D1 + b1) -> A2 and the layer-1 mask
-            {
-                float av[16];
-                tmem_ld16(lane_base + COL_D1 + 16 * cb, av);
-                uint32_t mask1 = 0;
-                float z[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float pre = av[j] + b1[16 * cb + j];
-                    mask1 |= (pre > 0.f ? 1u : 0u) << j;
-                    z[j] = fmaxf(pre, 0.f);
-                }
-                if (sv.m1 && row_in) sv.m1[cb * N3 + row_vox] = (uint16_t)mask1;
-                put8<BF>(A2h, A2l, row, 16 * cb, z);
-                put8<BF>(A2h, A2l, row, 16 * cb + 8, z + 8);
-            }
-            fence_async_smem();
-            tc_fence_before();
-            mbar_arrive(bars + 1);
-            // (3) the next tile's A1 while layer 2 runs
-            if (nxt < ntiles) {
-                build_A1();
-                load_lines(nxt + gridDim.x);
-            }
-            // (4) layer 2 of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 3, ph2, ctl.wait_limit));
-            ph2 ^= 1;
-            if (!ok) break;
-            tc_fence_after();
-            // (5) y = b3 + w3 . relu(D2 + b2) and the head
             {
                 float av[8];
                 tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
@@ -591,26 +607,51 @@ __global__ void __launch_bounds__(NTW, 1)
                     sacc = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), sacc);
                 }
                 part[cb * TM + row] = sacc;
-                if (sv.m2 && row_in) sv.m2[cb * N3 + row_vox] = (uint8_t)mask2;
+                if (sv.m2 && z0 + row < N) sv.m2[cb * N3 + line_vox + row] = (uint8_t)mask2;
             }
             tc_fence_before();
             nbar_sync(NT);
             if (tid < TM && z0 + tid < N) {
                 const int64_t vox = line_vox + tid;
-                const float y = b3[0] + ((part[tid] + part[TM + tid]) + (part[2 * TM + tid] + part[3 * TM + tid]));
-                if (sv.y) sv.y[vox] = y;
+                const float yv = b3[0] + ((part[tid] + part[TM + tid]) + (part[2 * TM + tid] + part[3 * TM + tid]));
+                if (sv.y) sv.y[vox] = yv;
                 if (TWO_NET) {
-                    const float pl = sigmoidf(a * y);
+                    const float pl = sigmoidf(a * yv);
                     float u0, u1, u2;
                     M_out[vox] = M_scale * pl *
                                  mass_net<false>(vec + VEC_MASS, feat[vox], feat[N3 + vox], feat[2 * N3 + vox], 0.f,
                                                  u0, u1, u2);
                 } else {
-                    M_out[vox] = M_scale * softplusf(y);
+                    M_out[vox] = M_scale * softplusf(yv);
                 }
             }
             nbar_sync(NT);  // part is rewritten by the next tile
+        };
+
+        int tile = blockIdx.x, prev = -1;
+        load_lines(tile);
+        if (tile < ntiles) {
+            build_A1(0);
+            load_lines(tile + gridDim.x);
         }
+        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+            const int b = it & 1, nxt = tile + gridDim.x;
+            // (1) the next tile's A1 (its buffer's previous layer 1 and D1 reads are done)
+            if (nxt < ntiles) {
+                build_A1(b ^ 1);
+                load_lines(nxt + gridDim.x);
+            }
+            // (2) the previous tile's layer 2 (frees A2 and D2)
+            if (prev >= 0) {
+                if (!(ok = wait_commit(FB_D2, ph2, 0))) break;
+                epilogue2(prev);
+            }
+            // (3) this tile's layer 1 -> A2
+            if (!(ok = wait_commit(FB_D1 + b, ph1, b))) break;
+            epilogue1(tile, b);
+            prev = tile;
+        }
+        if (ok && prev >= 0 && (ok = wait_commit(FB_D2, ph2, 0))) epilogue2(prev);
         if (!ok && tid == 0) atomicExch(err, 1);
     }
     tc_fence_before();
