@@ -55,9 +55,8 @@ constexpr int NT = 512;           // threads per block (16 warps; 4 per TMEM lan
 constexpr int TX = 2, TY = 4, TZ = 16, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HALO = 3 * HX * HY * HZ;
 
-// TMEM columns. Forward: D1 buffers at COL_D1 and COL_D1 + 64, D2 at COL_D2.
-// Backward: D3 at COL_D3, D4 at COL_D4.
-constexpr uint32_t COL_D1 = 0, COL_D2 = 128, COL_D3 = 96, COL_D4 = 160;
+// TMEM columns of the forward: D1 buffers at COL_D1 and COL_D1 + 64, D2 at COL_D2
+constexpr uint32_t COL_D1 = 0, COL_D2 = 128;
 
 constexpr uint32_t VEC_MASS = 160;  // float offset of the mass-network weights in the vector block
 constexpr uint32_t SZ_VEC = 1920;    // b1[64], b2[32], w3[32], b3[4], mass network[301]: 4 * 461 rounded to 128 B
@@ -313,8 +312,10 @@ constexpr int NTW = NT + 32;  // 16 compute warps + the warp whose lane 0 issues
 // sequence), the issuing lane runs
 //   wait A1(t+1), MMA1(t+1) -> D1[b^1]; wait A2(t), MMA2(t) -> D2
 // and the compute warps
-//   lines(t+1) -> A1[b^1], arrive A1(t+1); wait D2(t-1), D2 -> y, M of t-1;
+//   lines(t+1) -> A1[b^1], arrive A1(t+1); wait D2(t-1), D2 -> y, M of t-1
+//   (one warp per TMEM lane quadrant, taking turns over the tiles);
 //   wait D1(t), relu(D1[b] + b1) -> A2, arrive A2(t).
+// No named barrier sits in the loop: warps meet only through the mbarriers.
 // Handshakes (mbarriers): "A1 full" [2] and "A2 full" take 512 compute-thread
 // arrivals, each after its operand stores (async-proxy fence) and after its
 // own reads of the accumulator the next MMA into that buffer overwrites;
@@ -335,8 +336,8 @@ struct LayF {
     static constexpr uint32_t S_A1 = L::IMG_FWD;
     static constexpr uint32_t S_A2 = S_A1 + 2 * A1_BUF;
     static constexpr uint32_t S_TAIL = S_A2 + L::NP * SZ_A2;
-    // partial sums [4][TM], 7 barriers + TMEM slot
-    static constexpr uint32_t SMEM = S_TAIL + 4 * 4 * TM + 64;
+    // 7 barriers + TMEM slot
+    static constexpr uint32_t SMEM = S_TAIL + 64;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(S_A1 % 128 == 0 && S_A2 % 128 == 0 && S_TAIL % 16 == 0 && SZ_A1 % 128 == 0, "aligned regions");
     static_assert(CH % 2 == 0 && KST * 2 == CH, "a k-step is two 16-byte chunks");
@@ -361,8 +362,7 @@ __global__ void __launch_bounds__(NTW, 1)
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* A2h = sm + F::S_A2;
     unsigned char* A2l = A2h + (L::NP - 1) * F::SZ_A2;
-    float* part = reinterpret_cast<float*>(sm + F::S_TAIL);  // [4][TM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(part + 4 * TM);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + F::S_TAIL);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + FB_COUNT);
     const float* vec = reinterpret_cast<const float*>(sm + L::S_VEC);
     const float *b1 = vec, *b2 = vec + 64, *w3 = vec + 96, *b3 = vec + 128;
@@ -561,9 +561,11 @@ __global__ void __launch_bounds__(NTW, 1)
             tc_fence_before();
             mbar_arrive(bars + FB_A1 + b);
         };
-        // bounded wait on a commit barrier, agreed by all compute threads
+        // bounded wait on a commit barrier. Each thread waits and gives up on its own:
+        // no named barrier is left in the loop, so a thread that gives up leaves no
+        // other thread waiting without a bound.
         auto wait_commit = [&](int bar, uint32_t& ph, int bit) {
-            const bool got = nbar_and(NT, mbar_wait(bars + bar, (ph >> bit) & 1u, ctl.wait_limit));
+            const bool got = mbar_wait(bars + bar, (ph >> bit) & 1u, ctl.wait_limit);
             ph ^= 1u << bit;
             if (got) tc_fence_after();
             return got;
@@ -590,69 +592,74 @@ __global__ void __launch_bounds__(NTW, 1)
             tc_fence_before();
             mbar_arrive(bars + FB_A2);
         };
-        // y = b3 + w3 . relu(D2 + b2) of a tile, the layer-2 mask and the head
+        // y = b3 + w3 . relu(D2 + b2) of a tile, its layer-2 masks and the head, by the
+        // warp of column block `sel` of each TMEM lane quadrant (one voxel per thread;
+        // the column blocks' partial sums are added in the order of a 4-warp split)
         auto epilogue2 = [&](int tile) {
             int x, y, z0;
             tile_origin(tile, x, y, z0);
-            const int64_t line_vox = ((int64_t)x * N + y) * N + z0;
-            {
-                float av[8];
-                tmem_ld8(lane_base + COL_D2 + 8 * cb, av);
-                uint32_t mask2 = 0;
-                float sacc = 0.f;
+            const int64_t vox = ((int64_t)x * N + y) * N + z0 + row;
+            const bool in = z0 + row < N;
+            float p[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float pre = av[j] + b2[8 * cb + j];
-                    mask2 |= (pre > 0.f ? 1u : 0u) << j;
-                    sacc = fmaf(w3[8 * cb + j], fmaxf(pre, 0.f), sacc);
-                }
-                part[cb * TM + row] = sacc;
-                if (sv.m2 && z0 + row < N) sv.m2[cb * N3 + line_vox + row] = (uint8_t)mask2;
-            }
-            tc_fence_before();
-            nbar_sync(NT);
-            if (tid < TM && z0 + tid < N) {
-                const int64_t vox = line_vox + tid;
-                const float yv = b3[0] + ((part[tid] + part[TM + tid]) + (part[2 * TM + tid] + part[3 * TM + tid]));
-                if (sv.y) sv.y[vox] = yv;
-                if (TWO_NET) {
-                    const float pl = sigmoidf(a * yv);
-                    float u0, u1, u2;
-                    M_out[vox] = M_scale * pl *
-                                 mass_net<false>(vec + VEC_MASS, feat[vox], feat[N3 + vox], feat[2 * N3 + vox], 0.f,
-                                                 u0, u1, u2);
-                } else {
-                    M_out[vox] = M_scale * softplusf(yv);
+            for (int h = 0; h < 2; ++h) {
+                float av[16];
+                tmem_ld16(lane_base + COL_D2 + 16 * h, av);
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const int blk = 2 * h + g;
+                    uint32_t mask2 = 0;
+                    float sacc = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float pre = av[8 * g + j] + b2[8 * blk + j];
+                        mask2 |= (pre > 0.f ? 1u : 0u) << j;
+                        sacc = fmaf(w3[8 * blk + j], fmaxf(pre, 0.f), sacc);
+                    }
+                    p[blk] = sacc;
+                    if (sv.m2 && in) sv.m2[blk * N3 + vox] = (uint8_t)mask2;
                 }
             }
-            nbar_sync(NT);  // part is rewritten by the next tile
+            if (!in) return;
+            const float yv = b3[0] + ((p[0] + p[1]) + (p[2] + p[3]));
+            if (sv.y) sv.y[vox] = yv;
+            if (TWO_NET) {
+                const float pl = sigmoidf(a * yv);
+                float u0, u1, u2;
+                M_out[vox] = M_scale * pl *
+                             mass_net<false>(vec + VEC_MASS, feat[vox], feat[N3 + vox], feat[2 * N3 + vox], 0.f, u0,
+                                             u1, u2);
+            } else {
+                M_out[vox] = M_scale * softplusf(yv);
+            }
         };
 
-        int tile = blockIdx.x, prev = -1;
+        int tile = blockIdx.x, prev = -1, last_it = 0;
         load_lines(tile);
         if (tile < ntiles) {
             build_A1(0);
             load_lines(tile + gridDim.x);
         }
-        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
+        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it, last_it = it) {
             const int b = it & 1, nxt = tile + gridDim.x;
             // (1) the next tile's A1 (its buffer's previous layer 1 and D1 reads are done)
             if (nxt < ntiles) {
                 build_A1(b ^ 1);
                 load_lines(nxt + gridDim.x);
             }
-            // (2) the previous tile's layer 2 (frees A2 and D2)
+            // (2) the previous tile's layer 2 (frees A2 and D2); column block
+            //     (it - 1) mod 4 reads it
             if (prev >= 0) {
                 if (!(ok = wait_commit(FB_D2, ph2, 0))) break;
-                epilogue2(prev);
+                if (cb == ((it - 1) & 3)) epilogue2(prev);
             }
             // (3) this tile's layer 1 -> A2
             if (!(ok = wait_commit(FB_D1 + b, ph1, b))) break;
             epilogue1(tile, b);
             prev = tile;
         }
-        if (ok && prev >= 0 && (ok = wait_commit(FB_D2, ph2, 0))) epilogue2(prev);
-        if (!ok && tid == 0) atomicExch(err, 1);
+        if (ok && prev >= 0 && (ok = wait_commit(FB_D2, ph2, 0)) && cb == ((last_it - 1) & 3)) epilogue2(prev);
+        if (!ok && lane == 0) atomicExch(err, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -662,11 +669,17 @@ __global__ void __launch_bounds__(NTW, 1)
 }
 
 // Backward (input gradient) from the forward's saved activations, warp-
-// specialised and pipelined like k_mlp_tc_fwd, with separate A3 / A4 operand
-// buffers and g_v staging. Per tile t (t' = the CTA's next tile), compute warps:
-//   wait D3(t); D3 [a1 > 0] -> A4, arrive A4; g_y(t') -> A3, arrive A3;
-//   wait D4(t); D4 -> g_v -> box sums
-// and the issuing lane: wait A3(t), MMA3(t) -> D3; wait A4(t), MMA4(t) -> D4.
+// specialised and software-pipelined like k_mlp_tc_fwd. A3 and the
+// accumulators D3 and D4 are double-buffered (buffer = the CTA's tile count
+// mod 2), A4 and the g_v staging are single. Per tile t of the CTA (t-1, t+1
+// its neighbours in the CTA's sequence), the issuing lane runs
+//   wait A4(t), MMA4(t) -> D4[t]; wait A3(t+1), MMA3(t+1) -> D3[t+1]
+// and the compute warps
+//   wait D4(t-1) (frees A4); wait D3(t), D3[t] [a1 > 0] -> A4, arrive A4(t);
+//   g_y(t+1) -> A3[t+1], arrive A3(t+1); D4[t-1] -> g_v -> box sums of t-1,
+// so layer 1's input gradient of tile t runs on the tensor cores while the
+// compute warps sum the boxes of tile t-1. One barrier per buffer keeps every
+// waiter within one phase of its barrier.
 // Only the layer-2 and layer-1 weight images (B3 = W2, B4 = W1) and the vector
 // block are staged.
 template <bool BF>
@@ -676,17 +689,25 @@ struct LayB {
     static constexpr uint32_t IMG_BYTES = L::IMG_ALL - L::S_VEC;
     static constexpr uint32_t S_VEC = 0, S_B3 = L::S_B3 - L::S_VEC, S_B4 = L::S_B4 - L::S_VEC;
     static constexpr uint32_t SZ_A3 = L::bytes(TM, K3), SZ_A4 = L::bytes(TM, K4);
+    static constexpr uint32_t A3_BUF = L::NP * SZ_A3;  // one A3 buffer (head and tail parts)
     static constexpr uint32_t S_A3 = (IMG_BYTES + 127) / 128 * 128;
-    static constexpr uint32_t S_A4 = S_A3 + L::NP * SZ_A3;
+    static constexpr uint32_t S_A4 = S_A3 + 2 * A3_BUF;
     static constexpr uint32_t S_GV = S_A4 + L::NP * SZ_A4;
-    static constexpr uint32_t S_TAIL = S_GV + 4 * NI * TM;
-    // g_y [TM], centre-value gradients [2][3][TM], 5 barriers + TMEM slot
-    static constexpr uint32_t SMEM = S_TAIL + 4 * TM + 4 * 6 * TM + 64;
+    static constexpr int NTS = 27 * TX * TY * HZ;  // z-folded g_v, Ts[27][TX][TY][HZ]
+    static constexpr uint32_t S_TAIL = S_GV + 4 * NTS;
+    // g_y [TM], centre-value gradients [3 slots][3][TM], 8 barriers + TMEM slot
+    static constexpr uint32_t SMEM = S_TAIL + 4 * TM + 4 * 9 * TM + 80;
     static_assert(SMEM <= 232448, "shared memory budget");
-    static_assert(S_B3 % 128 == 0 && S_B4 % 128 == 0 && S_A3 % 128 == 0 && S_A4 % 128 == 0 && S_GV % 16 == 0,
+    static_assert(S_B3 % 128 == 0 && S_B4 % 128 == 0 && S_A3 % 128 == 0 && S_A4 % 128 == 0 && S_GV % 16 == 0 &&
+                      A3_BUF % 128 == 0 && S_TAIL % 16 == 0,
                   "aligned regions");
     static_assert(IMG_OFF % 16 == 0 && IMG_BYTES % 16 == 0, "16-byte image copy");
 };
+
+// mbarriers of the backward
+enum : int { BB_A3 = 0, BB_A4 = 2, BB_D3 = 3, BB_D4 = 5, BB_DRAIN = 7, BB_COUNT = 8 };
+// TMEM columns of the backward's buffers: D3 [2] x 64, D4 [2] x 96 (at 128-column offsets)
+constexpr uint32_t COL_D3B = 0, COL_D4B = 128;
 
 template <bool TWO_NET, bool BF>
 __global__ void __launch_bounds__(NTW, 1)
@@ -696,22 +717,20 @@ __global__ void __launch_bounds__(NTW, 1)
     using L = Lay<BF>;
     using B = LayB<BF>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    unsigned char* A3h = sm + B::S_A3;
-    unsigned char* A3l = A3h + (L::NP - 1) * B::SZ_A3;
     unsigned char* A4h = sm + B::S_A4;
     unsigned char* A4l = A4h + (L::NP - 1) * B::SZ_A4;
-    float* gvs = reinterpret_cast<float*>(sm + B::S_GV);  // [81][TM]
+    float* gvs = reinterpret_cast<float*>(sm + B::S_GV);  // Ts[27][TX][TY][HZ]
     float* gys = reinterpret_cast<float*>(sm + B::S_TAIL);
-    float* gcen = gys + TM;  // [2 slots][3][TM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(gcen + 6 * TM);  // A3 full, A4 full, D3 full, D4 full, drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 5);
+    float* gcen = gys + TM;  // [3 slots][3][TM]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gcen + 9 * TM);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + BB_COUNT);
     const float* vec = reinterpret_cast<const float*>(sm + B::S_VEC);
     const float* w3 = vec + 96;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, cb = warp >> 2;
     const int row = quad * 32 + lane;
-    constexpr uint32_t ncols = 256;
+    constexpr uint32_t ncols = 512;  // D3 [2] at 0, 64; D4 [2] at 128, 256
     const int N = tm.N;
     const int64_t N3 = tm.N3;
 
@@ -722,10 +741,11 @@ __global__ void __launch_bounds__(NTW, 1)
         for (uint32_t i = tid; i < n16; i += NTW) dst[i] = src[i];
     }
     if (tid == 0) {
-        const uint32_t cnt[5] = {(uint32_t)NT, (uint32_t)NT, 1u, 1u, 1u};
 #pragma unroll
-        for (int b = 0; b < 5; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt[b]) : "memory");
+        for (int b = 0; b < BB_COUNT; ++b) {
+            const uint32_t cnt = b < BB_D3 ? (uint32_t)NT : 1u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -742,37 +762,56 @@ __global__ void __launch_bounds__(NTW, 1)
     if (warp == NT / 32) {
         // ---- MMA issue (one lane)
         if (lane == 0) {
-            const uint32_t sA3h = smem_u32(A3h), sA3l = smem_u32(A3l), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
-            uint32_t pa3 = 0, pa4 = 0;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-                if (!mbar_wait(bars + 0, pa3, ctl.wait_limit)) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                pa3 ^= 1;
+            const uint32_t sA3 = smem_u32(sm + B::S_A3), sA4h = smem_u32(A4h), sA4l = smem_u32(A4l);
+            auto mma3 = [&](int b) {  // A3 buffer b -> D3 buffer b
+                const uint32_t hi = sA3 + (uint32_t)b * B::A3_BUF;
+                issue_layer<BF>(tmem + COL_D3B + (uint32_t)b * 64, hi, hi + (L::NP - 1) * B::SZ_A3,
+                                smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3), K3, NB3, nsplit);
+                mma_commit(bars + BB_D3 + b);
+            };
+            uint32_t pa3 = 0, pa4 = 0;  // phase bits: A3 full (bit b), A4 full
+            auto wait_a3 = [&](int b) {
+                if (!mbar_wait(bars + BB_A3 + b, (pa3 >> b) & 1u, ctl.wait_limit)) return false;
+                pa3 ^= 1u << b;
                 tc_fence_after();
-                if (!ctl.issue) continue;  // test hook: D3 never completes
-                issue_layer<BF>(tmem + COL_D3, sA3h, sA3l, smem_u32(sm + B::S_B3), smem_u32(sm + B::S_B3 + L::SZ_B3),
-                                K3, NB3, nsplit);
-                mma_commit(bars + 2);
-                if (!mbar_wait(bars + 1, pa4, ctl.wait_limit)) {
+                return true;
+            };
+            int tile = blockIdx.x;
+            bool run = tile < ntiles;
+            if (run) {
+                run = wait_a3(0);
+                if (!run) atomicExch(err, 1);
+                else if (ctl.issue) mma3(0);  // ctl.issue = 0, the test hook: no D3 ever completes
+            }
+            for (int it = 0; run && tile < ntiles; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                if (!mbar_wait(bars + BB_A4, pa4, ctl.wait_limit)) {
                     atomicExch(err, 1);
                     break;
                 }
                 pa4 ^= 1;
                 tc_fence_after();
-                issue_layer<BF>(tmem + COL_D4, sA4h, sA4l, smem_u32(sm + B::S_B4), smem_u32(sm + B::S_B4 + L::SZ_B4),
-                                K4, NB4, nsplit);
-                mma_commit(bars + 3);
+                if (ctl.issue) {
+                    issue_layer<BF>(tmem + COL_D4B + (uint32_t)b * 128, sA4h, sA4l, smem_u32(sm + B::S_B4),
+                                    smem_u32(sm + B::S_B4 + L::SZ_B4), K4, NB4, nsplit);
+                    mma_commit(bars + BB_D4 + b);
+                }
+                if (tile + (int)gridDim.x < ntiles) {
+                    if (!wait_a3(b ^ 1)) {
+                        atomicExch(err, 1);
+                        break;
+                    }
+                    if (ctl.issue) mma3(b ^ 1);
+                }
             }
-            mma_commit(bars + 4);  // completes once every MMA issued above has
-            mbar_wait(bars + 4, 0, ctl.wait_limit);
+            mma_commit(bars + BB_DRAIN);  // completes once every MMA issued above has
+            mbar_wait(bars + BB_DRAIN, 0, ctl.wait_limit);
         }
         __syncwarp();
     } else {
         // ---- compute warps
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-        uint32_t ph3 = 0, ph4 = 0;
+        uint32_t ph3 = 0, ph4 = 0;  // phase bits: D3 full (bit b), D4 full (bit b)
         bool ok = true;
         auto tile_origin = [&](int tile, int& x0, int& y0, int& z0) {
             const uint32_t t2 = tm.ntz.div((uint32_t)tile);
@@ -807,8 +846,11 @@ __global__ void __launch_bounds__(NTW, 1)
             L_m1 = in ? sv.m1[cb * N3 + v] : 0u;
             L_m2 = in ? sv.m2[cb * N3 + v] : 0u;
         };
-        // g_y of the loaded tile, A3 = g_a2 = w3 g_y [a2 > 0], arrive on "A3 full"; gcen slot `slot`
-        auto build_A3 = [&](int tile, int slot) {
+        // g_y of the loaded tile, A3 = g_a2 = w3 g_y [a2 > 0] into A3 buffer b, arrive on
+        // its "A3 full"; the centre-value gradients (two-network head) into gcen slot `slot`
+        auto build_A3 = [&](int tile, int b, int slot) {
+            unsigned char* A3h = sm + B::S_A3 + (uint32_t)b * B::A3_BUF;
+            unsigned char* A3l = A3h + (L::NP - 1) * B::SZ_A3;  // == A3h with one part
             int x0, y0, z0;
             tile_origin(tile, x0, y0, z0);
             if (tid < TM) {
@@ -839,9 +881,28 @@ __global__ void __launch_bounds__(NTW, 1)
             }
             fence_async_smem();
             tc_fence_before();
-            mbar_arrive(bars + 0);
+            mbar_arrive(bars + BB_A3 + b);
         };
-
+        // bounded wait on a commit barrier, agreed by all compute threads (the box
+        // sums below keep named barriers in the loop)
+        auto wait_commit = [&](int bar, uint32_t& ph, int bit) {
+            const bool got = nbar_and(NT, mbar_wait(bars + bar, (ph >> bit) & 1u, ctl.wait_limit));
+            ph ^= 1u << bit;
+            if (got) tc_fence_after();
+            return got;
+        };
+        // A4 = g_a1 [a1 > 0] from D3 buffer b, then arrive on "A4 full"
+        auto epilogue3 = [&](int b, uint32_t m1) {
+            float av[16];
+            tmem_ld16(lane_base + COL_D3B + (uint32_t)b * 64 + 16 * cb, av);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) av[j] = ((m1 >> j) & 1u) ? av[j] : 0.f;
+            put8<BF>(A4h, A4l, row, 16 * cb, av);
+            put8<BF>(A4h, A4l, row, 16 * cb + 8, av + 8);
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(bars + BB_A4);
+        };
         // box cells e = tid + NT j of this thread (fixed over the tiles): field c, cell
         // (hx, hy, hz); the term of (ox, oy) sits at gvs[box_base + ((ox + 1) 3 + oy + 1) *
         // TX TY HZ - (ox TY + oy) HZ], present when bit (ox + 1) 3 + oy + 1 of the cell's
@@ -865,56 +926,18 @@ __global__ void __launch_bounds__(NTW, 1)
             box_mask |= msk << (9 * j);
         }
 
-        int tile = blockIdx.x;
-        uint32_t m1_cur = 0;
-        load_saved(tile);
-        if (tile < ntiles) {
-            build_A3(tile, 0);
-            m1_cur = L_m1;
-            load_saved(tile + gridDim.x);
-        }
-        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-            const int nxt = tile + gridDim.x;
-            const int slot = it & 1;
+        // g_v of a tile from D4 buffer b (gcen slot `slot`), folded over the z offset in
+        // registers: a thread holds 24 columns = 8 whole (c, ox, oy) triples over oz
+        // (k = 3 q + oz + 1), and the voxels z - 1, z + 1 of its row are the neighbouring
+        // lanes of its 16-lane group, so T_q(hz) = g_v[q, oz=-1](hz) + g_v[q, 0](hz - 1) +
+        // g_v[q, 1](hz - 2) (box z index hz = lz + 1; lane 0 also gives hz = 0, lane 15
+        // hz = 17) needs two shuffles per triple. T goes to shared memory as
+        // Ts[q][lx][ly][hz] (27 x 2 x 4 x 18; rows outside the mesh give 0). Then the box
+        // sums: field c at box cell (hx, hy, hz) collects T of the triples (c, ox, oy) at
+        // tile (lx, ly) = (hx - 1 - ox, hy - 1 - oy), in a fixed order.
+        auto epilogue4 = [&](int tile, int b, int slot) {
             int x0, y0, z0;
             tile_origin(tile, x0, y0, z0);
-
-            // (1) layer-2 input gradient of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 2, ph3, ctl.wait_limit));
-            ph3 ^= 1;
-            if (!ok) break;
-            tc_fence_after();
-            // (2) A4 = g_a1 [a1 > 0]
-            {
-                float av[16];
-                tmem_ld16(lane_base + COL_D3 + 16 * cb, av);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) av[j] = ((m1_cur >> j) & 1u) ? av[j] : 0.f;
-                put8<BF>(A4h, A4l, row, 16 * cb, av);
-                put8<BF>(A4h, A4l, row, 16 * cb + 8, av + 8);
-            }
-            fence_async_smem();
-            tc_fence_before();
-            mbar_arrive(bars + 1);
-            // (3) the next tile's A3 while MMA4 runs
-            uint32_t m1_nxt = 0;
-            if (nxt < ntiles) {
-                build_A3(nxt, slot ^ 1);
-                m1_nxt = L_m1;
-                load_saved(nxt + gridDim.x);
-            }
-            // (4) layer-1 input gradient of this tile
-            ok = nbar_and(NT, mbar_wait(bars + 3, ph4, ctl.wait_limit));
-            ph4 ^= 1;
-            if (!ok) break;
-            tc_fence_after();
-            // (5) g_v, folded over the z offset in registers: a thread holds 24
-            //     columns = 8 whole (c, ox, oy) triples over oz (k = 3 q + oz + 1), and
-            //     the voxels z - 1, z + 1 of its row are the neighbouring lanes of its
-            //     16-lane group, so T_q(hz) = g_v[q, oz=-1](hz) + g_v[q, 0](hz - 1) +
-            //     g_v[q, 1](hz - 2) (box z index hz = lz + 1; lane 0 also gives hz = 0,
-            //     lane 15 hz = 17) needs two shuffles per triple. T goes to shared
-            //     memory as Ts[q][lx][ly][hz] (27 x 2 x 4 x 18; rows outside the mesh give 0).
             {
                 const int lx = row >> 6, ly = (row >> 4) & 3, lz = row & 15;
                 const bool in = x0 + lx < N && y0 + ly < N && z0 + lz < N;
@@ -924,7 +947,7 @@ __global__ void __launch_bounds__(NTW, 1)
 #pragma unroll
                 for (int h = 0; h < 3; ++h) {
                     float av[8];
-                    tmem_ld8(lane_base + COL_D4 + 24 * cb + 8 * h, av);
+                    tmem_ld8(lane_base + COL_D4B + (uint32_t)b * 128 + 24 * cb + 8 * h, av);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int k = 24 * cb + 8 * h + j;
@@ -954,8 +977,6 @@ __global__ void __launch_bounds__(NTW, 1)
             }
             tc_fence_before();
             nbar_sync(NT);
-            // (6) box sums: field c at box cell (hx, hy, hz) collects T of the triples
-            //     (c, ox, oy) at tile (lx, ly) = (hx - 1 - ox, hy - 1 - oy), in a fixed order
 #pragma unroll
             for (int j = 0; j < BOX_PER_THREAD; ++j) {
                 const int e = tid + NT * j;
@@ -970,8 +991,39 @@ __global__ void __launch_bounds__(NTW, 1)
                             acc += gvs[box_base[j] + ((ox + 1) * 3 + (oy + 1)) * (TX * TY * HZ) - (ox * TY + oy) * HZ];
                 gbox[(int64_t)tile * NBOX + e] = acc;
             }
+            // the next writes of Ts and gcen come after the next tile's barriers
+        };
+
+        int tile = blockIdx.x, prev = -1, last_it = 0;
+        uint32_t m1_cur = 0;
+        load_saved(tile);
+        if (tile < ntiles) {
+            build_A3(tile, 0, 0);
+            m1_cur = L_m1;
+            load_saved(tile + gridDim.x);
+        }
+        for (int it = 0; tile < ntiles; tile += gridDim.x, ++it, last_it = it) {
+            const int b = it & 1, nxt = tile + gridDim.x;
+            // (1) the previous tile's layer-1 input gradient (frees A4)
+            if (prev >= 0 && !(ok = wait_commit(BB_D4 + (b ^ 1), ph4, b ^ 1))) break;
+            // (2) this tile's layer-2 input gradient -> A4
+            if (!(ok = wait_commit(BB_D3 + b, ph3, b))) break;
+            epilogue3(b, m1_cur);
+            // (3) the next tile's A3 (its buffer's previous MMA3 and D3 reads are done)
+            uint32_t m1_nxt = 0;
+            if (nxt < ntiles) {
+                build_A3(nxt, b ^ 1, (it + 1) % 3);
+                m1_nxt = L_m1;
+                load_saved(nxt + gridDim.x);
+            }
+            // (4) g_v and box sums of the previous tile while this tile's MMA4 runs
+            if (prev >= 0) epilogue4(prev, b ^ 1, (it + 2) % 3);
             m1_cur = m1_nxt;
-            nbar_sync(NT);  // gvs is rewritten by the next tile
+            prev = tile;
+        }
+        if (ok && prev >= 0) {
+            const int b = (last_it - 1) & 1;
+            if ((ok = wait_commit(BB_D4 + b, ph4, b))) epilogue4(prev, b, (last_it - 1) % 3);
         }
         if (!ok && tid == 0) atomicExch(err, 1);
     }
