@@ -96,6 +96,10 @@ def test_fft_force_smooth_full(job):
     k = to_np(ctx.rfft(to_dev(f)))
     assert rel_l2(k, np.fft.rfftn(f32(f))) <= FIELD_TOL
     assert rel_l2(to_np(ctx.irfft(to_dev(f32(k)))), opm.irfft3(f32(k))) <= FIELD_TOL
+    # an arbitrary (non-Hermitian) half array: the imaginary parts of the
+    # self-conjugate entries are ignored, as by the oracle's irfftn
+    u = synth.gaussian_vector((N, N, N // 2 + 1), seed=106) + 1j * synth.gaussian_vector((N, N, N // 2 + 1), seed=107)
+    assert rel_l2(to_np(ctx.irfft(to_dev(u))), opm.irfft3(f32(u))) <= FIELD_TOL
     d = synth.lognormal_density(N, seed=105)
     assert rel_l2(to_np(ctx.force(to_dev(d))), opm.force(f32(d), cfg.omega_m)) <= FIELD_TOL
     assert rel_l2(to_np(ctx.smooth(to_dev(d), 4.0)), opm.smooth(f32(d), 4.0 / (L / N))) <= FIELD_TOL
