@@ -149,6 +149,7 @@ void for_each_buffer(const pmr_config& cfg, pmr_ctx* c, F alloc) {
     alloc((void**)(c ? &c->sfrac_all : nullptr), sizeof(float) * 3 * N3 * (cfg.nsteps + 1));
     alloc((void**)(c ? &c->delta : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->F : nullptr), sizeof(float) * 3 * N3);
+    alloc((void**)(c ? &c->F_all : nullptr), sizeof(float) * 3 * N3 * (cfg.nsteps > 0 ? cfg.nsteps : 1));
     alloc((void**)(c ? &c->feat : nullptr), sizeof(float) * 3 * N3);
     alloc((void**)(c ? &c->M : nullptr), sizeof(float) * N3);
     alloc((void**)(c ? &c->MR : nullptr), sizeof(float) * N3);

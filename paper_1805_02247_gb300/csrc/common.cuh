@@ -193,7 +193,8 @@ struct pmr_ctx {
 
     // meshes
     float* delta = nullptr;
-    float* F = nullptr;     // 3 * N3
+    float* F = nullptr;     // 3 * N3 scratch (forces of standalone calls, adjoint temporaries)
+    float* F_all = nullptr; // [nsteps][3][N^3] the force of every step of the forward sweep, kept for the adjoint
     float* feat = nullptr;  // 3 * N3
     float* M = nullptr;
     float* MR = nullptr;

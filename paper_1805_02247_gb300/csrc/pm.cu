@@ -1021,13 +1021,14 @@ int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
     const float om15 = (float)(1.5 * c->cfg.omega_m);
     Mul fm[3];
     for (int j = 0; j < 3; ++j) fm[j] = Mul{MUL_ODD, j, om15, 0.f, 0};
-    float* Fj[3] = {c->F, c->F + N3, c->F + 2 * N3};
     for (int s = 0; s < c->cfg.nsteps; ++s) {
         const float* din = c->disp + (int64_t)s * 3 * N3;
         float* dout = c->disp + (int64_t)(s + 1) * 3 * N3;
+        float* F = c->F_all + (int64_t)s * 3 * N3;  // kept for the adjoint
+        float* Fj[3] = {F, F + N3, F + 2 * N3};
         PMR_TRY(density_slot(c, s, din, c->delta, true));
         PMR_TRY(conv_1toN(c, c->delta, Fj, fm, 3));
-        PMR_TRY(kick_drift(c, c->F, din, dout, c->mom, (float)c->kick[s], (float)c->drift[s]));
+        PMR_TRY(kick_drift(c, F, din, dout, c->mom, (float)c->kick[s], (float)c->drift[s]));
     }
     c->have_forward = true;
     c->fwd_id++;
@@ -1040,32 +1041,24 @@ int pm_forward_impl(pmr_ctx* c, const float2* s_k) {
 int pm_adjoint_impl(pmr_ctx* c, const float* gfin, float2* grad) {
     const int64_t N3 = c->N3;
     const float om15 = (float)(1.5 * c->cfg.omega_m);
-    Mul fm[3], fmT[3];
-    for (int j = 0; j < 3; ++j) {
-        fm[j] = Mul{MUL_ODD, j, om15, 0.f, 0};
-        fmT[j] = Mul{MUL_ODD, j, -om15, 0.f, 0};  // conj of an imaginary multiplier
-    }
-    float* Fj[3] = {c->F, c->F + N3, c->F + 2 * N3};
+    Mul fmT[3];
+    for (int j = 0; j < 3; ++j) fmT[j] = Mul{MUL_ODD, j, -om15, 0.f, 0};  // conj of an imaginary multiplier
     float* Gj[3] = {c->gfeat, c->gfeat + N3, c->gfeat + 2 * N3};
-    // Step s of the adjoint: force F(x_s) recomputed from the forward sweep's
-    // sort; direct kick term; three-mass paint and its force transpose into G;
-    // readout gradient of G at x_s. The readout of step s and the direct term
-    // of step s - 1 share one particle pass (as do the final density's readout
-    // and the direct term of the last step), so F(x_{s-1}) is recomputed first.
+    // Step s of the adjoint: direct kick term with the force F(x_s) the forward
+    // sweep kept; three-mass paint (on the forward sweep's sort) and its force
+    // transpose into G; readout gradient of G at x_s. The readout of step s and
+    // the direct term of step s - 1 share one particle pass (as do the final
+    // density's readout and the direct term of the last step).
     const int S = c->cfg.nsteps;
     const FastDiv fN((uint32_t)c->N);
-    auto force_at = [&](int s) -> int {
-        PMR_TRY(density_slot(c, s, c->disp + (int64_t)s * 3 * N3, c->delta, false));
-        return conv_1toN(c, c->delta, Fj, fm, 3);
-    };
+    auto force_at = [&](int s) -> const float* { return c->F_all + (int64_t)s * 3 * N3; };
     if (S == 0) {
         PMR_TRY(readout_grad(c, gfin, c->disp, N3, true, 1.0f, false, c->lam_x));
         PMR_TRY(check_cuda(c, cudaMemsetAsync(c->lam_p, 0, sizeof(float) * 3 * N3, c->stream), "memset"));
     } else {
-        PMR_TRY(force_at(S - 1));
         k_adj_readout_direct<true><<<nblocks(N3, kT), kT, 0, c->stream>>>(
-            gfin, c->disp + (int64_t)S * 3 * N3, c->F, c->disp + (int64_t)(S - 1) * 3 * N3, c->lam_x, c->lam_p, N3,
-            c->N, fN, (float)c->kick[S - 1], (float)c->drift[S - 1]);
+            gfin, c->disp + (int64_t)S * 3 * N3, force_at(S - 1), c->disp + (int64_t)(S - 1) * 3 * N3, c->lam_x,
+            c->lam_p, N3, c->N, fN, (float)c->kick[S - 1], (float)c->drift[S - 1]);
         PMR_TRY(check_launch(c, "adj_readout_direct"));
     }
     for (int s = S - 1; s >= 0; --s) {
@@ -1078,9 +1071,8 @@ int pm_adjoint_impl(pmr_ctx* c, const float* gfin, float2* grad) {
             PMR_TRY(readout_grad(c, c->gm, d, N3, true, 1.0f, true, c->lam_x));
             break;
         }
-        PMR_TRY(force_at(s - 1));
         k_adj_readout_direct<false><<<nblocks(N3, kT), kT, 0, c->stream>>>(
-            c->gm, d, c->F, c->disp + (int64_t)(s - 1) * 3 * N3, c->lam_x, c->lam_p, N3, c->N, fN,
+            c->gm, d, force_at(s - 1), c->disp + (int64_t)(s - 1) * 3 * N3, c->lam_x, c->lam_p, N3, c->N, fN,
             (float)c->kick[s - 1], (float)c->drift[s - 1]);
         PMR_TRY(check_launch(c, "adj_readout_direct"));
     }
