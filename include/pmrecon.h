@@ -145,8 +145,9 @@ int pmr_linear_field(pmr_ctx* ctx, const float* white, double amplitude, void* s
 int pm_forward(pmr_ctx* ctx, const void* s_k, float* delta_out);
 
 /* Adjoint of the last pm_forward() on this context (Sec. 5.2, PM derivatives
- * written by hand): grad_s_k = (d delta/d s)^T grad_delta. Force fields are
- * recomputed from the stored positions. Returns PMR_ESTATE without a forward. */
+ * written by hand): grad_s_k = (d delta/d s)^T grad_delta, from the per-step
+ * positions, sorts and force fields the forward stored. Returns PMR_ESTATE
+ * without a forward. */
 int pm_adjoint(pmr_ctx* ctx, const float* grad_delta, void* grad_s_k);
 
 /* Network halo-mass map (Sec. 2): delta -> three Gaussian-smoothed fields,

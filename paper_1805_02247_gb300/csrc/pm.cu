@@ -864,8 +864,8 @@ int paint_with(pmr_ctx* c, const float* pos, int64_t np, bool lattice, const uin
 
 // Three-mass paint of the lattice particles with their masses first moved into
 // the sort's order, so the paint's bin loop reads offsets and masses as
-// independent, coalesced loads. Scratch: c->F (the adjoint step has used the
-// force by then; the next step recomputes it).
+// independent, coalesced loads. Scratch: c->F (the kept per-step forces live
+// in c->F_all).
 int paint3_sorted(pmr_ctx* c, const uint32_t* perm, const uint32_t* start, const float* sfrac, const float* mass,
                   float scale, float* const* rho) {
     const int64_t np = c->N3;
