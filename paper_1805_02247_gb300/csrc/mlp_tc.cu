@@ -18,15 +18,18 @@
 // The forward saves, per voxel, y and the ReLU masks of both hidden layers
 // (16 bytes); the backward starts from them at layer 3 instead of recomputing
 // layers 1-2 (halo, operand build, two MMA layers and their epilogues).
-// The backward stages g_v (81 columns) in shared memory and sums it per target
-// cell of the tile's box (the tile grown by one cell, 3 fields x 4 x 6 x 18), so
-// a tile writes 1296 floats instead of 81 x 128; k_stencil_tiles adds the
-// overlapping boxes of up to 8 tiles per cell in a fixed order.
+// The backward folds g_v (81 columns) over the stencil's z offset in
+// registers, stages the 27 folded images in shared memory and sums them per
+// target cell of the tile's box (the tile grown by one cell, 3 fields x 4 x 6 x
+// 18), so a tile writes 1296 floats instead of 81 x 128; k_stencil_tiles adds
+// the overlapping boxes of up to 8 tiles per cell in a fixed order.
 //
 // Both kernels are persistent (one CTA of 17 warps per SM) and warp-
 // specialised: 16 warps build operands and read accumulators, lane 0 of the
-// 17th issues the MMAs, and each layer has its own operand buffer, so one
-// tile's MMAs overlap the next tile's operand build.
+// 17th issues the MMAs. The first layer's operand and accumulator (forward)
+// and the backward's A3, D3 and D4 are double-buffered, so the tensor cores
+// run the next tile's first MMA layer while the compute warps read this tile's
+// accumulators.
 //
 // Every mbarrier wait is bounded; on timeout the block records an error flag,
 // waits (bounded) for its MMAs, frees its TMEM and returns. The host reports
