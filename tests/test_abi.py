@@ -47,6 +47,31 @@ def test_config_struct_matches_defaults_and_layout():
     assert pmrecon.workspace_bytes(pmrecon.default_config(N=10)) == 0  # 10/2 = 5 has no radix-2/3/4 plan
 
 
+def test_workspace_grows_by_one_step_of_kept_state():
+    """One more PM step keeps, per particle of the lattice, its position (12 B),
+    its step's sort (perm 4 B, cell offsets 4 B) and sorted fractional offsets
+    (12 B), and the step's force for the adjoint (12 B): the footprint query the
+    server admits jobs by must grow by exactly that (each buffer rounded to 256 B)."""
+    build.build()
+
+    def r(b):
+        return (b + 255) // 256 * 256
+
+    N = 64
+    N3 = N ** 3
+    for k in (1, 5):
+        a = pmrecon.workspace_bytes(pmrecon.default_config(N=N, nsteps=k))
+        b = pmrecon.workspace_bytes(pmrecon.default_config(N=N, nsteps=k + 1))
+        per_step = (
+            r(12 * N3 * (k + 2)) - r(12 * N3 * (k + 1))        # positions
+            + r(4 * N3 * (k + 2)) - r(4 * N3 * (k + 1))        # perm of each step
+            + r(4 * (N3 + 1) * (k + 2)) - r(4 * (N3 + 1) * (k + 1))  # cell offsets of each step
+            + r(12 * N3 * (k + 2)) - r(12 * N3 * (k + 1))      # sorted fractional offsets
+            + r(12 * N3 * (k + 1)) - r(12 * N3 * k)            # forces kept for the adjoint
+        )
+        assert b - a == per_step
+
+
 def test_growth_is_host_only_and_matches_oracle():
     # pmr_growth needs no device: the library's own quadrature vs the oracle's
     from oracle import cosmo
