@@ -547,11 +547,17 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
     // warp w walks the bins of x-row w along y; the next row's bin bounds are
     // loaded before this row's particles
     const int bx = w;
+    // the warp's rows (x0 - 1 + bx, y0 - 1 + by): the x part of the base is fixed,
+    // y advances by one per row (periodic)
+    int gxw = x0 - 1 + bx;
+    gxw = gxw < 0 ? gxw + N : (gxw >= N ? gxw - N : gxw);
+    const int64_t xbase = (int64_t)gxw * N * N + z;
+    int gy_n = y0 - 1 < 0 ? y0 - 1 + N : y0 - 1;
     uint32_t s_n = 0, e_n = 0;
     if (zin) {
-        const int64_t rb = row_base(bx * WT::RY);
-        s_n = start[rb + z];
-        e_n = start[rb + z + 1];
+        const int64_t rb = xbase + (int64_t)gy_n * N;
+        s_n = start[rb];
+        e_n = start[rb + 1];
     }
     // first the halo bin z0 - 1 of each of the warp's rows (lane 0's left
     // neighbour there), one row per lane; only this warp reads them
@@ -573,10 +579,11 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
     for (int by = 0; by < WT::RY; ++by) {
         const int r = bx * WT::RY + by;
         const uint32_t s = s_n, e = e_n;
+        gy_n = gy_n + 1 == N ? 0 : gy_n + 1;
         if (by + 1 < WT::RY && zin) {
-            const int64_t rb = row_base(r + 1);
-            s_n = start[rb + z];
-            e_n = start[rb + z + 1];
+            const int64_t rb = xbase + (int64_t)gy_n * N;
+            s_n = start[rb];
+            e_n = start[rb + 1];
         }
         float S[2][2][2][NM] = {};
         for (uint32_t j = s; j < e; ++j) acc(j, S, false);
