@@ -568,6 +568,7 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
         const int64_t rb = row_base(r);
         float H[2][2][2][NM] = {};
         const uint32_t hs = start[rb + zh], he = start[rb + zh + 1];
+#pragma unroll 1
         for (uint32_t j = hs; j < he; ++j) acc(j, H, true);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -586,6 +587,8 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
             e_n = start[rb + 1];
         }
         float S[2][2][2][NM] = {};
+        // bins hold about one particle: no unrolled body to skip past
+#pragma unroll 1
         for (uint32_t j = s; j < e; ++j) acc(j, S, false);
 #pragma unroll
         for (int ox = 0; ox < 2; ++ox)
