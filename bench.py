@@ -95,8 +95,6 @@ def algorithmic(name: str, N: int):
 # kernels on this workload, one evaluation's launches averaged; kernels changed
 # since their counters were taken have no entry. Valid for N = 256 only.
 TRAFFIC_256 = {
-    "paint3": 472.8e6 + 174.1e6,
-    "paint": 271.1e6 + 48.5e6,
     "x_conv_3": 68.6e6 + 141.2e6,
     "adj_readout_direct": 1035.9e6 + 373.0e6,  # mean of the 9 + 1 launches of its two forms
     "x_conv_in3": 203.0e6 + 43.5e6,
