@@ -482,8 +482,9 @@ struct WTile {
     static constexpr int X = 8, Y = NM == 1 ? 16 : 8;
     static constexpr int RX = X + 1, RY = Y + 1, NR = RX * RY;
     static constexpr int W = RX;  // warps per block: one per x-row of bins
-    // U values [2 (ox)][NM][RX][Y][32], then the halo bins' S_(ox,oy,1) [4][NM][NR]
-    static constexpr size_t smem = sizeof(float) * (2 * NM * RX * Y * 32 + 4 * NM * NR);
+    // U values [2 (ox)][NM][X][Y][32] (U_0 of bin rows 1..X, U_1 of rows 0..X-1: the
+    // ones the x fold reads), then the halo bins' S_(ox,oy,1) [4][NM][NR]
+    static constexpr size_t smem = sizeof(float) * (2 * NM * X * Y * 32 + 4 * NM * NR);
 };
 
 template <int NM, int MMODE>
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
                                                                      float scale, float offset, float* r0, float* r1,
                                                                      float* r2) {
     using WT = WTile<NM>;
-    extern __shared__ float Us[];  // [2 (ox)][NM][RX][Y][32]
+    extern __shared__ float Us[];  // [2 (ox)][NM][X][Y][32]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int z0 = blockIdx.x * 32, y0 = blockIdx.y * WT::Y, x0 = blockIdx.z * WT::X;
     const int z = z0 + lane;
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
     }
     // first the halo bin z0 - 1 of each of the warp's rows (lane 0's left
     // neighbour there), one row per lane; only this warp reads them
-    float* Hs = Us + 2 * NM * WT::RX * WT::Y * 32;  // [4 (ox,oy)][NM][NR]
+    float* Hs = Us + 2 * NM * WT::X * WT::Y * 32;  // [4 (ox,oy)][NM][NR]
     static_assert(WTile<NM>::RY <= 32, "one halo row per lane");
     if (lane < WT::RY) {
         const int r = bx * WT::RY + lane;
@@ -601,7 +602,9 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
                     if (lane == 0) left = Hs[((ox * 2 + oy) * NM + m) * WT::NR + r];
                     T[oy] = S[ox][oy][0][m] + left;
                 }
-                if (by > 0) Us[(((ox * NM + m) * WT::RX + bx) * WT::Y + by - 1) * 32 + lane] = T[0] + C[ox][m];
+                const int ux = bx - 1 + ox;  // U_0 of row bx at slot bx - 1, U_1 at slot bx
+                if (by > 0 && ux >= 0 && ux < WT::X)
+                    Us[(((ox * NM + m) * WT::X + ux) * WT::Y + by - 1) * 32 + lane] = T[0] + C[ox][m];
                 C[ox][m] = T[1];
             }
     }
@@ -613,8 +616,8 @@ __global__ void __launch_bounds__(WTile<NM>::W * 32, NM == 1 ? 4 : 3) k_paint_wt
         const int64_t c = ((int64_t)gx * N + gy) * N + z;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            const float u0 = Us[(((0 * NM + m) * WT::RX + lx + 1) * WT::Y + ly) * 32 + lane];
-            const float u1 = Us[(((1 * NM + m) * WT::RX + lx) * WT::Y + ly) * 32 + lane];
+            const float u0 = Us[(((0 * NM + m) * WT::X + lx) * WT::Y + ly) * 32 + lane];
+            const float u1 = Us[(((1 * NM + m) * WT::X + lx) * WT::Y + ly) * 32 + lane];
             float* out = m == 0 ? r0 : (m == 1 ? r1 : r2);
             out[c] = (u0 + u1) * scale + offset;
         }
