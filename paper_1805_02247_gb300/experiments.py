@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import sys
 import time
 
 import numpy as np
@@ -216,6 +217,43 @@ def precision(N=256, L=400.0, nsteps=5, iters=200, R_sm=4.0, M0=1e8, device="cud
                                               "control_rel_diff": abs(yard["c"] / yard[0] - 1)}}
 
 
+def summarize_recon(res: dict, command: str, nk: int = 16) -> dict:
+    """The per-stage summary of full_reconstruction's result: the loss of every
+    iteration, and r_c, TF and s (Sec. 4.3) of the linear field on the first nk
+    k bins after each stage."""
+    def stats(d, keys):
+        return {k: [round(float(v), 4) for v in d[k][:nk]] for k in keys}
+
+    cfg = res["config"]
+    what = "annealed reconstruction on the GPU"
+    if cfg.get("schedule") == "paper":
+        what += (", the procedure of Sec. 5.3 (M0 = 1e12 with N_sm = 4, 2, 1, 0.5, 0 cells, then M0 = 1e11 with "
+                 "N_sm = 1, 0.5, 0; a stage ends when an iteration lowers the loss by less than 0.1%, from its "
+                 f"{cfg['min_iter']}th iteration on, at most {cfg['max_iter']} iterations)")
+    return {
+        "what": what,
+        "command": command,
+        "config": cfg,
+        "setup_seconds": round(res["setup_seconds"], 2),
+        "reconstruction_seconds": round(res["reconstruction_seconds"], 3),
+        "iterations": res["iterations"],
+        "k_h_per_Mpc": [round(float(v), 4) for v in res["before"]["linear"]["k"][:nk]],
+        "modes": [float(v) for v in res["before"]["linear"]["modes"][:nk]],
+        "start": {"linear_r_c": stats(res["before"]["linear"], ["r_c"])["r_c"]},
+        "stages": [{
+            "R_sm_Mpc_h": st["R_sm"],
+            "M0": st["M0"],
+            "iterations": st["iterations"],
+            "converged": st["converged"],
+            "seconds": round(st["seconds"], 3),
+            "loss_per_iteration": [round(float(v), 1) for v in st["losses"]],
+            "linear_after": stats(st["linear_after"], ["r_c", "transfer", "stochasticity"]),
+        } for st in res["stages"]],
+        "final": {"linear": stats(res["after"]["linear"], ["r_c", "transfer", "stochasticity"]),
+                  "final_density": stats(res["after"]["final"], ["r_c", "transfer"])},
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("run", choices=["recon", "precision"])
@@ -231,6 +269,8 @@ def main(argv=None):
     ap.add_argument("--R-sm", type=float, default=4.0, help="precision: residual smoothing, Mpc/h")
     ap.add_argument("--M0", type=float, default=1e8, help="precision: M0")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--summary", default=None,
+                    help="recon: also write the per-stage summary (first 16 k bins, rounded) to this path")
     args = ap.parse_args(argv)
     if args.run == "precision":
         res = precision(N=args.N or 256, L=args.L, nsteps=args.nsteps, iters=args.iters or 200,
@@ -247,6 +287,13 @@ def main(argv=None):
     if args.out:
         with open(args.out, "w") as f:
             f.write(text)
+    if args.summary:
+        words = ["python -m paper_1805_02247_gb300.experiments"] + list(argv if argv is not None else sys.argv[1:])
+        command = " ".join(w for i, w in enumerate(words)
+                           if w not in ("--summary", "--out") and words[i - 1] not in ("--summary", "--out"))
+        with open(args.summary, "w") as f:
+            json.dump(summarize_recon(res, command), f, indent=1)
+            f.write("\n")
     s = res["stages"]
     print(json.dumps({"iterations": res["iterations"], "seconds": res["reconstruction_seconds"],
                       "stages": [(x["R_sm"], x["iterations"], x["loss_first"], x["loss_last"]) for x in s],
