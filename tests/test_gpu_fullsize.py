@@ -126,6 +126,13 @@ def test_lpt2_ics_full():
     x_want, p_want = opm.lpt_ics(s, setup)
     assert rel_l2(to_np(disp), x_want - opm.lattice(N)) <= FIELD_TOL
     assert rel_l2(to_np(mom), p_want) <= FIELD_TOL
+    # and their adjoint, element by element: the three-to-one fused x-pass (the
+    # force transpose of every adjoint step) at the benchmark's mesh, plus the
+    # accumulating three-to-one pass of the Hessian terms
+    lx = f32(synth.gaussian_vector((3, N ** 3), seed=33))
+    lp = f32(synth.gaussian_vector((3, N ** 3), seed=34))
+    g = to_np(ctx.lpt_ics_adjoint(to_dev(s), to_dev(lx), to_dev(lp)))
+    assert rel_l2(g, opm.lpt_ics_T(lx, lp, s, setup)) <= GRAD_TOL
     ctx.close()
 
 

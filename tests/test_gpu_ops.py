@@ -164,7 +164,7 @@ def test_rfft_irfft_parity(N):
     assert rel_l2(got, opm.irfft3(f32(u))) <= FIELD_TOL
 
 
-@pytest.mark.parametrize("N", [32, 64, 128])
+@pytest.mark.parametrize("N", [32, 64, 128, 192])
 def test_force_and_smooth_parity(N):
     ctx, cfg = context(N=N, L=100.0)
     d = synth.gaussian_vector((N, N, N), seed=11)
@@ -230,7 +230,7 @@ def test_power_spectra_parity(N, L):
     assert all(np.array_equal(x, y) for x, y in zip(got, again))
 
 
-@pytest.mark.parametrize("N,L", [(32, 100.0), (24, 400.0)])
+@pytest.mark.parametrize("N,L", [(32, 100.0), (24, 400.0), (192, 400.0)])
 def test_lpt2_ics_and_adjoint_parity(N, L):
     # second-order LPT initial conditions (Sec. 3) and their adjoint
     ctx, _ = context(N=N, L=L, lpt_order=2)
