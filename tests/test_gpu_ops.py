@@ -164,6 +164,21 @@ def test_rfft_irfft_parity(N):
     assert rel_l2(got, opm.irfft3(f32(u))) <= FIELD_TOL
 
 
+def test_fft_and_force_parity_at_the_largest_mesh():
+    # N = 512, the largest mesh a context accepts, has register plans of its own
+    # (512-point columns as 16 x 32, 256-point rows as 16 x 16)
+    N = 512
+    ctx, cfg = context(N=N, L=800.0, nsteps=1)
+    f = synth.gaussian_vector((N, N, N), seed=41)
+    k = to_np(ctx.rfft(to_dev(f)))
+    assert rel_l2(k, np.fft.rfftn(f32(f))) <= FIELD_TOL
+    assert rel_l2(to_np(ctx.irfft(to_dev(f32(k)))), opm.irfft3(f32(k))) <= FIELD_TOL
+    del f, k
+    d = synth.lognormal_density(N, seed=42)
+    assert rel_l2(to_np(ctx.force(to_dev(d))), opm.force(f32(d), cfg.omega_m)) <= FIELD_TOL
+    ctx.close()
+
+
 @pytest.mark.parametrize("N", [32, 64, 128, 192])
 def test_force_and_smooth_parity(N):
     ctx, cfg = context(N=N, L=100.0)
