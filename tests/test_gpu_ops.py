@@ -150,7 +150,7 @@ def test_readout_and_grad_parity():
     assert rel_l2(rg, opm.readout_grad(f32(g), f32(x), f32_wrap=True)) <= FIELD_TOL
 
 
-@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96, 128, 192])
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 64, 96, 128, 192, 384])
 def test_rfft_irfft_parity(N):
     # 64, 128, 192 (and 256, 512) take the register four-step column passes
     ctx, _ = context(N=N)
