@@ -8,6 +8,7 @@ import pytest
 import torch
 
 from oracle import loss as oloss
+from oracle import nn as onn
 from oracle import pm as opm
 from paper_1805_02247_gb300 import synth
 
@@ -290,3 +291,28 @@ def test_two_point_statistics_parity(N, L):
         assert rel_l2(got[key].numpy(), want) <= FIELD_TOL, key
     _, P_nn, _, _ = twopt.power_spectra(f32(h) - f32(a), f32(h) - f32(a), L)
     assert rel_l2(got["s"].numpy(), P_nn) <= 1e-4  # the stochasticity is the noise power
+
+
+def test_network_and_adjoint_on_ragged_z_lines():
+    # 192 = 128 + 64: every z-line of the tensor-core forward is one full tile and
+    # one ragged tile (64 of its 128 rows); sampled voxels, the rows on both sides
+    # of the tile boundary and the line's last rows included, and the adjoint there
+    N, L = 192, 300.0
+    ctx, _ = context(N=N, L=L, nsteps=1)
+    setup = opm.PMSetup(N=N, L=L, nsteps=1)
+    ls = oloss.LossSetup()
+    w = synth.xavier_weights(1)
+    d = synth.lognormal_density(N, seed=121)
+    M = to_np(ctx.nn_halo_map(to_dev(d)))
+    feats = oloss.features(f32(d), setup, ls)
+    edge = np.array([[x, y, z] for x in (0, 1, N - 1) for y in (0, 5, N - 1)
+                     for z in (0, 1, 126, 127, 128, 129, 190, 191)], np.int64)
+    vox = np.concatenate([synth.sample_voxels(N, 2048, seed=122), edge])
+    assert rel_l2(M[vox[:, 0], vox[:, 1], vox[:, 2]], onn.mlp_at(feats, vox, w, ls.M_scale)) <= FIELD_TOL
+    vals = f32(synth.gaussian_vector(vox.shape[0], seed=123))
+    gM = np.zeros((N, N, N), np.float32)
+    np.add.at(gM, (vox[:, 0], vox[:, 1], vox[:, 2]), vals.astype(np.float32))
+    got = to_np(ctx.nn_halo_map_adjoint(to_dev(d), to_dev(gM)))
+    want = oloss.features_T(onn.mlp_backward_at(vals, vox, feats, w, ls.M_scale), setup, ls)
+    assert rel_l2(got, want) <= GRAD_TOL
+    ctx.close()
