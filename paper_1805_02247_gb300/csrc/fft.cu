@@ -904,18 +904,26 @@ __global__ void __launch_bounds__(ZReg<RG>::T) k_z_r2c_reg(const float* __restri
         float2 v1[RG::A1][RG::N1], v2[RG::A2][RG::N2];
         row_fft<RG, false>(A + r * Z::PITCH, s_twM, g, v1, v2);
     }
-    // X_k = E_k + exp(-2 pi i k / N) O_k from Z_k and conj(Z_(M-k))
-    for (int t = tid; t < Z::R * P; t += Z::T) {
-        const int rr = t / P, k = t - rr * P;
+    // X_k = E_k + exp(-2 pi i k / N) O_k from Z_k and conj(Z_(M-k)); one thread per
+    // pair (k, M - k), which both come from the same two values (k = 0 also gives X_M)
+    auto split = [&](float2 zk, float2 zc, int kk) {
+        zc.y = -zc.y;
+        const float2 e = cscale(cadd(zk, zc), 0.5f);
+        const float2 dd = csub(zk, zc);
+        const float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
+        return cadd(e, cmul(s_twN[kk], o));
+    };
+    for (int t = tid; t < Z::R * (M / 2 + 1); t += Z::T) {
+        const int rr = t / (M / 2 + 1), k = t - rr * (M / 2 + 1);
         if (rr >= rows) continue;
         const float2* Zr = A + rr * Z::PITCH;
-        float2 zk = Zr[k == M ? 0 : k];
-        float2 zc = Zr[k == 0 ? 0 : M - k];
-        zc.y = -zc.y;
-        float2 e = cscale(cadd(zk, zc), 0.5f);
-        float2 dd = csub(zk, zc);
-        float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // -i/2 (zk - zc)
-        out[(row0 + rr) * P + k] = cadd(e, cmul(s_twN[k], o));
+        const float2 za = Zr[k], zb = Zr[k == 0 ? 0 : M - k];  // Z_k, Z_(M-k)
+        float2* orow = out + (row0 + rr) * P;
+        orow[k] = split(za, zb, k);
+        if (k == 0)
+            orow[M] = split(za, za, M);
+        else if (M - k != k)
+            orow[M - k] = split(zb, za, M - k);
     }
 }
 
